@@ -1,0 +1,242 @@
+"""Seeded synthetic inputs shared by the oracle and the GPU path.
+
+This module only *generates data*: random circuits written out as explicit gate
+matrices, random tail bitstrings, sliced-edge selections and synthetic head
+tensors.  It contains none of the contraction, sampling or fidelity arithmetic
+of the method, so the oracle and the CUDA path stay independent: both read the
+same numbers and compute everything else on their own.
+
+Circuit model (the paper's Sycamore-style random circuits, Sec. "Method" and the
+fSim equation; gate-set details that the paper leaves to its data files are a
+documented reading):
+
+* qubits on an R x C grid, qubit q = r*C + c;
+* each cycle = a layer of single-qubit gates on every qubit, drawn uniformly
+  from {sqrt(X), sqrt(Y), sqrt(W)} excluding the previous one on that qubit,
+  followed by one layer of fSim gates on the couplers of one pattern;
+* couplers: A = horizontal bonds with even column, B = horizontal with odd
+  column, C = vertical with even row, D = vertical with odd row; cycle t uses
+  pattern "ABCDCDAB"[t mod 8];
+* a final layer of single-qubit gates after the last cycle;
+* fSim(theta, phi) per the paper's fSim equation, theta = pi/2 + U(-0.11, 0.11)
+  and phi = pi/6 + U(-0.05, 0.05), fixed per coupler.
+
+Gate matrix convention: row = output, column = input; for two-qubit gates the
+basis is |q0 q1> with q0 the high bit.  Bitstrings are uint64 with qubit q at
+bit q.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+PATTERN_ABCD = "ABCDCDAB"
+
+# kinds of a cut edge (match the C ABI's TN_EDGE_* values)
+EDGE_SLICE = 0
+EDGE_PIN = 1
+
+
+@dataclass
+class Gate:
+    arity: int
+    q0: int
+    q1: int          # -1 for single-qubit gates
+    U: np.ndarray    # (2,2) or (4,4) complex128, row = output, column = input
+    kind: str = ""   # "sx", "sy", "sw", "fsim"
+    theta: float = 0.0
+    phi: float = 0.0
+
+
+@dataclass
+class Circuit:
+    n_qubits: int
+    gates: list
+    rows: int = 0
+    cols: int = 0
+    cycles: int = 0
+    seed: int = 0
+    cycle_first_gate: list = field(default_factory=list)  # index of each cycle's first 2q gate
+
+    def two_qubit_gates(self):
+        return [i for i, g in enumerate(self.gates) if g.arity == 2]
+
+
+def _sqrt_gate(G):
+    # (I - iG)/sqrt(2): a square root of G up to a global phase
+    return (np.eye(2, dtype=np.complex128) - 1j * G) / math.sqrt(2.0)
+
+
+_X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+_Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+_W = (_X + _Y) / math.sqrt(2.0)
+SQRT_GATES = {"sx": _sqrt_gate(_X), "sy": _sqrt_gate(_Y), "sw": _sqrt_gate(_W)}
+
+
+def fsim(theta: float, phi: float) -> np.ndarray:
+    """fSim(theta, phi) in the basis |q0 q1> (q0 high bit), as printed in the
+    paper's fSim equation."""
+    c, s = math.cos(theta), math.sin(theta)
+    U = np.zeros((4, 4), dtype=np.complex128)
+    U[0, 0] = 1.0
+    U[1, 1] = c
+    U[1, 2] = -1j * s
+    U[2, 1] = -1j * s
+    U[2, 2] = c
+    U[3, 3] = np.exp(-1j * phi)
+    return U
+
+
+def grid_couplers(rows: int, cols: int):
+    """Coupler lists of the four patterns A, B, C, D on an R x C grid."""
+    pats = {"A": [], "B": [], "C": [], "D": []}
+    for r in range(rows):
+        for c in range(cols - 1):
+            pats["A" if c % 2 == 0 else "B"].append((r * cols + c, r * cols + c + 1))
+    for r in range(rows - 1):
+        for c in range(cols):
+            pats["C" if r % 2 == 0 else "D"].append((r * cols + c, (r + 1) * cols + c))
+    return pats
+
+
+def make_grid_circuit(rows: int, cols: int, cycles: int, seed: int,
+                      sequence: str = PATTERN_ABCD) -> Circuit:
+    """Seeded Sycamore-like circuit on an R x C grid (see the module docstring)."""
+    rng = np.random.default_rng(seed)
+    n = rows * cols
+    pats = grid_couplers(rows, cols)
+    params = {}
+    for p in pats.values():
+        for cp in p:
+            params[cp] = (math.pi / 2 + rng.uniform(-0.11, 0.11),
+                          math.pi / 6 + rng.uniform(-0.05, 0.05))
+    gates = []
+    prev = [None] * n
+    names = ["sx", "sy", "sw"]
+
+    def single_layer():
+        for q in range(n):
+            choices = [k for k in names if k != prev[q]]
+            k = choices[rng.integers(len(choices))]
+            prev[q] = k
+            gates.append(Gate(1, q, -1, SQRT_GATES[k].copy(), kind=k))
+
+    first = []
+    for t in range(cycles):
+        single_layer()
+        first.append(len(gates))
+        for (a, b) in pats[sequence[t % len(sequence)]]:
+            th, ph = params[(a, b)]
+            gates.append(Gate(2, a, b, fsim(th, ph), kind="fsim", theta=th, phi=ph))
+    single_layer()
+    return Circuit(n, gates, rows, cols, cycles, seed, first)
+
+
+def make_random_2q_circuit(n: int, depth: int, seed: int) -> Circuit:
+    """Circuit of random (Haar-ish) 1q and generic 2q unitaries on random qubit
+    pairs, both orientations; exercises conventions the symmetric fSim cannot."""
+    rng = np.random.default_rng(seed)
+    gates = []
+    for _ in range(depth):
+        for q in range(n):
+            Z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+            Q, _ = np.linalg.qr(Z)
+            gates.append(Gate(1, q, -1, Q, kind="u1"))
+        perm = rng.permutation(n)
+        for i in range(0, n - 1, 2):
+            a, b = int(perm[i]), int(perm[i + 1])
+            Z = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+            Q, _ = np.linalg.qr(Z)
+            gates.append(Gate(2, a, b, Q, kind="u2"))
+    return Circuit(n, gates, 0, 0, depth, seed, [])
+
+
+def draw_tails(n_qubits: int, open_qubits, L: int, seed: int, distinct: bool = True) -> np.ndarray:
+    """L uniformly random tail bitstrings (uint64, open-qubit bits zero), drawn by
+    coin flips and, when `distinct`, without repetition (duplicates redrawn)."""
+    rng = np.random.default_rng(seed)
+    open_mask = 0
+    for q in open_qubits:
+        open_mask |= 1 << int(q)
+    full = (1 << n_qubits) - 1
+    tail_mask = full & ~open_mask
+    n_tail = n_qubits - len(open_qubits)
+    if distinct and L > (1 << n_tail):
+        raise ValueError("more distinct tails requested than tail patterns exist")
+    out, seen = [], set()
+    while len(out) < L:
+        bits = rng.integers(0, 2, size=n_qubits)
+        v = 0
+        for q in range(n_qubits):
+            if bits[q]:
+                v |= 1 << q
+        v &= tail_mask
+        if distinct and v in seen:
+            continue
+        seen.add(v)
+        out.append(v)
+    return np.array(out, dtype=np.uint64)
+
+
+def mid_circuit_cut_edges(circ: Circuit, n_gates: int, kind: int = EDGE_SLICE, cycle: int | None = None,
+                          value: int = 0):
+    """Input edges of `n_gates` fSim gates of one middle cycle, spread over the
+    layer (two edges per gate, leg 0 = input of q0, leg 1 = input of q1).
+    Returns a list of (gate_index, leg, kind, value)."""
+    if cycle is None:
+        cycle = circ.cycles // 2
+    start = circ.cycle_first_gate[cycle]
+    end = circ.cycle_first_gate[cycle + 1] if cycle + 1 < len(circ.cycle_first_gate) else len(circ.gates)
+    layer = [i for i in range(start, end) if circ.gates[i].arity == 2]
+    if len(layer) < n_gates:
+        raise ValueError("not enough two-qubit gates in the chosen cycle")
+    pick = np.linspace(0, len(layer) - 1, n_gates).round().astype(int)
+    edges = []
+    for j in pick:
+        gi = layer[int(j)]
+        edges.append((gi, 0, kind, value))
+        edges.append((gi, 1, kind, value))
+    return edges
+
+
+def synthetic_head(L: int, h: int, seed: int) -> np.ndarray:
+    """Seeded complex128 head tensor [L][2^h] with Porter-Thomas-like magnitudes
+    (complex Gaussian entries), for sampler tests that need no contraction."""
+    rng = np.random.default_rng(seed)
+    H = (rng.normal(size=(L, 1 << h)) + 1j * rng.normal(size=(L, 1 << h))) / math.sqrt(2.0)
+    return H.astype(np.complex128)
+
+
+# ---- the five workloads (shapes of the paper's experiments, synthetic data) ----
+
+def config_tiny():
+    """12-qubit 3x4 grid, 8 cycles, all qubits open, one group, no slicing."""
+    circ = make_grid_circuit(3, 4, 8, seed=1)
+    open_q = list(range(12))
+    tails = np.zeros(1, dtype=np.uint64)
+    return dict(circuit=circ, open_qubits=open_q, tails=tails, edges=[], n_samples=10_000,
+                sample_seed=2, name="grid3x4_m8_open12")
+
+
+def config_sliced30():
+    """30-qubit 5x6 grid, 14 cycles; 10 open qubits (the last two rows) x 64
+    distinct tails; 6 sliced edges = inputs of 3 mid-circuit fSim gates."""
+    circ = make_grid_circuit(5, 6, 14, seed=3)
+    open_q = list(range(20, 30))
+    tails = draw_tails(30, open_q, 64, seed=33)
+    edges = mid_circuit_cut_edges(circ, 3, EDGE_SLICE)
+    return dict(circuit=circ, open_qubits=open_q, tails=tails, edges=edges, n_samples=64,
+                sample_seed=4, name="grid5x6_m14_open10_L64_k6")
+
+
+def config_small(rows=4, cols=4, cycles=8, seed=11, n_open=6, L=8, n_cut_gates=2, tail_seed=12):
+    """Scaled-down sliced sparse-state case used by parity tests."""
+    circ = make_grid_circuit(rows, cols, cycles, seed=seed)
+    n = rows * cols
+    open_q = list(range(n - n_open, n))
+    tails = draw_tails(n, open_q, L, seed=tail_seed)
+    edges = mid_circuit_cut_edges(circ, n_cut_gates, EDGE_SLICE) if n_cut_gates else []
+    return dict(circuit=circ, open_qubits=open_q, tails=tails, edges=edges, n_samples=L,
+                sample_seed=5, name=f"grid{rows}x{cols}_m{cycles}")

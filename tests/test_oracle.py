@@ -1,0 +1,276 @@
+"""Pins of the CPU oracle to facts other than itself (no GPU needed).
+
+Each test names the passage or the mathematics it checks against.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import circuit_inputs as ci
+import oracle as O
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+
+
+# ---------------- gates (fSim equation; Supplement, sliced fSim) ----------------
+
+def test_gates_unitary_and_square_roots():
+    for k, U in ci.SQRT_GATES.items():
+        assert np.allclose(U.conj().T @ U, np.eye(2), atol=1e-14)
+        G = {"sx": np.array([[0, 1], [1, 0]]), "sy": np.array([[0, -1j], [1j, 0]]),
+             "sw": (np.array([[0, 1], [1, 0]]) + np.array([[0, -1j], [1j, 0]])) / math.sqrt(2)}[k]
+        # (I - iG)/sqrt 2 squares to -iG: a square root of G up to a global phase
+        assert np.allclose(U @ U, -1j * G, atol=1e-14)
+    U = ci.fsim(1.3, 0.4)
+    assert np.allclose(U.conj().T @ U, np.eye(4), atol=1e-14)
+
+
+@pytest.mark.parametrize("theta", [math.pi / 2, math.pi / 2 + 0.1, math.pi / 2 - 0.07, 1.0])
+@pytest.mark.parametrize("leg,v", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_pinned_fsim_singular_values_fix_companion_factor(theta, leg, v):
+    """Supplement, singular values of the sliced fSim: pinning one input of the
+    fSim leaves squared singular values {1 + sin^2 theta, cos^2 theta} across
+    the partner qubit's output (the companion edge); the kept share of the
+    norm is the companion factor."""
+    G = ci.fsim(theta, 0.5).reshape(2, 2, 2, 2)           # [o0, o1, i0, i1]
+    T = G[:, :, v, :] if leg == 0 else G[:, :, :, v]      # [o0, o1, free input]
+    if leg == 0:       # companion = partner output o1: group (free input, o0) vs o1
+        M = np.transpose(T, (2, 0, 1)).reshape(4, 2)
+    else:              # companion = partner output o0
+        M = np.transpose(T, (2, 1, 0)).reshape(4, 2)
+    s2 = np.sort(np.linalg.svd(M, compute_uv=False) ** 2)[::-1]
+    assert np.allclose(s2, [1 + math.sin(theta) ** 2, math.cos(theta) ** 2], atol=1e-13)
+    assert math.isclose(s2[0] / s2.sum(), O.companion_factor(theta), rel_tol=1e-13)
+
+
+def test_double_pin_is_rank_one_product():
+    """Method case (i): both inputs pinned to 0 gives B = (1,0) x (1,0)."""
+    G = ci.fsim(math.pi / 2 + 0.05, math.pi / 6).reshape(2, 2, 2, 2)
+    B = G[:, :, 0, 0]
+    assert np.allclose(B, np.outer([1, 0], [1, 0]), atol=1e-15)
+
+
+# ---------------- simulator ----------------
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_statevector_matches_brute_force(seed):
+    c = ci.make_random_2q_circuit(5, 3, seed=seed)
+    twoq = c.two_qubit_gates()
+    cuts = [(twoq[1], 0, 1), (twoq[3], 1, 0)]
+    for cc in ([], cuts):
+        a = O.statevector(c, cc)
+        b = O.brute_force_state(c, cc)
+        assert np.abs(a - b).max() < 1e-13
+
+
+def test_statevector_grid_brute_force_and_norm():
+    c = ci.make_grid_circuit(2, 3, 5, seed=9)
+    a = O.statevector(c)
+    assert abs(np.linalg.norm(a) - 1.0) < 1e-13      # unitary network
+    assert np.abs(a - O.brute_force_state(c)).max() < 1e-13
+
+
+def test_bitstring_index_convention():
+    # qubit q is bit q; open qubit j takes bit j of mu
+    assert O.bitstring_index(0b1010, [0, 2], 0b11) == 0b1111
+    assert O.bitstring_index(0b1111, [1], 0) == 0b1101
+
+
+# ---------------- O1 vs O2 (two independent routes) ----------------
+
+@pytest.mark.parametrize("case", [dict(r=3, c=4, m=6, seed=5, n_open=4, L=6, cut=1),
+                                  dict(r=2, c=4, m=8, seed=6, n_open=0, L=5, cut=1),
+                                  dict(r=3, c=3, m=5, seed=8, n_open=9, L=1, cut=0)])
+def test_statevector_matches_network(case):
+    cfg = ci.config_small(case["r"], case["c"], case["m"], seed=case["seed"], n_open=case["n_open"],
+                          L=case["L"], n_cut_gates=case["cut"])
+    circ = cfg["circuit"]
+    se = [(g, l) for (g, l, k, v) in cfg["edges"]]
+    psi = O.sliced_statevector(circ, se, slice_range=(1, 3) if se else None)
+    H1 = O.sparse_state_from_vector(psi, cfg["open_qubits"], cfg["tails"])
+    H2 = O.network_amplitudes(circ, cfg["open_qubits"], cfg["tails"], se, slice_range=(1, 3) if se else None)
+    assert np.abs(H1 - H2).max() <= 1e-12 * max(1e-300, np.abs(H1).max())
+
+
+def test_generic_gates_network_matches_statevector():
+    c = ci.make_random_2q_circuit(6, 3, seed=4)
+    tails = ci.draw_tails(6, [1, 4], 5, seed=1)
+    twoq = c.two_qubit_gates()
+    se = [(twoq[2], 0), (twoq[4], 1)]
+    pins = [(twoq[5], 0, 1)]
+    psi = O.sliced_statevector(c, se, pins=pins)
+    H1 = O.sparse_state_from_vector(psi, [1, 4], tails)
+    H2 = O.network_amplitudes(c, [1, 4], tails, se, pins=pins)
+    assert np.abs(H1 - H2).max() < 1e-13
+
+
+# ---------------- slicing identities (Supplement, slicing) ----------------
+
+def test_slice_sum_equals_unsliced():
+    c = ci.make_grid_circuit(3, 4, 8, seed=2)
+    se = [(g, l) for (g, l, k, v) in ci.mid_circuit_cut_edges(c, 3)]      # 2^6 slices
+    full = O.statevector(c)
+    summed = O.sliced_statevector(c, se)
+    assert np.abs(full - summed).max() < 1e-14
+
+
+def test_prefix_kept_range_equals_pinned_top_bits():
+    """Keeping slices [0, 2^(k-t)) is the same as pinning the top t sliced
+    edges to 0 and summing the others (kept fraction 2^-t)."""
+    c = ci.make_grid_circuit(3, 3, 7, seed=4)
+    se = [(g, l) for (g, l, k, v) in ci.mid_circuit_cut_edges(c, 2)]      # k = 4
+    kept = O.sliced_statevector(c, se, slice_range=(0, 4))
+    pinned = O.sliced_statevector(c, se[:2], pins=[(g, l, 0) for (g, l) in se[2:]])
+    assert np.abs(kept - pinned).max() < 1e-14
+
+
+def test_hole_equals_gate_removed_and_outputs_projected():
+    """Method case (i): pinning both inputs of an fSim to 0 acts like the
+    product of (1,0) vectors: the gate disappears and both wires are |0><0|."""
+    c = ci.make_grid_circuit(3, 3, 6, seed=12)
+    gi = ci.mid_circuit_cut_edges(c, 1)[0][0]
+    a = O.statevector(c, [(gi, 0, 0), (gi, 1, 0)])
+    c2 = ci.Circuit(c.n_qubits, list(c.gates), c.rows, c.cols, c.cycles, c.seed, c.cycle_first_gate)
+    g = c.gates[gi]
+    c2.gates[gi] = ci.Gate(2, g.q0, g.q1, np.diag([1.0, 0, 0, 0]).astype(np.complex128), kind="proj00")
+    b = O.statevector(c2)
+    assert np.abs(a - b).max() < 1e-15
+
+
+# ---------------- fidelity and statistics ----------------
+
+def test_kept_fraction_tracks_fidelity_and_norm():
+    """Method (path-integral view) and Supplement (slicing): summing a fraction
+    f of the slices gives fidelity ~ f and squared norm ~ f (Results, norm vs
+    summed fraction).  Bands measured on this seeded circuit."""
+    c = ci.make_grid_circuit(4, 4, 12, seed=21)
+    se = [(g, l) for (g, l, k, v) in ci.mid_circuit_cut_edges(c, 2)]      # k = 4
+    psi = O.statevector(c)
+    for kept in (2, 4, 8):
+        hat = O.sliced_statevector(c, se, slice_range=(0, kept))
+        f = kept / 16
+        F = O.fidelity(psi, hat)
+        nrm = np.vdot(hat, hat).real
+        assert 0.6 * f < F < 1.5 * f, (kept, F)
+        assert 0.6 * f < nrm < 1.5 * f, (kept, nrm)
+        assert math.isclose(O.f_estimate(0, kept, 16), f)
+
+
+def test_porter_thomas_and_exact_sampling_xeb():
+    """Results (Porter-Thomas histogram) and the validation section's XEB: the
+    exact state of a deep random circuit is close to Porter-Thomas and exact
+    one-group sampling has E[XEB] = 2^n sum P^2 - 1 ~ 1."""
+    c = ci.make_grid_circuit(4, 4, 14, seed=31)
+    n = 16
+    psi = O.statevector(c)
+    P = np.abs(psi) ** 2
+    assert O.porter_thomas_ks(P * 2 ** n) < 0.03
+    H = psi.reshape(1, -1)                              # one group, all qubits open
+    samples = O.sample_groups(H, np.zeros(1, np.uint64), list(range(n)), n, 20000, 0.0, 1.0, seed=7)
+    x = 2 ** n * P[samples.astype(np.int64)]
+    expect = O.expected_group_sampler_xeb(H, P.reshape(1, -1), n)
+    assert abs(expect - ((2 ** n) * (P * P).sum() - 1)) < 1e-12
+    assert abs(x.mean() - 1 - expect) < 3 * x.std() / math.sqrt(x.size)
+    assert 0.8 < expect < 1.2
+
+
+def test_group_sampler_xeb_dirichlet_closed_form():
+    """For Porter-Thomas weights, one exact draw per group of size l has
+    E[XEB] = (l - 1)/(l + 1) (Dirichlet(1,...,1) weights, Gamma(l) sum)."""
+    L, h = 20000, 4
+    l = 1 << h
+    H = ci.synthetic_head(L, h, seed=5)
+    n = 30
+    P = np.abs(H) ** 2 / 2 ** n                        # ideal = approximate, mean 2^-n
+    s = O.sample_groups(H, np.arange(L, dtype=np.uint64) << np.uint64(h), list(range(h)), n, L, 0.0, 1.0,
+                        seed=11)
+    mu = (s & np.uint64(l - 1)).astype(np.int64)
+    x = 2 ** n * P[np.arange(L), mu]
+    closed = (l - 1) / (l + 1)
+    assert abs(x.mean() - 1 - closed) < 3 * x.std() / math.sqrt(L) + 0.01
+
+
+def test_sampler_categorical_frequencies_and_mixing():
+    H = ci.synthetic_head(1, 3, seed=2)
+    w = np.abs(H[0]) ** 2
+    w /= w.sum()
+    n = 20000
+    s = O.sample_groups(H, np.zeros(1, np.uint64), [0, 1, 2], 3, n, 0.0, 1.0, seed=3)
+    cnt = np.bincount(s.astype(np.int64), minlength=8)
+    chi2 = ((cnt - n * w) ** 2 / (n * w)).sum()
+    assert chi2 < 24.3                                 # chi2(7) 99.9% quantile
+    # mixing: fraction 1 - f/F_head of draws replaced by uniform 20-qubit strings
+    s = O.sample_groups(H, np.zeros(1, np.uint64), [0, 1, 2], 20, n, 0.25, 1.0, seed=4)
+    frac_high = np.mean(s >= 8)                        # exact draws never set bits >= 3
+    assert abs(frac_high - 0.75 * (1 - 8 / 2 ** 20)) < 0.02
+
+
+def test_philox_words_uniform():
+    words = []
+    for i in range(4000):
+        words.extend(O.philox4x32_10((i, 0, 0, 0), (123, 456)))
+    w = np.array(words, dtype=np.uint64)
+    bits = np.unpackbits(w.astype(">u4").view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.005
+    hist = np.bincount((w >> np.uint64(28)).astype(np.int64), minlength=16)
+    e = w.size / 16
+    assert ((hist - e) ** 2 / e).sum() < 37.7          # chi2(15) 99.9%
+    # different keys / counters give different streams
+    assert O.philox4x32_10((0, 0, 0, 0), (0, 0)) != O.philox4x32_10((0, 0, 0, 0), (1, 0))
+    assert O.philox4x32_10((0, 0, 0, 0), (0, 0)) != O.philox4x32_10((1, 0, 0, 0), (0, 0))
+
+
+def test_normalisation_mean_one():
+    H = ci.synthetic_head(64, 6, seed=1)
+    p = O.normalised_probabilities(H, 30)
+    assert abs(p.mean() * 2 ** 30 - 1.0) < 1e-12
+
+
+# ---------------- the paper's printed numbers ----------------
+
+def test_paper_efficiency_numbers():
+    e = GOLDEN["efficiency"]
+    P = e["v100_fp32_peak_flops"]
+    assert abs(O.gpu_efficiency(e["Tc_head_branch_merged"], P, e["t_head_s"]) - e["eff_head"]) < 0.005
+    assert abs(O.gpu_efficiency(e["Tc_tail_branch_merged"], P, e["t_tail_s"]) - e["eff_tail"]) < 0.005
+    tot = e["Tc_head_branch_merged"] + e["Tc_tail_branch_merged"]
+    assert abs(O.gpu_efficiency(tot, P, e["t_subtask_s"]) - e["eff_overall"]) < 0.005
+
+
+def test_paper_complexity_and_walltime():
+    c = GOLDEN["complexity"]
+    tot = 2 ** c["subtasks_log2"] * (c["Tc_head"] + c["Tc_tail"])
+    assert abs(tot / c["Tc_overall"] - 1) < 0.001
+    assert abs(8 * c["Tc_overall"] / c["flops_overall"] - 1) < 0.01
+    w = GOLDEN["wall_time"]
+    hours = 2 ** c["subtasks_log2"] * GOLDEN["efficiency"]["t_subtask_s"] / w["gpus"] / 3600
+    assert abs(hours - w["hours"]) < 0.5
+
+
+def test_paper_fidelity_estimate():
+    f = GOLDEN["fidelity"]
+    F = 2.0 ** -f["K_broken_edges"] * f["rank_one_factor"]
+    assert abs(F - f["F_estimate"]) < 0.00005
+    # the estimate's structure: 2^-K, kept fraction, companion factors
+    th = [math.pi / 2 - 0.1] * 3
+    assert math.isclose(O.f_estimate(8, 1, 1, th), 2 ** -8 * ((math.sin(th[0]) ** 2 + 1) / 2) ** 3)
+    # companions at theta = pi/2 cost nothing (cos^2 theta = 0: the cut is exact)
+    assert O.companion_factor(math.pi / 2) == 1.0
+
+
+def test_paper_sparse_state_example_amplitudes():
+    """Supplement worked example: the sparse state {111, 010, 000} of a 3-qubit
+    circuit is the 3 requested amplitudes (L = 3 groups, no open qubit)."""
+    ex = GOLDEN["sparse_state_example"]
+    c = ci.make_random_2q_circuit(3, 2, seed=1)
+    tails = np.array([int(t[::-1], 2) for t in ex["targets"]], dtype=np.uint64)   # char i = qubit i
+    psi = O.statevector(c)
+    H = O.sparse_state_from_vector(psi, [], tails)
+    H2 = O.network_amplitudes(c, [], tails)
+    assert H.shape == (3, 1)
+    assert np.abs(H - H2).max() < 1e-14
+    for g, t in enumerate(tails):
+        assert H[g, 0] == psi[int(t)]
