@@ -1,0 +1,172 @@
+/*
+ * tn_gb300.h -- C ABI of the sliced sparse-state tensor-network contraction
+ * (Pan, Chen, Zhang, "Solving the Sampling Problem of the Sycamore Quantum
+ * Circuits", arXiv:2111.03011) on one GB300 GPU.
+ *
+ * What it computes.  A quantum circuit U is a tensor network (Method section):
+ * |0> vectors on the initial boundary, a matrix per single-qubit gate and a
+ * four-way tensor per two-qubit gate.  The final boundary is the sparse state
+ * (Supplement, "The sparse-state method"): L groups, group g fixing every
+ * non-open ("tail") qubit to the bits of tails[g] and leaving the h open qubits
+ * free, so the result is the head tensor H[g][mu] of L x 2^h amplitudes,
+ *     H[g][mu] = sum_{s in kept slices} <tails[g] (+) mu| U_s |0...0>,
+ * where U_s is the network with the k sliced edges fixed to the bits of the
+ * slice id s (Supplement, slicing).  Summing all 2^k slices gives the exact
+ * amplitudes; summing a fraction f of them gives a state of fidelity ~ f
+ * (Method, edge breaking; Supplement, slicing).  Samples are then drawn one
+ * per group (Method, last paragraph).
+ *
+ * Conventions (the paper fixes none of these):
+ *   - qubit q <-> bit q of a uint64 bitstring (LSB = qubit 0);
+ *   - open index mu = sum_j bit(open_qubits[j]) << j;
+ *   - group g = position of its tail in tails[]; tail bits on open qubits are ignored;
+ *   - slice id s in [0, 2^k): sliced edge j (in the order given) takes (s >> j) & 1;
+ *   - gate matrices: row = output, column = input; two-qubit basis |q0 q1>, q0 high bit.
+ *
+ * Ownership.  The library owns plans and heads.  A head may wrap a caller-owned
+ * device buffer, which must outlive the head.  A plan must outlive its heads.
+ * Errors.  Every call returns TN_OK (0) or a TN_ERR_* code and never aborts;
+ * tn_last_error() gives a message for the calling thread's last failure.
+ * Streams.  `stream` arguments are cudaStream_t values (NULL = legacy default
+ * stream).  Calls that return host-visible results synchronise that stream.
+ */
+#ifndef TN_GB300_H
+#define TN_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TN_OK = 0,
+  TN_ERR_INVALID = 1,       /* bad argument: qubit, edge, range, order, size */
+  TN_ERR_OOM = 2,           /* size cap exceeded or device allocation failed */
+  TN_ERR_NOT_IN_STATE = 3,  /* a requested bitstring's tail is not in tails[] */
+  TN_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+  TN_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+  TN_ERR_UNSUPPORTED = 6    /* valid request this build does not implement */
+};
+
+enum { TN_EDGE_SLICE = 0, TN_EDGE_PIN = 1, TN_EDGE_COMPANION = 2 };
+enum { TN_C64 = 0, TN_C128 = 1 };
+enum { TN_GEMM_AUTO = 0, TN_GEMM_TC_3XTF32 = 1, TN_GEMM_SIMT_FP32 = 2 };
+
+/* One gate, in time order.  arity 1: re/im[0..3] hold the 2x2 matrix
+ * (row-major, row = output); arity 2: re/im[0..15] hold the 4x4 matrix. */
+typedef struct { int arity; int q0, q1; double re[16], im[16]; } tn_gate;
+typedef struct { int n_qubits; int n_gates; const tn_gate* gates; } tn_circuit;
+
+/* The sparse state: L = n_tails groups x 2^n_open members (Supplement, sparse
+ * state; Results: 6 open qubits, 2^20 groups).  n_qubits <= 64, n_open <= 30. */
+typedef struct {
+  const int* open_qubits; int n_open;
+  const uint64_t* tails; int64_t n_tails;
+} tn_open_spec;
+
+/* A cut edge: the wire entering gate `gate` on its q0 (leg 0) or q1 (leg 1).
+ * SLICE: enumerated by the slice id (Supplement, slicing).
+ * PIN:   fixed at `value` for every slice -- an edge broken by inserting
+ *        E = (1,0)x(1,0) (value 0), each halving the fidelity estimate
+ *        (Method, edge breaking); both inputs of one fSim pinned drill a hole.
+ * COMPANION: rank-one companion cut (Method case (ii)); not implemented, rejected
+ *        with TN_ERR_UNSUPPORTED. */
+typedef struct { int gate; int leg; int kind; int value; } tn_edge;
+typedef struct { int64_t begin, end; } tn_range;
+
+typedef struct {
+  double max_log2_elements;   /* cap on every intermediate, log2 complex64 elements (0: 28) */
+  int    gemm;                /* TN_GEMM_*: GEMM-step engine (0: auto = tensor cores)         */
+  int    host_only;           /* 1: plan on the host only (no device upload; inspect only)   */
+  int    order_trials;        /* randomised greedy order restarts (0: 64)                   */
+  uint64_t order_seed;        /* seed of those restarts                                      */
+  int    max_host_absorb_log2;/* size cap of host-side absorption of order<=2 tensors (0: 12)*/
+  int    small_max_bits;      /* contractions with <= this many contracted and new legs use the
+                                 streaming small-operand kernel (0: 4; -1: none, all GEMM steps) */
+} tn_plan_opts;
+
+typedef struct tn_plan tn_plan_t;
+typedef struct tn_head tn_head_t;
+
+/* Per-plan figures for one slice. */
+typedef struct {
+  int     n_qubits, n_open;
+  int64_t n_tails;            /* L */
+  int64_t n_patterns;         /* distinct tails (rows of the final pattern axis) */
+  int     n_sliced;           /* k */
+  int     n_pinned;           /* PIN edges (each halves F_est) */
+  int     n_leaves;           /* tensors left after host simplification */
+  int     n_contractions;     /* pairwise contractions per slice */
+  int     n_launches;         /* kernel launches per slice (steps incl. permutes/prep + accumulate) */
+  double  tc_macs;            /* T_c: complex multiply-adds per slice (algorithmic) */
+  double  alg_bytes;          /* algorithmic HBM bytes per slice (each operand read once, result written once) */
+  double  max_log2_elements;  /* largest intermediate */
+  int64_t workspace_bytes;    /* device arena of one slice */
+  int     n_gemm_tc, n_gemm_simt, n_small, n_permute;  /* step counts by kernel kind */
+} tn_plan_stats;
+
+/* Plan the contraction (host).  `order`: n_pairs pairs (i, j) of leaf ids, the
+ * result of contracting i and j stored at i (the convention of the paper's
+ * contraction-order listing); NULL lets the greedy planner choose.  Leaf ids are
+ * the tensors left after host simplification, see tn_plan_order().  Unless
+ * opts->host_only, uploads leaves and step tables to the current device
+ * (synchronous).  Errors: TN_ERR_INVALID for a bad circuit, qubit, edge or order;
+ * TN_ERR_OOM if no order fits the cap. */
+int tn_plan(const tn_circuit* circuit, const tn_open_spec* open_spec,
+            const tn_edge* sliced_edges, int n_edges,
+            const int32_t* order, int64_t n_pairs,
+            const tn_plan_opts* opts, tn_plan_t** out);
+void tn_plan_free(tn_plan_t* plan);
+int  tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* out);
+/* Copies up to `cap` pairs of the order used into pairs[2*i], pairs[2*i+1];
+ * *n_pairs receives the full count. */
+int  tn_plan_order(const tn_plan_t* plan, int32_t* pairs, int64_t cap, int64_t* n_pairs);
+/* JSON description of leaves and steps (for tests and tooling); the string is
+ * owned by the plan and valid until the next call on it. */
+const char* tn_plan_describe(tn_plan_t* plan, int with_data);
+
+/* Head tensor H[L][2^h] complex128 (row g = group).  dev_c128 = NULL: the head
+ * allocates it; else it wraps the caller's device buffer of L*2^h complex128.
+ * Zeroed on creation (synchronous). */
+int  tn_head_create(tn_plan_t* plan, void* dev_c128, tn_head_t** out);
+void tn_head_free(tn_head_t* head);
+void* tn_head_data(tn_head_t* head);  /* device pointer of H */
+/* F_est = 2^-n_pinned * slices_done / 2^k (fidelity-estimate equation). */
+int  tn_head_fidelity(const tn_head_t* head, double* f_est, int64_t* slices_done);
+/* Override F_est for a head filled by the caller (not by contraction). */
+int  tn_head_set_fidelity(tn_head_t* head, double f_est);
+
+/* Contract slices [begin, end) and add them into the head (FP64).  Asynchronous
+ * on `stream`.  A slice already accumulated into this head is rejected
+ * (TN_ERR_INVALID) -- ranges are additive and may come from several calls. */
+int  tn_contract_slices(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, void* stream);
+
+/* out[i] = H[g(s_i)][mu(s_i)] for n bitstrings.  `bitstrings` and `out` may be
+ * host or device pointers; dtype TN_C64 or TN_C128.  Synchronises `stream`.
+ * TN_ERR_NOT_IN_STATE if a bitstring's tail is not a group (the first such
+ * index is in tn_last_error()); `out` then holds 0 for those entries. */
+int  tn_amplitudes(tn_head_t* head, const uint64_t* bitstrings, int64_t n,
+                   void* out, int dtype, void* stream);
+
+/* Draw n bitstrings: sample i from group i mod L, with probability
+ * |H[g][mu]|^2 / sum_nu |H[g][nu]|^2 (exact categorical draw, the stationary law
+ * of the paper's Metropolis chain), replaced with probability
+ * 1 - target_fidelity / F_head by a uniform n_qubits-bit string (the noisy-state
+ * mixture of the Supplement's slicing section).  target_fidelity <= 0 or
+ * >= F_head: no mixing.  Random numbers: Philox-4x32-10 keyed by `seed`.
+ * out_bitstrings may be host or device memory; synchronises `stream`. */
+int  tn_sample(tn_head_t* head, int64_t n, double target_fidelity, uint64_t seed,
+               uint64_t* out_bitstrings, void* stream);
+
+/* Squared norm N = sum |H|^2 (FP64) and, if group_norms != NULL, the L
+ * per-group sums (host memory).  Synchronises `stream`. */
+int  tn_head_norm(tn_head_t* head, double* norm, double* group_norms, void* stream);
+
+const char* tn_last_error(void);
+const char* tn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_GB300_H */

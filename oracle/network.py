@@ -13,8 +13,9 @@ group, which is the plain definition the sparse-state contraction has to
 reproduce.  A slice range sums over the sliced edges' values, each slice a
 separate contraction.
 
-Contraction: repeated pairwise ``numpy.tensordot`` over shared labels, the pair
-picked greedily (smallest size(C) - size(A) - size(B)).
+Contraction: repeated pairwise ``numpy.tensordot`` over shared labels, in an
+order chosen on the label lists alone by randomised greedy restarts (smallest
+largest intermediate wins).
 """
 from __future__ import annotations
 
@@ -76,39 +77,93 @@ def _build(circ, cuts, open_qubits, tail):
     return net, out_labels
 
 
-def _contract(net, out_labels):
-    T = net.tensors
-    out_set = set(out_labels)
-    while len(T) > 1:
+def _find_order(shapes, out_set, trials=24, seed=0):
+    """Pairwise order for tensors given only their label lists: randomised
+    greedy restarts (score size(C) - size(A) - size(B) plus noise), keeping the
+    order with the smallest largest intermediate, then the fewest flops."""
+    rng = np.random.default_rng(seed)
+    best = None
+    for trial in range(trials):
+        T = {i: list(l) for i, l in shapes.items()}
+        nxt = max(T) + 1 if T else 0
+        order, mx, flops = [], 0, 0.0
+        tau = 0.0 if trial == 0 else rng.uniform(0.05, 1.0)
+        while len(T) > 1:
+            where = {}
+            for tid, labs in T.items():
+                for l in labs:
+                    where.setdefault(l, []).append(tid)
+            cand = set()
+            for l, tids in where.items():
+                if len(tids) == 2:
+                    cand.add((min(tids), max(tids)))
+            if cand:
+                keys = []
+                for (a, b) in cand:
+                    la, lb = T[a], T[b]
+                    sh = set(la) & set(lb)
+                    lc = len(la) + len(lb) - 2 * len(sh)
+                    sc = 2.0 ** lc - 2.0 ** len(la) - 2.0 ** len(lb)
+                    k = np.sign(sc) * np.log2(1 + abs(sc))
+                    if tau:
+                        k -= tau * np.log(-np.log(rng.uniform(1e-12, 1)))
+                    keys.append((k, a, b))
+                _, a, b = min(keys)
+            else:
+                ids = sorted(T, key=lambda t: len(T[t]))
+                a, b = ids[0], ids[1]
+            la, lb = T.pop(a), T.pop(b)
+            sh = [l for l in la if l in lb and l not in out_set]
+            lc = [l for l in la if l not in sh] + [l for l in lb if l not in sh]
+            mx = max(mx, len(lc))
+            flops += 2.0 ** (len(la) + len(lb) - len(sh))
+            T[nxt] = lc
+            order.append((a, b, nxt))
+            nxt += 1
+        key = (mx, flops)
+        if best is None or key < best[0]:
+            best = (key, order)
+    return best[1]
+
+
+def _pairwise(A, la, B, lb, out_set):
+    shared = [l for l in la if l in lb and l not in out_set]
+    C = np.tensordot(A, B, axes=([la.index(l) for l in shared], [lb.index(l) for l in shared]))
+    return C, [l for l in la if l not in shared] + [l for l in lb if l not in shared]
+
+
+def _absorb_small(T, out_set):
+    """Contract every tensor with at most two labels into a neighbour (exact)."""
+    changed = True
+    while changed and len(T) > 1:
+        changed = False
         where = {}
         for tid, (_, labs) in T.items():
             for l in labs:
                 where.setdefault(l, []).append(tid)
-        best = None
-        for l, tids in where.items():
-            if len(tids) != 2:
+        for tid in list(T):
+            if tid not in T or len(T[tid][1]) > 2:
                 continue
-            a, b = tids
-            la, lb = T[a][1], T[b][1]
-            shared = set(la) & set(lb)
-            size_c = 2 ** (len(la) + len(lb) - 2 * len(shared))
-            score = size_c - T[a][0].size - T[b][0].size
-            key = (score, size_c, min(a, b), max(a, b))
-            if best is None or key < best[0]:
-                best = (key, a, b)
-        if best is None:                              # disconnected: outer product of two smallest
-            ids = sorted(T, key=lambda t: T[t][0].size)
-            a, b = ids[0], ids[1]
-        else:
-            a, b = best[1], best[2]
+            nbrs = [o for l in T[tid][1] for o in where.get(l, []) if o != tid and o in T]
+            if not nbrs:
+                continue
+            o = min(nbrs, key=lambda x: T[x][0].size)
+            A, la = T.pop(o)
+            B, lb = T.pop(tid)
+            T[o] = _pairwise(A, la, B, lb, out_set)
+            changed = True
+            break
+
+
+def _contract(net, out_labels):
+    T = net.tensors
+    out_set = set(out_labels)
+    _absorb_small(T, out_set)
+    order = _find_order({i: l for i, (_, l) in T.items()}, out_set)
+    for (a, b, c) in order:
         A, la = T.pop(a)
         B, lb = T.pop(b)
-        shared = [l for l in la if l in lb and l not in out_set]
-        ia = [la.index(l) for l in shared]
-        ib = [lb.index(l) for l in shared]
-        C = np.tensordot(A, B, axes=(ia, ib))
-        lc = [l for l in la if l not in shared] + [l for l in lb if l not in shared]
-        net.add(C, lc)
+        T[c] = _pairwise(A, la, B, lb, out_set)
     (arr, labs), = T.values()
     return arr, labs
 

@@ -1,0 +1,545 @@
+// C ABI: plans, heads, slice contraction, amplitudes, sampling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "planner.h"
+#include "tn_gb300.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(x)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (x);                                                                    \
+    if (e_ != cudaSuccess) return fail(TN_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct tn_plan {
+  tn::Plan P;
+  bool on_device = false;
+  int device = -1;
+  float2* d_leaves = nullptr;
+  uint32_t* d_meta = nullptr;
+  char* d_arena = nullptr;
+  uint64_t* d_keys = nullptr;      // sorted masked tails
+  uint32_t* d_key_groups = nullptr;
+  uint64_t* d_tails = nullptr;     // tails in group order
+  int* d_open = nullptr;
+  unsigned int* d_status = nullptr;
+  int64_t n_keys = 0;
+};
+
+struct tn_head {
+  tn_plan_t* plan = nullptr;
+  double2* H = nullptr;
+  bool owns = false;
+  std::map<int64_t, int64_t> done;   // begin -> end of accumulated slice ranges
+  int64_t slices_done = 0;
+  bool f_override = false;
+  double f_value = 0.0;
+  // scratch
+  double* d_Z = nullptr;
+  double* d_N = nullptr;
+  unsigned long long* d_status = nullptr;
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+static const char* kVersion = "tn_gb300 0.1 (sm_103a)";
+
+extern "C" const char* tn_last_error(void) { return g_err.c_str(); }
+extern "C" const char* tn_version(void) { return kVersion; }
+
+static void plan_release(tn_plan_t* p) {
+  if (!p) return;
+  if (p->on_device) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (p->device >= 0) cudaSetDevice(p->device);
+    cudaFree(p->d_leaves);
+    cudaFree(p->d_meta);
+    cudaFree(p->d_arena);
+    cudaFree(p->d_keys);
+    cudaFree(p->d_key_groups);
+    cudaFree(p->d_tails);
+    cudaFree(p->d_open);
+    cudaFree(p->d_status);
+    if (cur >= 0) cudaSetDevice(cur);
+  }
+  delete p;
+}
+
+extern "C" void tn_plan_free(tn_plan_t* plan) { plan_release(plan); }
+
+static int plan_upload(tn_plan_t* p) {
+  tn::Plan& P = p->P;
+  CUDA_TRY(cudaGetDevice(&p->device));
+  std::vector<float2> leaves(P.leaf_arena.size());
+  for (size_t i = 0; i < leaves.size(); ++i)
+    leaves[i] = make_float2((float)P.leaf_arena[i].real(), (float)P.leaf_arena[i].imag());
+  p->on_device = true;
+  CUDA_TRY(cudaMalloc(&p->d_leaves, std::max<size_t>(leaves.size(), 1) * sizeof(float2)));
+  if (!leaves.empty())
+    CUDA_TRY(cudaMemcpy(p->d_leaves, leaves.data(), leaves.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMalloc(&p->d_meta, std::max<size_t>(P.meta.size(), 1) * sizeof(uint32_t)));
+  if (!P.meta.empty())
+    CUDA_TRY(cudaMemcpy(p->d_meta, P.meta.data(), P.meta.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  if (P.workspace_bytes > 0) {
+    cudaError_t e = cudaMalloc(&p->d_arena, (size_t)P.workspace_bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TN_ERR_OOM, "workspace of " + std::to_string(P.workspace_bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+  }
+  // amplitude lookup table
+  const size_t L = P.tails_raw.size();
+  std::vector<std::pair<uint64_t, uint32_t>> kv(L);
+  for (size_t g = 0; g < L; ++g) kv[g] = {P.tails_raw[g] & P.tail_mask, (uint32_t)g};
+  std::sort(kv.begin(), kv.end());
+  std::vector<uint64_t> keys(L);
+  std::vector<uint32_t> grp(L);
+  for (size_t i = 0; i < L; ++i) { keys[i] = kv[i].first; grp[i] = kv[i].second; }
+  p->n_keys = (int64_t)L;
+  CUDA_TRY(cudaMalloc(&p->d_keys, L * sizeof(uint64_t)));
+  CUDA_TRY(cudaMalloc(&p->d_key_groups, L * sizeof(uint32_t)));
+  CUDA_TRY(cudaMalloc(&p->d_tails, L * sizeof(uint64_t)));
+  CUDA_TRY(cudaMemcpy(p->d_keys, keys.data(), L * sizeof(uint64_t), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(p->d_key_groups, grp.data(), L * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(p->d_tails, P.tails_raw.data(), L * sizeof(uint64_t), cudaMemcpyHostToDevice));
+  const size_t h = P.open_qubits.size();
+  CUDA_TRY(cudaMalloc(&p->d_open, std::max<size_t>(h, 1) * sizeof(int)));
+  if (h) CUDA_TRY(cudaMemcpy(p->d_open, P.open_qubits.data(), h * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMalloc(&p->d_status, sizeof(unsigned int)));
+  CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(unsigned int)));
+  return TN_OK;
+}
+
+extern "C" int tn_plan(const tn_circuit* circuit, const tn_open_spec* open_spec, const tn_edge* sliced_edges,
+                       int n_edges, const int32_t* order, int64_t n_pairs, const tn_plan_opts* opts,
+                       tn_plan_t** out) {
+  if (!out) return fail(TN_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!circuit || !open_spec) return fail(TN_ERR_INVALID, "circuit or open_spec is NULL");
+  if (circuit->n_gates > 0 && !circuit->gates) return fail(TN_ERR_INVALID, "gates is NULL");
+  if (open_spec->n_open < 0 || (open_spec->n_open > 0 && !open_spec->open_qubits))
+    return fail(TN_ERR_INVALID, "bad open qubit list");
+  if (open_spec->n_tails < 1 || !open_spec->tails) return fail(TN_ERR_INVALID, "need at least one tail");
+  if (n_edges < 0 || (n_edges > 0 && !sliced_edges)) return fail(TN_ERR_INVALID, "bad edge list");
+  if (order && n_pairs < 0) return fail(TN_ERR_INVALID, "n_pairs < 0");
+  tn::PlanInput in;
+  in.n_qubits = circuit->n_qubits;
+  in.n_gates = circuit->n_gates;
+  std::vector<int> ar(circuit->n_gates), q0(circuit->n_gates), q1(circuit->n_gates);
+  std::vector<tn::cd> mats((size_t)circuit->n_gates * 16);
+  for (int g = 0; g < circuit->n_gates; ++g) {
+    const tn_gate& G = circuit->gates[g];
+    ar[g] = G.arity;
+    q0[g] = G.q0;
+    q1[g] = G.q1;
+    for (int e = 0; e < 16; ++e) mats[(size_t)g * 16 + e] = tn::cd(G.re[e], G.im[e]);
+  }
+  in.arity = ar.data();
+  in.q0 = q0.data();
+  in.q1 = q1.data();
+  in.mats = mats.data();
+  in.open_qubits.assign(open_spec->open_qubits, open_spec->open_qubits + open_spec->n_open);
+  in.tails.assign(open_spec->tails, open_spec->tails + open_spec->n_tails);
+  for (int e = 0; e < n_edges; ++e)
+    in.edges.push_back({sliced_edges[e].gate, sliced_edges[e].leg, sliced_edges[e].kind, sliced_edges[e].value});
+  in.order = order;
+  in.n_pairs = order ? n_pairs : 0;
+  bool host_only = false;
+  if (opts) {
+    if (opts->max_log2_elements > 0) in.cap_log2 = opts->max_log2_elements;
+    in.gemm_engine = opts->gemm;
+    host_only = opts->host_only != 0;
+    if (opts->order_trials > 0) in.order_trials = opts->order_trials;
+    if (opts->order_seed) in.order_seed = opts->order_seed;
+    if (opts->max_host_absorb_log2 > 0) in.absorb_log2 = opts->max_host_absorb_log2;
+    if (opts->small_max_bits != 0) in.small_max_bits = opts->small_max_bits < 0 ? -1 : std::min(4, opts->small_max_bits);
+  }
+  if (in.gemm_engine < 0 || in.gemm_engine > 2) return fail(TN_ERR_INVALID, "unknown gemm engine");
+  if (in.cap_log2 > 34) return fail(TN_ERR_INVALID, "size cap above 2^34 elements");
+  tn_plan_t* p = new tn_plan_t();
+  std::string err;
+  int rc = tn::build_plan(in, p->P, err);
+  if (rc) {
+    delete p;
+    return fail(rc, err);
+  }
+  if (!host_only) {
+    rc = plan_upload(p);
+    if (rc) {
+      plan_release(p);
+      return rc;
+    }
+  }
+  *out = p;
+  return TN_OK;
+}
+
+extern "C" int tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* s) {
+  if (!plan || !s) return fail(TN_ERR_INVALID, "NULL argument");
+  const tn::Plan& P = plan->P;
+  std::memset(s, 0, sizeof(*s));
+  s->n_qubits = P.n_qubits;
+  s->n_open = (int)P.open_qubits.size();
+  s->n_tails = (int64_t)P.tails_raw.size();
+  s->n_patterns = P.n_patterns_final;
+  s->n_sliced = P.n_sliced;
+  s->n_pinned = P.n_pinned;
+  s->n_leaves = (int)P.leaves.size();
+  s->n_contractions = P.n_contractions;
+  s->n_launches = (int)P.steps.size() + 1;
+  s->tc_macs = P.tc_macs;
+  s->alg_bytes = P.alg_bytes;
+  s->max_log2_elements = P.max_log2;
+  s->workspace_bytes = P.workspace_bytes;
+  for (auto& st : P.steps) {
+    if (st.kind == tn::ST_GEMM_TC) ++s->n_gemm_tc;
+    if (st.kind == tn::ST_GEMM_SIMT) ++s->n_gemm_simt;
+    if (st.kind == tn::ST_SMALL) ++s->n_small;
+    if (st.kind == tn::ST_PERMUTE) ++s->n_permute;
+  }
+  return TN_OK;
+}
+
+extern "C" int tn_plan_order(const tn_plan_t* plan, int32_t* pairs, int64_t cap, int64_t* n_pairs) {
+  if (!plan || !n_pairs) return fail(TN_ERR_INVALID, "NULL argument");
+  const auto& o = plan->P.order;
+  *n_pairs = (int64_t)o.size();
+  for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)o.size()); ++i) {
+    pairs[2 * i] = o[i].first;
+    pairs[2 * i + 1] = o[i].second;
+  }
+  return TN_OK;
+}
+
+extern "C" const char* tn_plan_describe(tn_plan_t* plan, int with_data) {
+  if (!plan) return "";
+  plan->P.describe_cache = tn::describe_plan(plan->P, with_data != 0);
+  return plan->P.describe_cache.c_str();
+}
+
+// ----------------------------------------------------------------- heads
+
+extern "C" int tn_head_create(tn_plan_t* plan, void* dev_c128, tn_head_t** out) {
+  if (!plan || !out) return fail(TN_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  if (!plan->on_device) return fail(TN_ERR_INVALID, "plan was made host_only");
+  tn_head* h = new tn_head();
+  h->plan = plan;
+  const int64_t L = (int64_t)plan->P.tails_raw.size();
+  const int64_t elems = L << plan->P.open_qubits.size();
+  if (dev_c128) {
+    h->H = (double2*)dev_c128;
+  } else {
+    cudaError_t e = cudaMalloc(&h->H, (size_t)elems * sizeof(double2));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return fail(TN_ERR_OOM, std::string("head allocation: ") + cudaGetErrorString(e));
+    }
+    h->owns = true;
+  }
+  cudaError_t e1 = cudaMemset(h->H, 0, (size_t)elems * sizeof(double2));
+  cudaError_t e2 = cudaMalloc(&h->d_Z, (size_t)std::max<int64_t>(L, 1) * sizeof(double));
+  cudaError_t e3 = cudaMalloc(&h->d_N, sizeof(double));
+  cudaError_t e4 = cudaMalloc(&h->d_status, sizeof(unsigned long long));
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+    cudaGetLastError();
+    tn_head_free(h);
+    return fail(TN_ERR_CUDA, "head set-up failed");
+  }
+  *out = h;
+  return TN_OK;
+}
+
+extern "C" void tn_head_free(tn_head_t* h) {
+  if (!h) return;
+  if (h->owns) cudaFree(h->H);
+  cudaFree(h->d_Z);
+  cudaFree(h->d_N);
+  cudaFree(h->d_status);
+  cudaFree(h->d_stage);
+  delete h;
+}
+
+extern "C" void* tn_head_data(tn_head_t* h) { return h ? (void*)h->H : nullptr; }
+
+extern "C" int tn_head_fidelity(const tn_head_t* h, double* f_est, int64_t* slices_done) {
+  if (!h) return fail(TN_ERR_INVALID, "NULL head");
+  const tn::Plan& P = h->plan->P;
+  double f = h->f_override ? h->f_value
+                           : std::ldexp((double)h->slices_done, -P.n_sliced) * std::ldexp(1.0, -P.n_pinned);
+  if (f_est) *f_est = f;
+  if (slices_done) *slices_done = h->slices_done;
+  return TN_OK;
+}
+
+extern "C" int tn_head_set_fidelity(tn_head_t* h, double f) {
+  if (!h || !(f >= 0.0) || f > 1.0) return fail(TN_ERR_INVALID, "bad head or fidelity");
+  h->f_override = true;
+  h->f_value = f;
+  return TN_OK;
+}
+
+// -------------------------------------------------------- slice execution
+
+static inline const float2* ref_ptr(const tn_plan_t* p, const tn::Ref& r, int64_t s) {
+  if (r.kind == 0) {
+    const tn::LeafInfo& li = p->P.leaf_info[r.id];
+    int64_t v = 0;
+    for (size_t t = 0; t < li.var_slice_bits.size(); ++t) v |= ((s >> li.var_slice_bits[t]) & 1) << t;
+    return p->d_leaves + li.off + v * li.size;
+  }
+  return (const float2*)(p->d_arena + p->P.bufs[r.id].off);
+}
+
+static inline float2* buf_ptr(const tn_plan_t* p, const tn::Ref& r) {
+  return (float2*)(p->d_arena + p->P.bufs[r.id].off);
+}
+
+static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st) {
+  const tn::Plan& P = p->P;
+  for (const tn::Step& x : P.steps) {
+    cudaError_t e = cudaSuccess;
+    switch (x.kind) {
+      case tn::ST_SMALL: {
+        tn::SmallParams sp;
+        sp.A = ref_ptr(p, x.a, s);
+        sp.B = ref_ptr(p, x.b, s);
+        sp.C = buf_ptr(p, x.c);
+        sp.a_pstride = 1LL << x.rA;
+        sp.b_pstride = 1LL << x.rB;
+        sp.c_pstride = 1LL << x.rC;
+        sp.M = 1LL << (x.rA - x.nk);
+        sp.PC = x.PC;
+        sp.rA = x.rA;
+        sp.nk = x.nk;
+        sp.nn = x.nn;
+        for (int j = 0; j < 4; ++j) sp.kpos[j] = x.kposA[j];
+        std::memcpy(sp.boffK, x.boffK, sizeof(sp.boffK));
+        std::memcpy(sp.boffN, x.boffN, sizeof(sp.boffN));
+        sp.mapA = p->d_meta + x.mapA_off;
+        sp.mapB = p->d_meta + x.mapB_off;
+        sp.mapA_mode = x.mapA_mode;
+        sp.mapB_mode = x.mapB_mode;
+        e = tn::launch_small(sp, st);
+        break;
+      }
+      case tn::ST_PERMUTE: {
+        tn::PermParams pp;
+        pp.in = ref_ptr(p, x.a, s);
+        pp.out = buf_ptr(p, x.c);
+        pp.pstride = 1LL << x.rA;
+        pp.P = x.PA;
+        pp.t = x.t_bits;
+        pp.n_rest = x.n_rest;
+        std::memcpy(pp.rest_in, x.rest_in, sizeof(pp.rest_in));
+        std::memcpy(pp.rest_out, x.rest_out, sizeof(pp.rest_out));
+        pp.tab = p->d_meta + x.tab_off;
+        e = tn::launch_permute(pp, st);
+        break;
+      }
+      case tn::ST_BPREP_C:
+      case tn::ST_BPREP_TC: {
+        tn::BPrepParams bp;
+        bp.B = ref_ptr(p, x.a, s);
+        bp.out = buf_ptr(p, x.c);
+        bp.b_pstride = 1LL << x.rA;
+        bp.PB = x.PA;
+        bp.nk = x.nk;
+        bp.nn = x.nn;
+        bp.bk = p->d_meta + x.bk_off;
+        bp.bn = p->d_meta + x.bn_off;
+        e = x.kind == tn::ST_BPREP_C ? tn::launch_bprep_c(bp, st) : tn::launch_bprep_tc(bp, st);
+        break;
+      }
+      case tn::ST_GEMM_SIMT:
+      case tn::ST_GEMM_TC: {
+        tn::GemmParams gp;
+        gp.A = ref_ptr(p, x.a, s);
+        gp.B = (const void*)ref_ptr(p, x.b, s);
+        gp.C = buf_ptr(p, x.c);
+        gp.M = 1LL << x.nm;
+        gp.N = 1LL << x.nn;
+        gp.K = 1LL << x.nk;
+        gp.PA = x.PA;
+        gp.PB = x.PB;
+        gp.PC = x.PC;
+        gp.mapA = p->d_meta + x.mapA_off;
+        gp.mapB = p->d_meta + x.mapB_off;
+        gp.mapA_mode = x.mapA_mode;
+        gp.mapB_mode = x.mapB_mode;
+        e = x.kind == tn::ST_GEMM_SIMT ? tn::launch_gemm_simt(gp, st) : tn::launch_gemm_tc(gp, p->d_status, st);
+        break;
+      }
+      default:
+        return fail(TN_ERR_INVALID, "internal: unknown step kind");
+    }
+    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  }
+  tn::AccumParams ap;
+  ap.F = ref_ptr(p, P.fin.ref, s);
+  ap.H = H;
+  ap.f_pstride = 1LL << P.fin.rF;
+  ap.L = (int64_t)P.tails_raw.size();
+  ap.h = (int)P.open_qubits.size();
+  ap.pidx = p->d_meta + P.fin.pidx_off;
+  for (int j = 0; j < ap.h && j < 32; ++j) ap.open_pos[j] = P.fin.open_pos[j];
+  cudaError_t e = tn::launch_accum(ap, st);
+  if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("accumulate launch: ") + cudaGetErrorString(e));
+  return TN_OK;
+}
+
+extern "C" int tn_contract_slices(tn_plan_t* plan, tn_range r, tn_head_t* head, void* stream) {
+  if (!plan || !head) return fail(TN_ERR_INVALID, "NULL argument");
+  if (head->plan != plan) return fail(TN_ERR_INVALID, "head belongs to another plan");
+  const int64_t ns = 1LL << plan->P.n_sliced;
+  if (r.begin < 0 || r.end > ns || r.begin > r.end) return fail(TN_ERR_INVALID, "slice range outside [0, 2^k)");
+  if (r.begin == r.end) return TN_OK;
+  // reject overlap with accumulated ranges
+  auto it = head->done.upper_bound(r.begin);
+  if (it != head->done.begin()) {
+    auto pv = std::prev(it);
+    if (pv->second > r.begin) return fail(TN_ERR_INVALID, "slice range overlaps slices already accumulated");
+  }
+  if (it != head->done.end() && it->first < r.end)
+    return fail(TN_ERR_INVALID, "slice range overlaps slices already accumulated");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int64_t s = r.begin; s < r.end; ++s) {
+    int rc = run_slice(plan, s, head->H, st);
+    if (rc) return rc;
+  }
+  head->done[r.begin] = r.end;
+  head->slices_done += r.end - r.begin;
+  return TN_OK;
+}
+
+// ------------------------------------------------------ amplitudes, sampling
+
+static int ensure_stage(tn_head* h, size_t bytes) {
+  if (h->stage_bytes >= bytes) return TN_OK;
+  cudaFree(h->d_stage);
+  h->d_stage = nullptr;
+  h->stage_bytes = 0;
+  cudaError_t e = cudaMalloc(&h->d_stage, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TN_ERR_OOM, "staging buffer allocation failed");
+  }
+  h->stage_bytes = bytes;
+  return TN_OK;
+}
+
+extern "C" int tn_amplitudes(tn_head_t* h, const uint64_t* bitstrings, int64_t n, void* out, int dtype, void* stream) {
+  if (!h || (n > 0 && (!bitstrings || !out))) return fail(TN_ERR_INVALID, "NULL argument");
+  if (n < 0) return fail(TN_ERR_INVALID, "n < 0");
+  if (dtype != TN_C64 && dtype != TN_C128) return fail(TN_ERR_INVALID, "dtype must be TN_C64 or TN_C128");
+  if (n == 0) return TN_OK;
+  tn_plan_t* p = h->plan;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t esz = dtype == TN_C128 ? 16 : 8;
+  const bool dev_in = is_device_ptr(bitstrings), dev_out = is_device_ptr(out);
+  size_t need = 0;
+  if (!dev_in) need += (size_t)n * 8;
+  size_t out_off = (need + 255) / 256 * 256;
+  if (!dev_out) need = out_off + (size_t)n * esz;
+  if (need) {
+    int rc = ensure_stage(h, need);
+    if (rc) return rc;
+  }
+  const uint64_t* d_bits = bitstrings;
+  if (!dev_in) {
+    CUDA_TRY(cudaMemcpyAsync(h->d_stage, bitstrings, (size_t)n * 8, cudaMemcpyHostToDevice, st));
+    d_bits = (const uint64_t*)h->d_stage;
+  }
+  void* d_out = dev_out ? out : (void*)((char*)h->d_stage + out_off);
+  unsigned long long init = ~0ULL;
+  CUDA_TRY(cudaMemcpyAsync(h->d_status, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(tn::launch_amplitudes(h->H, (int)p->P.open_qubits.size(), p->d_keys, p->d_key_groups, p->n_keys,
+                                 p->P.tail_mask, p->d_open, d_bits, n, d_out, dtype == TN_C128 ? 1 : 0, h->d_status,
+                                 st));
+  unsigned long long status = 0;
+  CUDA_TRY(cudaMemcpyAsync(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
+  if (!dev_out) CUDA_TRY(cudaMemcpyAsync(out, d_out, (size_t)n * esz, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (status != ~0ULL)
+    return fail(TN_ERR_NOT_IN_STATE, "bitstring " + std::to_string(status) + " has a tail that is not a group");
+  return TN_OK;
+}
+
+extern "C" int tn_head_norm(tn_head_t* h, double* norm, double* group_norms, void* stream) {
+  if (!h) return fail(TN_ERR_INVALID, "NULL head");
+  tn_plan_t* p = h->plan;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t L = (int64_t)p->P.tails_raw.size();
+  CUDA_TRY(tn::launch_group_norms(h->H, L, (int)p->P.open_qubits.size(), h->d_Z, h->d_N, st));
+  if (norm) CUDA_TRY(cudaMemcpyAsync(norm, h->d_N, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (group_norms) CUDA_TRY(cudaMemcpyAsync(group_norms, h->d_Z, (size_t)L * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return TN_OK;
+}
+
+extern "C" int tn_sample(tn_head_t* h, int64_t n, double target_fidelity, uint64_t seed, uint64_t* out, void* stream) {
+  if (!h || (n > 0 && !out)) return fail(TN_ERR_INVALID, "NULL argument");
+  if (n < 0) return fail(TN_ERR_INVALID, "n < 0");
+  if (n == 0) return TN_OK;
+  tn_plan_t* p = h->plan;
+  double f_head = 0.0;
+  tn_head_fidelity(h, &f_head, nullptr);
+  if (target_fidelity > f_head && target_fidelity > 0.0 && f_head > 0.0 && target_fidelity - f_head > 1e-15)
+    return fail(TN_ERR_INVALID, "target fidelity above the head's estimated fidelity");
+  double mix = 0.0;
+  if (target_fidelity > 0.0 && f_head > 0.0 && target_fidelity < f_head) mix = 1.0 - target_fidelity / f_head;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev_out = is_device_ptr(out);
+  uint64_t* d_out = out;
+  if (!dev_out) {
+    int rc = ensure_stage(h, (size_t)n * 8);
+    if (rc) return rc;
+    d_out = (uint64_t*)h->d_stage;
+  }
+  tn::SampleParams sp;
+  sp.H = h->H;
+  sp.L = (int64_t)p->P.tails_raw.size();
+  sp.h = (int)p->P.open_qubits.size();
+  sp.tails = p->d_tails;
+  sp.open_mask = p->P.open_mask;
+  sp.open_q = p->d_open;
+  sp.n_qubits = p->P.n_qubits;
+  sp.n = n;
+  sp.mix = mix;
+  sp.seed = seed;
+  sp.out = d_out;
+  CUDA_TRY(tn::launch_sample(sp, st));
+  if (!dev_out) CUDA_TRY(cudaMemcpyAsync(out, d_out, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return TN_OK;
+}

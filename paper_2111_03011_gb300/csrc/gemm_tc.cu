@@ -1,0 +1,337 @@
+// Complex GEMM step on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// C[p][m][n] = sum_k A[mapA(p)][m][k] * B[mapB(p)][k][n] in complex64 is run as
+// one real GEMM on interleaved data (the 4M real embedding):
+//     C_r[m][j] = sum_i A_r[m][i] * Bt[j][i],  A_r = A viewed as fp32 [M][2K],
+//     Bt = the real-embedded B, [2N][2K] K-major (prepared by k_bprep_tc).
+// FP32 accuracy from TF32 tensor cores by the 3xTF32 split
+//     A_r Bt ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// hi = round-to-tf32, lo = x - hi.  The A split is done in shared memory by
+// four converter warps right after the TMA load; B arrives pre-split.
+//
+// Roles (192 threads): warps 0-3 convert A tiles and run the epilogue
+// (TMEM -> registers -> global), warp 4 issues TMA loads, warp 5 owns TMEM
+// and issues the MMAs.  One CTA computes a 128 x BN tile of C_r.  Every
+// mbarrier wait is bounded; on timeout the CTA records a status code and
+// leaves its loops instead of hanging.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "kernels.h"
+
+namespace tn {
+
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 32;                  // fp32 per 128-byte swizzle row
+constexpr int kThreads = 192;
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\tselp.u32 %0, 1, 0, P;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false (and flags the CTA) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = BN.
+template <int BN>
+__device__ __forceinline__ uint32_t idesc_tf32() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <int BN, int STAGES>
+struct Layout {
+  static constexpr int A_BYTES = BM * BK * 4;
+  static constexpr int B_BYTES = BN * BK * 4;
+  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // A hi (in place), A lo, B hi, B lo
+  static constexpr int DATA = STAGES * STAGE;
+  static constexpr int TOTAL = DATA + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+              const __grid_constant__ CUtensorMap tmBlo, float* __restrict__ C, int64_t M, int64_t N2, int64_t K2,
+              int64_t tilesM, int64_t tilesN, const uint32_t* __restrict__ mapA, const uint32_t* __restrict__ mapB,
+              int mapA_mode, int mapB_mode, unsigned int* status) {
+  using Lay = Layout<BN, STAGES>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + Lay::DATA);
+  uint64_t* full = bars;
+  uint64_t* conv = bars + STAGES;
+  uint64_t* empty = bars + 2 * STAGES;
+  uint64_t* accum = bars + 3 * STAGES;
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 3 * STAGES + 1);
+  volatile int* abort_flag = (volatile int*)(bars + 3 * STAGES + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tile = blockIdx.x;
+  const int64_t pc = tile / (tilesM * tilesN);
+  const int64_t rem = tile % (tilesM * tilesN);
+  const int64_t tm = rem / tilesN, tn_ = rem % tilesN;
+  const int64_t pa = mapA_mode == 0 ? pc : (mapA_mode == 1 ? 0 : (int64_t)mapA[pc]);
+  const int64_t pb = mapB_mode == 0 ? pc : (mapB_mode == 1 ? 0 : (int64_t)mapB[pc]);
+  const int nkb = (int)((K2 + BK - 1) / BK);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tmem_slot)),
+                 "r"(Lay::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES, r = kb / STAGES;
+        if (!mbar_wait(&empty[s], (uint32_t)((r & 1) ^ 1), abort_flag)) break;
+        uint8_t* st = smem + s * Lay::STAGE;
+        mbar_expect_tx(&full[s], (uint32_t)(Lay::A_BYTES + 2 * Lay::B_BYTES));
+        tma_load_3d(st, &tmA, &full[s], kb * BK, (int)(tm * BM), (int)pa);
+        tma_load_3d(st + 2 * Lay::A_BYTES, &tmBhi, &full[s], kb * BK, (int)(tn_ * BN), (int)pb);
+        tma_load_3d(st + 2 * Lay::A_BYTES + Lay::B_BYTES, &tmBlo, &full[s], kb * BK, (int)(tn_ * BN), (int)pb);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32<BN>();
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES, r = kb / STAGES;
+        if (!mbar_wait(&conv[s], (uint32_t)(r & 1), abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t st = smem_u32(smem + s * Lay::STAGE);
+        const uint32_t a_hi = st, a_lo = st + Lay::A_BYTES;
+        const uint32_t b_hi = st + 2 * Lay::A_BYTES, b_lo = b_hi + Lay::B_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 8; ++kk) {
+          const uint32_t o = kk * 32;  // 8 tf32 = 32 bytes along K
+          const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+          mma_tf32(tmem, sdesc(a_hi + o), sdesc(b_hi + o), idesc, acc);
+          mma_tf32(tmem, sdesc(a_hi + o), sdesc(b_lo + o), idesc, 1u);
+          mma_tf32(tmem, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accum);
+    }
+  } else {
+    // converter warps: split the A tile into tf32 hi (in place) and lo
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, r = kb / STAGES;
+      if (!mbar_wait(&full[s], (uint32_t)(r & 1), abort_flag)) break;
+      float4* a = (float4*)(smem + s * Lay::STAGE);
+      float4* lo = (float4*)(smem + s * Lay::STAGE + Lay::A_BYTES);
+#pragma unroll
+      for (int i = 0; i < Lay::A_BYTES / 16 / 128; ++i) {
+        const int idx = threadIdx.x + 128 * i;
+        float4 v = a[idx];
+        float4 h;
+        h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
+        a[idx] = h;
+        lo[idx] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&conv[s]);
+    }
+    // epilogue
+    const bool ok = mbar_wait(accum, 0u, abort_flag);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+      const int64_t row = tm * BM + warp * 32 + lane;
+      float* crow = C + (pc * M + row) * N2;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int64_t col = tn_ * BN + c0;
+        if (row < M) {
+          if (col + 16 <= N2) {
+            float4* dst = (float4*)(crow + col);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              dst[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                   __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (col + q < N2) crow[col + q] = __uint_as_float(v[q]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(status, 1u);
+  if (warp == 5) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lay::TMEM_COLS));
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+static bool encode3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
+                     uint32_t b1) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {d0 * 4, d0 * d1 * 4};
+  cuuint32_t box[3] = {b0, b1, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s) {
+  using Lay = Layout<BN, STAGES>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int64_t K2 = 2 * p.K, N2 = 2 * p.N;
+  CUtensorMap ta, tbh, tbl;
+  const float* bhi = (const float*)p.B;
+  const float* blo = bhi + p.PB * N2 * K2;
+  if (!encode3d(&ta, p.A, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BK, BM)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BK, BN)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BK, BN)) return cudaErrorInvalidValue;
+  const int64_t tilesM = (p.M + BM - 1) / BM, tilesN = (N2 + BN - 1) / BN;
+  const int64_t grid = tilesM * tilesN * p.PC;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_gemm_tc<BN, STAGES><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(ta, tbh, tbl, (float*)p.C, p.M, N2, K2, tilesM,
+                                                                      tilesN, p.mapA, p.mapB, p.mapA_mode,
+                                                                      p.mapB_mode, status);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+
+cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s) {
+  if (p.K < 2) return cudaErrorInvalidValue;  // row pitch 2K*4 bytes must be a multiple of 16
+  const int64_t N2 = 2 * p.N;
+  if (N2 <= 16) return tc::run<16, 4>(p, status, s);
+  if (N2 <= 32) return tc::run<32, 4>(p, status, s);
+  if (N2 <= 64) return tc::run<64, 4>(p, status, s);
+  if (N2 <= 128) return tc::run<128, 3>(p, status, s);
+  return tc::run<256, 2>(p, status, s);
+}
+
+}  // namespace tn

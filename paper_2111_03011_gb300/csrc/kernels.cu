@@ -1,0 +1,453 @@
+// Streaming kernels of the contraction path (HBM-bound steps), the plain
+// FP32 CUDA-core complex GEMM, slice accumulation, amplitude lookup, norms and
+// the group sampler.
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace tn {
+
+static constexpr int kSMs = 152;
+
+__device__ __forceinline__ int64_t map_p(int mode, const uint32_t* tab, int64_t p) {
+  return mode == 0 ? p : (mode == 1 ? 0 : (int64_t)__ldg(tab + p));
+}
+
+__device__ __forceinline__ float2 cmul_add(float2 acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
+}
+
+// ------------------------------------------------------------------ K8 / K3
+// Small-operand contraction (a gate-like tensor of <= 16x16 applied to a big
+// one).  Each thread owns one row m of the big operand: it gathers the 2^NK
+// elements addressed by the contracted legs, multiplies by the small operand
+// held in shared memory, and writes 2^NN outputs.  Consecutive threads touch
+// consecutive addresses, so loads and stores coalesce whatever the leg layout.
+template <int NK, int NN>
+__global__ void __launch_bounds__(256) k_small(SmallParams p) {
+  constexpr int KK = 1 << NK, NNN = 1 << NN;
+  __shared__ float2 Bs[KK][NNN];
+  int64_t offK[KK];
+#pragma unroll
+  for (int k = 0; k < KK; ++k) {
+    int64_t o = 0;
+#pragma unroll
+    for (int j = 0; j < NK; ++j)
+      if ((k >> j) & 1) o |= 1LL << p.kpos[j];
+    offK[k] = o;
+  }
+  const int64_t rowsC = p.M;  // C stride of the n index
+  for (int64_t pc = blockIdx.y; pc < p.PC; pc += gridDim.y) {
+    const int64_t pa = map_p(p.mapA_mode, p.mapA, pc);
+    const int64_t pb = map_p(p.mapB_mode, p.mapB, pc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < KK * NNN; i += blockDim.x) {
+      const int k = i / NNN, n = i % NNN;
+      Bs[k][n] = p.B[pb * p.b_pstride + p.boffK[k] + p.boffN[n]];
+    }
+    __syncthreads();
+    const float2* __restrict__ Ap = p.A + pa * p.a_pstride;
+    float2* __restrict__ Cp = p.C + pc * p.c_pstride;
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p.M; m += (int64_t)gridDim.x * blockDim.x) {
+      int64_t x = m;
+#pragma unroll
+      for (int j = 0; j < NK; ++j) {
+        const int pos = p.kpos[j];
+        x = ((x >> pos) << (pos + 1)) | (x & ((1LL << pos) - 1));
+      }
+      float2 a[KK];
+#pragma unroll
+      for (int k = 0; k < KK; ++k) a[k] = __ldg(Ap + x + offK[k]);
+#pragma unroll
+      for (int n = 0; n < NNN; ++n) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < KK; ++k) acc = cmul_add(acc, a[k], Bs[k][n]);
+        Cp[m + (int64_t)n * rowsC] = acc;
+      }
+    }
+  }
+}
+
+template <int NK, int NN>
+static cudaError_t launch_small_t(const SmallParams& p, cudaStream_t s) {
+  const int threads = 256;
+  int64_t bx = (p.M + threads - 1) / threads;
+  const int64_t cap = (int64_t)kSMs * 8;
+  int64_t by = p.PC < 65535 ? p.PC : 65535;
+  if (bx * by > cap * 4) bx = std::max<int64_t>(1, (cap * 4) / by);
+  if (bx < 1) bx = 1;
+  k_small<NK, NN><<<dim3((unsigned)bx, (unsigned)by), threads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+typedef cudaError_t (*small_fn)(const SmallParams&, cudaStream_t);
+#define SMALL_ROW(NK) {launch_small_t<NK, 0>, launch_small_t<NK, 1>, launch_small_t<NK, 2>, launch_small_t<NK, 3>, launch_small_t<NK, 4>}
+static const small_fn small_table[5][5] = {SMALL_ROW(0), SMALL_ROW(1), SMALL_ROW(2), SMALL_ROW(3), SMALL_ROW(4)};
+
+cudaError_t launch_small(const SmallParams& p, cudaStream_t s) {
+  if (p.nk < 0 || p.nk > 4 || p.nn < 0 || p.nn > 4) return cudaErrorInvalidValue;
+  return small_table[p.nk][p.nn](p, s);
+}
+
+// ---------------------------------------------------------------------- K1
+// Bit-permutation transpose.  A tile covers the input's low bits and the
+// preimages of the output's low bits (<= 10 bits); it is read with the input's
+// contiguous order and written with the output's, through shared memory.
+__global__ void __launch_bounds__(256) k_permute(PermParams p) {
+  extern __shared__ float2 tile[];
+  const int nt = 1 << p.t;
+  const uint32_t* in_off = p.tab;
+  const uint32_t* out_off = p.tab + nt;
+  const uint32_t* slot = p.tab + 2 * nt;
+  const int64_t nrest = 1LL << p.n_rest;
+  for (int64_t blk = blockIdx.x; blk < nrest * p.P; blk += gridDim.x) {
+    const int64_t pp = blk / nrest, b = blk % nrest;
+    int64_t bi = 0, bo = 0;
+    for (int v = 0; v < p.n_rest; ++v)
+      if ((b >> v) & 1) { bi |= 1LL << p.rest_in[v]; bo |= 1LL << p.rest_out[v]; }
+    const float2* __restrict__ src = p.in + pp * p.pstride + bi;
+    float2* __restrict__ dst = p.out + pp * p.pstride + bo;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) tile[i] = __ldg(src + __ldg(in_off + i));
+    __syncthreads();
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) dst[__ldg(out_off + j)] = tile[__ldg(slot + j)];
+  }
+}
+
+cudaError_t launch_permute(const PermParams& p, cudaStream_t s) {
+  const int64_t blocks = (1LL << p.n_rest) * p.P;
+  const int64_t grid = std::min<int64_t>(blocks, (int64_t)kSMs * 16);
+  const size_t smem = sizeof(float2) << p.t;
+  k_permute<<<(unsigned)grid, 256, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ B prep
+__global__ void k_bprep_c(BPrepParams p) {
+  const int64_t K = 1LL << p.nk, N = 1LL << p.nn;
+  const int64_t total = p.PB * K * N;
+  float2* out = (float2*)p.out;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pb = e / (K * N), r = e % (K * N);
+    const int64_t k = r / N, n = r % N;
+    out[e] = p.B[pb * p.b_pstride + p.bk[k] + p.bn[n]];
+  }
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Real embedding of B for C_r = A_r B_r with interleaved complex rows:
+// Bt[j][i] (j = 2n + jc output column, i = 2k + ic reduction index) is
+// [[re, -im], [im, re]] in (jc, ic); stored K-major, split into tf32 hi + lo.
+__global__ void k_bprep_tc(BPrepParams p) {
+  const int64_t K2 = 2LL << p.nk, N2 = 2LL << p.nn;
+  const int64_t per = K2 * N2;
+  const int64_t total = p.PB * per;
+  float* hi = (float*)p.out;
+  float* lo = hi + total;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pb = e / per, r = e % per;
+    const int64_t j = r / K2, i = r % K2;
+    const float2 b = p.B[pb * p.b_pstride + p.bk[i >> 1] + p.bn[j >> 1]];
+    const int jc = (int)(j & 1), ic = (int)(i & 1);
+    const float v = jc == 0 ? (ic == 0 ? b.x : -b.y) : (ic == 0 ? b.y : b.x);
+    const float h = tf32_round(v);
+    hi[e] = h;
+    lo[e] = v - h;
+  }
+}
+
+cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s) {
+  const int64_t total = p.PB << (p.nk + p.nn);
+  const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 8);
+  k_bprep_c<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s) {
+  const int64_t total = p.PB << (p.nk + p.nn + 2);
+  const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 8);
+  k_bprep_tc<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ SIMT GEMM
+// Plain FP32 complex GEMM on CUDA cores: 64x64 complex tile, 16-deep k slab,
+// 4x4 outputs per thread.  The reference "plain complex64" engine.
+__global__ void __launch_bounds__(256) k_gemm_simt(GemmParams p) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ float2 As[BK][BM + 1];
+  __shared__ float2 Bs[BK][BN];
+  const int64_t tilesN = (p.N + BN - 1) / BN;
+  const int64_t tm = blockIdx.x / tilesN, tn = blockIdx.x % tilesN;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const float2* __restrict__ Bg0 = (const float2*)p.B;
+  for (int64_t pc = blockIdx.y; pc < p.PC; pc += gridDim.y) {
+    const int64_t pa = map_p(p.mapA_mode, p.mapA, pc), pb = map_p(p.mapB_mode, p.mapB, pc);
+    const float2* __restrict__ Ag = p.A + pa * p.M * p.K;
+    const float2* __restrict__ Bg = Bg0 + pb * p.K * p.N;
+    float2* __restrict__ Cg = p.C + pc * p.M * p.N;
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int64_t k0 = 0; k0 < p.K; k0 += BK) {
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int e = tid + 256 * r;
+        const int ml = e / BK, kl = e % BK;
+        const int64_t m = tm * BM + ml, k = k0 + kl;
+        As[kl][ml] = (m < p.M && k < p.K) ? __ldg(Ag + m * p.K + k) : make_float2(0.f, 0.f);
+        const int kb = e / BN, nl = e % BN;
+        const int64_t n = tn * BN + nl, kk = k0 + kb;
+        Bs[kb][nl] = (n < p.N && kk < p.K) ? __ldg(Bg + kk * p.N + n) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        float2 a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = cmul_add(acc[i][j], a[i], b[j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t m = tm * BM + ty + 16 * i;
+      if (m >= p.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = tn * BN + tx + 16 * j;
+        if (n < p.N) Cg[m * p.N + n] = acc[i][j];
+      }
+    }
+  }
+}
+
+cudaError_t launch_gemm_simt(const GemmParams& p, cudaStream_t s) {
+  const int64_t tiles = ((p.M + 63) / 64) * ((p.N + 63) / 64);
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int64_t gy = std::min<int64_t>(p.PC, 65535);
+  k_gemm_simt<<<dim3((unsigned)tiles, (unsigned)gy), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------- K4
+// H[g][mu] += F[pidx[g]][open bits of mu]   (FP64 accumulation of slices)
+__global__ void k_accum(AccumParams p) {
+  const int64_t total = p.L << p.h;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = e >> p.h;
+    const int64_t mu = e & ((1LL << p.h) - 1);
+    int64_t off = (int64_t)__ldg(p.pidx + g) * p.f_pstride;
+    for (int j = 0; j < p.h; ++j)
+      if ((mu >> j) & 1) off |= 1LL << p.open_pos[j];
+    const float2 v = __ldg(p.F + off);
+    double2 hv = p.H[e];
+    hv.x += (double)v.x;
+    hv.y += (double)v.y;
+    p.H[e] = hv;
+  }
+}
+
+cudaError_t launch_accum(const AccumParams& p, cudaStream_t s) {
+  const int64_t total = p.L << p.h;
+  const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 8);
+  k_accum<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------- K7
+__global__ void k_amplitudes(const double2* __restrict__ H, int h, const uint64_t* __restrict__ keys,
+                             const uint32_t* __restrict__ groups, int64_t n_keys, uint64_t tail_mask,
+                             const int* __restrict__ open_q, const uint64_t* __restrict__ bits, int64_t n, void* out,
+                             int dtype, unsigned long long* status) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t b = bits[i];
+    const uint64_t key = b & tail_mask;
+    int64_t lo = 0, hi = n_keys;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (keys[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    double2 v = make_double2(0.0, 0.0);
+    if (lo < n_keys && keys[lo] == key) {
+      const int64_t g = groups[lo];
+      int64_t mu = 0;
+      for (int j = 0; j < h; ++j) mu |= (int64_t)((b >> open_q[j]) & 1ULL) << j;
+      v = H[(g << h) + mu];
+    } else {
+      atomicMin(status, (unsigned long long)i);
+    }
+    if (dtype == 1) ((double2*)out)[i] = v;
+    else ((float2*)out)[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+cudaError_t launch_amplitudes(const double2* H, int h, const uint64_t* keys, const uint32_t* groups, int64_t n_keys,
+                              uint64_t tail_mask, const int* open_q, const uint64_t* bits, int64_t n, void* out,
+                              int dtype, unsigned long long* status, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t grid = std::min<int64_t>((n + 255) / 256, (int64_t)kSMs * 8);
+  k_amplitudes<<<(unsigned)grid, 256, 0, s>>>(H, h, keys, groups, n_keys, tail_mask, open_q, bits, n, out, dtype,
+                                              status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------- K5
+// One warp per group: chunks of 32 members, each chunk reduced by an inclusive
+// warp scan whose last lane is added to a running carry.  The sampler repeats
+// exactly this order, so its prefix sums end at the same Z[g].
+__device__ __forceinline__ double warp_inclusive_scan(double v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += u;
+  }
+  return v;
+}
+
+__global__ void k_group_norms(const double2* __restrict__ H, int64_t L, int h, double* __restrict__ Z) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t l = 1LL << h;
+  for (int64_t g = warp; g < L; g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double carry = 0.0;
+    for (int64_t c = 0; c < l; c += 32) {
+      double w = 0.0;
+      if (c + lane < l) {
+        const double2 v = H[(g << h) + c + lane];
+        w = v.x * v.x + v.y * v.y;
+      }
+      const double s = warp_inclusive_scan(w);
+      carry += __shfl_sync(0xffffffffu, s, 31);
+    }
+    if (lane == 0) Z[g] = carry;
+  }
+}
+
+// Deterministic single-block sum of Z into N.
+__global__ void k_sum(const double* __restrict__ Z, int64_t L, double* N) {
+  __shared__ double part[32];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < L; i += blockDim.x) acc += Z[i];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if (threadIdx.x == 0) *N = v;
+  }
+}
+
+cudaError_t launch_group_norms(const double2* H, int64_t L, int h, double* Z, double* N, cudaStream_t s) {
+  const int64_t warps = L;
+  const int64_t grid = std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)kSMs * 8);
+  k_group_norms<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(H, L, h, Z);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (N) {
+    k_sum<<<1, 1024, 0, s>>>(Z, L, N);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+// ---------------------------------------------------------------------- K6
+// Philox-4x32-10 (Salmon et al., SC'11): multipliers 0xD2511F53, 0xCD9E8D57,
+// Weyl key increments 0x9E3779B9, 0xBB67AE85, ten rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    if (r != 9) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
+  const uint64_t x = ((uint64_t)hi << 32) | lo;
+  return (double)(x >> 11) * 0x1.0p-53;
+}
+
+// One warp per sample: group i mod L, draw by inverse CDF over the chunked
+// warp-scan prefix sums of |H[g][mu]|^2 (same order as k_group_norms).
+__global__ void k_sample(SampleParams p) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t l = 1LL << p.h;
+  const uint2 key = make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+  const uint64_t full = p.n_qubits >= 64 ? ~0ULL : ((1ULL << p.n_qubits) - 1);
+  for (int64_t i = warp; i < p.n; i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t g = i % p.L;
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, 0u), key);
+    const double u_mix = u53(r.x, r.y), u_pick = u53(r.z, r.w);
+    if (p.mix > 0.0 && u_mix < p.mix) {
+      const uint4 q = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 1u, 0u), key);
+      if (lane == 0) p.out[i] = ((((uint64_t)q.y) << 32) | q.x) & full;
+      continue;
+    }
+    const double2* __restrict__ Hg = p.H + (g << p.h);
+    // pass 1: total in chunk order
+    double Z = 0.0;
+    for (int64_t c = 0; c < l; c += 32) {
+      double w = 0.0;
+      if (c + lane < l) { const double2 v = Hg[c + lane]; w = v.x * v.x + v.y * v.y; }
+      const double s = warp_inclusive_scan(w);
+      Z += __shfl_sync(0xffffffffu, s, 31);
+    }
+    int64_t mu = l - 1;
+    if (Z > 0.0) {
+      const double t = u_pick * Z;
+      double carry = 0.0;
+      for (int64_t c = 0; c < l; c += 32) {
+        double w = 0.0;
+        if (c + lane < l) { const double2 v = Hg[c + lane]; w = v.x * v.x + v.y * v.y; }
+        const double s = warp_inclusive_scan(w);
+        const bool hit = (c + lane < l) && (carry + s > t);
+        const unsigned ball = __ballot_sync(0xffffffffu, hit);
+        if (ball) { mu = c + __ffs(ball) - 1; break; }
+        carry += __shfl_sync(0xffffffffu, s, 31);
+      }
+    } else {
+      mu = (int64_t)(u_pick * (double)l);
+      if (mu >= l) mu = l - 1;
+    }
+    if (lane == 0) {
+      uint64_t s = p.tails[g] & ~p.open_mask;
+      for (int j = 0; j < p.h; ++j) s |= (uint64_t)((mu >> j) & 1) << p.open_q[j];
+      p.out[i] = s;
+    }
+  }
+}
+
+cudaError_t launch_sample(const SampleParams& p, cudaStream_t s) {
+  if (p.n <= 0) return cudaSuccess;
+  const int64_t grid = std::min<int64_t>((p.n * 32 + 255) / 256, (int64_t)kSMs * 16);
+  k_sample<<<(unsigned)grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace tn

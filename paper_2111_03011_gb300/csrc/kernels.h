@@ -1,0 +1,86 @@
+// Device kernels of the contraction path and their launch parameters.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace tn {
+
+// C[p][m + (n << (rA-nk))] = sum_k A[mapA(p)][insert_K(m) + k-offset] * B[mapB(p)][boffK[k] + boffN[n]]
+struct SmallParams {
+  const float2* A; const float2* B; float2* C;
+  int64_t a_pstride, b_pstride, c_pstride;
+  int64_t M;            // rows per pattern = 2^(rA - nk)
+  int64_t PC;
+  int rA, nk, nn;
+  int kpos[4];
+  uint32_t boffK[16], boffN[16];
+  const uint32_t* mapA; const uint32_t* mapB;
+  int mapA_mode, mapB_mode;  // 0 identity, 1 zero, 2 table
+};
+
+// out[p][bo + out_off[j]] = in[p][bi + in_off[slot[j]]], (bi, bo) from the rest bits
+struct PermParams {
+  const float2* in; float2* out;
+  int64_t pstride, P;
+  int t;                 // tile bits
+  int n_rest;
+  uint8_t rest_in[64], rest_out[64];
+  const uint32_t* tab;   // in_off[2^t], out_off[2^t], slot[2^t]
+};
+
+struct BPrepParams {
+  const float2* B; void* out;
+  int64_t b_pstride, PB;
+  int nk, nn;
+  const uint32_t* bk; const uint32_t* bn;
+};
+
+// C[p][m][n] = sum_k A[mapA(p)][m][k] B[mapB(p)][k][n]
+struct GemmParams {
+  const float2* A; const void* B; float2* C;
+  int64_t M, N, K;      // complex dimensions (powers of two)
+  int64_t PA, PB, PC;
+  const uint32_t* mapA; const uint32_t* mapB;
+  int mapA_mode, mapB_mode;
+};
+
+struct AccumParams {
+  const float2* F; double2* H;
+  int64_t f_pstride;
+  int64_t L; int h;
+  const uint32_t* pidx;
+  int open_pos[32];
+};
+
+cudaError_t launch_small(const SmallParams& p, cudaStream_t s);
+cudaError_t launch_permute(const PermParams& p, cudaStream_t s);
+cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s);
+cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s);
+cudaError_t launch_gemm_simt(const GemmParams& p, cudaStream_t s);
+cudaError_t launch_accum(const AccumParams& p, cudaStream_t s);
+
+// Tensor-core GEMM (gemm_tc.cu).  B = real-embedded [PB][2N][2K] fp32 hi then lo.
+// `status` receives a nonzero code if a bounded wait gave up.
+cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s);
+
+// amplitude lookup: out[i] = H[g][mu] (c128 or c64); status <- min missing index
+cudaError_t launch_amplitudes(const double2* H, int h, const uint64_t* keys, const uint32_t* groups, int64_t n_keys,
+                              uint64_t tail_mask, const int* open_q, const uint64_t* bits, int64_t n, void* out,
+                              int dtype, unsigned long long* status, cudaStream_t s);
+
+// per-group squared norms Z[g] (chunked warp order) and the total N
+cudaError_t launch_group_norms(const double2* H, int64_t L, int h, double* Z, double* N, cudaStream_t s);
+
+struct SampleParams {
+  const double2* H; int64_t L; int h;
+  const uint64_t* tails; uint64_t open_mask; const int* open_q;
+  int n_qubits;
+  int64_t n;
+  double mix;                 // probability of a uniform draw
+  uint64_t seed;
+  uint64_t* out;
+};
+cudaError_t launch_sample(const SampleParams& p, cudaStream_t s);
+
+}  // namespace tn

@@ -1,0 +1,926 @@
+// Host-side planner: network construction, simplification, order, step layout.
+// See planner.h for the data model.
+#include "planner.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <random>
+#include <set>
+#include <sstream>
+
+#include "tn_gb300.h"
+
+namespace tn {
+
+const std::vector<uint64_t>& PatternBook::get(uint64_t mask) {
+  auto it = cache.find(mask);
+  if (it != cache.end()) return it->second;
+  std::vector<uint64_t> v;
+  v.reserve(tails.size());
+  for (uint64_t t : tails) v.push_back(t & mask);
+  std::sort(v.begin(), v.end());
+  v.erase(std::unique(v.begin(), v.end()), v.end());
+  return cache.emplace(mask, std::move(v)).first->second;
+}
+
+static int64_t pat_index(const std::vector<uint64_t>& pats, uint64_t v) {
+  auto it = std::lower_bound(pats.begin(), pats.end(), v);
+  if (it == pats.end() || *it != v) return -1;
+  return (int64_t)(it - pats.begin());
+}
+
+static int find_pos(const std::vector<int>& legs, int l) {
+  for (size_t i = 0; i < legs.size(); ++i)
+    if (legs[i] == l) return (int)i;
+  return -1;
+}
+
+// ---------------------------------------------------------------- host tensors
+
+// Contract A and B over every leg they share; result legs = A's free legs then B's.
+static HostTensor contract_host(const HostTensor& A, const HostTensor& B, PatternBook& book) {
+  std::vector<int> shared;
+  for (int l : A.legs)
+    if (find_pos(B.legs, l) >= 0) shared.push_back(l);
+  HostTensor C;
+  std::vector<int> srcA, srcB;  // for C leg i: position in A (or -1), position in B (or -1)
+  for (int l : A.legs)
+    if (find_pos(shared, l) < 0) { C.legs.push_back(l); srcA.push_back(find_pos(A.legs, l)); srcB.push_back(-1); }
+  for (int l : B.legs)
+    if (find_pos(shared, l) < 0) { C.legs.push_back(l); srcA.push_back(-1); srcB.push_back(find_pos(B.legs, l)); }
+  C.tq = A.tq | B.tq;
+  C.pats = book.get(C.tq);
+  const int rA = (int)A.legs.size(), rB = (int)B.legs.size(), rC = (int)C.legs.size();
+  const int nk = (int)shared.size();
+  std::vector<int64_t> ka(1LL << nk), kb(1LL << nk);
+  for (int64_t k = 0; k < (1LL << nk); ++k) {
+    int64_t a = 0, b = 0;
+    for (int j = 0; j < nk; ++j)
+      if ((k >> j) & 1) { a |= 1LL << find_pos(A.legs, shared[j]); b |= 1LL << find_pos(B.legs, shared[j]); }
+    ka[k] = a; kb[k] = b;
+  }
+  const int64_t nC = 1LL << rC;
+  C.data.assign((size_t)(C.P() * nC), cd(0, 0));
+  for (int64_t p = 0; p < C.P(); ++p) {
+    int64_t pa = pat_index(A.pats, C.pats[p] & A.tq);
+    int64_t pb = pat_index(B.pats, C.pats[p] & B.tq);
+    const cd* a0 = A.data.data() + pa * (1LL << rA);
+    const cd* b0 = B.data.data() + pb * (1LL << rB);
+    for (int64_t c = 0; c < nC; ++c) {
+      int64_t ia = 0, ib = 0;
+      for (int i = 0; i < rC; ++i)
+        if ((c >> i) & 1) {
+          if (srcA[i] >= 0) ia |= 1LL << srcA[i];
+          else ib |= 1LL << srcB[i];
+        }
+      cd s(0, 0);
+      for (size_t k = 0; k < ka.size(); ++k) s += a0[ia + ka[k]] * b0[ib + kb[k]];
+      C.data[(size_t)(p * nC + c)] = s;
+    }
+  }
+  return C;
+}
+
+// Fix leg at position `pos` to value v and drop it.
+static void select_leg(HostTensor& T, int pos, int v) {
+  const int r = (int)T.legs.size();
+  const int64_t n_old = 1LL << r, n_new = 1LL << (r - 1);
+  std::vector<cd> d((size_t)(T.P() * n_new));
+  const int64_t lo_mask = (1LL << pos) - 1;
+  for (int64_t p = 0; p < T.P(); ++p)
+    for (int64_t i = 0; i < n_new; ++i) {
+      int64_t src = ((i & ~lo_mask) << 1) | ((int64_t)v << pos) | (i & lo_mask);
+      d[(size_t)(p * n_new + i)] = T.data[(size_t)(p * n_old + src)];
+    }
+  T.data.swap(d);
+  T.legs.erase(T.legs.begin() + pos);
+}
+
+static double log2_size(const HostTensor& T) { return std::log2((double)T.P()) + (double)T.legs.size(); }
+
+// --------------------------------------------------------------- network build
+
+struct Builder {
+  Plan& plan;
+  std::vector<HostTensor> T;
+  std::vector<int> pin_of_leg;   // -1 or pinned value
+
+  explicit Builder(Plan& p) : plan(p) {}
+
+  int new_leg(int kind) {
+    Leg l;
+    l.kind = kind;
+    plan.legs.push_back(l);
+    pin_of_leg.push_back(-1);
+    return (int)plan.legs.size() - 1;
+  }
+};
+
+static int build_network(const PlanInput& in, Plan& plan, Builder& b, std::string& err) {
+  const int n = in.n_qubits;
+  std::vector<int> wire(n);
+  for (int q = 0; q < n; ++q) {
+    int l = b.new_leg(LEG_BOND);
+    HostTensor t;
+    t.legs = {l};
+    t.data = {cd(1, 0), cd(0, 0)};
+    b.T.push_back(t);
+    wire[q] = l;
+  }
+  // cuts by gate
+  std::map<int, std::vector<std::pair<int, int>>> cuts;  // gate -> (leg, edge index)
+  for (size_t e = 0; e < in.edges.size(); ++e) cuts[in.edges[e].gate].push_back({in.edges[e].leg, (int)e});
+  int slice_bit = 0;
+  std::vector<int> edge_slice_bit(in.edges.size(), -1);
+  for (size_t e = 0; e < in.edges.size(); ++e)
+    if (in.edges[e].kind == TN_EDGE_SLICE) edge_slice_bit[e] = slice_bit++;
+
+  for (int gi = 0; gi < in.n_gates; ++gi) {
+    const int ar = in.arity[gi];
+    const int q0 = in.q0[gi], q1 = in.q1[gi];
+    auto it = cuts.find(gi);
+    if (it != cuts.end()) {
+      for (auto& c : it->second) {
+        const int q = c.first == 0 ? q0 : q1;
+        const auto& E = in.edges[c.second];
+        int old = wire[q];
+        int nw = b.new_leg(LEG_HALF);
+        plan.legs[old].kind = LEG_HALF;
+        if (E.kind == TN_EDGE_SLICE) {
+          plan.legs[old].slice_bit = edge_slice_bit[c.second];
+          plan.legs[nw].slice_bit = edge_slice_bit[c.second];
+        } else {
+          b.pin_of_leg[old] = E.value;
+          b.pin_of_leg[nw] = E.value;
+        }
+        wire[q] = nw;
+      }
+    }
+    const cd* U = in.mats + (size_t)gi * 16;
+    HostTensor t;
+    if (ar == 1) {
+      int out = b.new_leg(LEG_BOND);
+      t.legs = {wire[q0], out};
+      t.data.assign(4, cd(0, 0));
+      for (int o = 0; o < 2; ++o)
+        for (int i = 0; i < 2; ++i) t.data[i + 2 * o] = U[o * 2 + i];
+      wire[q0] = out;
+    } else {
+      int o0 = b.new_leg(LEG_BOND), o1 = b.new_leg(LEG_BOND);
+      t.legs = {wire[q0], wire[q1], o0, o1};
+      t.data.assign(16, cd(0, 0));
+      for (int a0 = 0; a0 < 2; ++a0)
+        for (int a1 = 0; a1 < 2; ++a1)
+          for (int i0 = 0; i0 < 2; ++i0)
+            for (int i1 = 0; i1 < 2; ++i1)
+              t.data[i0 + 2 * i1 + 4 * a0 + 8 * a1] = U[(2 * a0 + a1) * 4 + (2 * i0 + i1)];
+      wire[q0] = o0;
+      wire[q1] = o1;
+    }
+    b.T.push_back(t);
+  }
+  // final boundary: open legs, tail projectors with a pattern axis
+  for (int q = 0; q < n; ++q) {
+    int j = find_pos(plan.open_qubits, q);
+    if (j >= 0) {
+      plan.legs[wire[q]].kind = LEG_OPEN;
+      plan.legs[wire[q]].open_index = j;
+    } else {
+      HostTensor t;
+      t.legs = {wire[q]};
+      t.tq = 1ULL << q;
+      t.pats = plan.book.get(t.tq);
+      t.data.assign((size_t)(2 * t.P()), cd(0, 0));
+      for (int64_t p = 0; p < t.P(); ++p) t.data[(size_t)(2 * p + ((t.pats[p] >> q) & 1))] = cd(1, 0);
+      b.T.push_back(t);
+    }
+  }
+  // apply pins (both half legs of a pinned edge take its value)
+  for (auto& t : b.T)
+    for (int pos = (int)t.legs.size() - 1; pos >= 0; --pos) {
+      int l = t.legs[pos];
+      if (plan.legs[l].kind == LEG_HALF && b.pin_of_leg[l] >= 0) select_leg(t, pos, b.pin_of_leg[l]);
+    }
+  (void)err;
+  return TN_OK;
+}
+
+// Absorb order-one and order-two tensors into neighbours and split rank-one
+// order-two tensors (the exact hole reduction of Method case (i)).
+static void simplify(Plan& plan, std::vector<HostTensor>& T, int absorb_log2) {
+  auto is_bond = [&](int l) { return plan.legs[l].kind == LEG_BOND; };
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    // rank-one split
+    const size_t n0 = T.size();
+    for (size_t i = 0; i < n0; ++i) {
+      HostTensor& t = T[i];
+      if (!t.alive || t.legs.size() != 2 || t.tq != 0) continue;
+      if (!is_bond(t.legs[0]) || !is_bond(t.legs[1])) continue;
+      // data[a + 2b]
+      cd m00 = t.data[0], m10 = t.data[1], m01 = t.data[2], m11 = t.data[3];
+      double nrm = std::norm(m00) + std::norm(m01) + std::norm(m10) + std::norm(m11);
+      if (nrm == 0.0) continue;
+      if (std::abs(m00 * m11 - m01 * m10) > 1e-13 * nrm) continue;
+      // pick largest entry
+      int ba = 0, bb = 0;
+      double best = -1;
+      for (int a = 0; a < 2; ++a)
+        for (int bq = 0; bq < 2; ++bq)
+          if (std::abs(t.data[a + 2 * bq]) > best) { best = std::abs(t.data[a + 2 * bq]); ba = a; bb = bq; }
+      HostTensor u, v;
+      u.legs = {t.legs[0]};
+      v.legs = {t.legs[1]};
+      u.data = {t.data[0 + 2 * bb], t.data[1 + 2 * bb]};
+      cd piv = t.data[ba + 2 * bb];
+      v.data = {t.data[ba + 0] / piv, t.data[ba + 2] / piv};
+      t.alive = false;
+      T.push_back(u);
+      T.push_back(v);
+      changed = true;
+    }
+    // absorption
+    std::unordered_map<int, std::vector<int>> owners;
+    for (size_t i = 0; i < T.size(); ++i)
+      if (T[i].alive)
+        for (int l : T[i].legs)
+          if (is_bond(l)) owners[l].push_back((int)i);
+    for (size_t i = 0; i < T.size(); ++i) {
+      HostTensor& t = T[i];
+      if (!t.alive || t.legs.size() > 2) continue;
+      int best_n = -1;
+      double best_sz = 1e300;
+      for (int l : t.legs) {
+        if (!is_bond(l)) continue;
+        for (int o : owners[l]) {
+          if (o == (int)i || !T[o].alive) continue;
+          // result size
+          int shared = 0;
+          for (int x : t.legs)
+            if (find_pos(T[o].legs, x) >= 0) ++shared;
+          double sz = std::log2((double)plan.book.count(T[o].tq | t.tq)) +
+                      (double)(T[o].legs.size() + t.legs.size() - 2 * shared);
+          if (sz < best_sz) { best_sz = sz; best_n = o; }
+        }
+      }
+      if (best_n < 0 || best_sz > absorb_log2) continue;
+      HostTensor merged = contract_host(T[best_n], t, plan.book);
+      T[best_n] = std::move(merged);
+      T[i].alive = false;
+      changed = true;
+      // refresh owners (cheap enough at circuit sizes)
+      owners.clear();
+      for (size_t k = 0; k < T.size(); ++k)
+        if (T[k].alive)
+          for (int l : T[k].legs)
+            if (is_bond(l)) owners[l].push_back((int)k);
+    }
+  }
+}
+
+// ------------------------------------------------------------------- ordering
+
+struct GNode {
+  std::vector<int> legs;  // device legs (bond + open)
+  uint64_t tq = 0;
+  double lsz = 0;         // log2 elements
+  bool alive = true;
+};
+
+static std::vector<int> sym_diff_bond(const std::vector<int>& a, const std::vector<int>& b) {
+  std::vector<int> out;
+  for (int l : a)
+    if (find_pos(b, l) < 0) out.push_back(l);
+  for (int l : b)
+    if (find_pos(a, l) < 0) out.push_back(l);
+  return out;
+}
+
+static int shared_count(const std::vector<int>& a, const std::vector<int>& b) {
+  int s = 0;
+  for (int l : a)
+    if (find_pos(b, l) >= 0) ++s;
+  return s;
+}
+
+// Rough execution-time model of a pairwise contraction (seconds), used only to
+// pick among greedy restarts.
+static double step_time_model(double lA, double lB, double lC, int nk, int nn_small, bool tc) {
+  const double bw = 6.5e12;
+  double A = std::exp2(lA), B = std::exp2(lB), C = std::exp2(lC);
+  double macs = C * std::exp2(nk);
+  double bytes = 8.0 * (A + B + C);
+  bool small = nk <= 4 && nn_small <= 4;
+  double peak = small ? 40e12 : (tc ? 250e12 : 40e12);
+  if (!small) bytes += 16.0 * std::max(A, B);  // permute of the big operand
+  return std::max(bytes / bw, 8.0 * macs / peak) + 3e-6;
+}
+
+// Randomised greedy search (restarts).  Each trial repeatedly contracts the
+// connected pair minimising size(C) - alpha * (size(A) + size(B)), with alpha
+// drawn per trial and Gumbel noise of temperature tau on log-scores after the
+// first trial.  A trial never stops at the cap: it records its largest
+// intermediate, and the best trial is the one under the cap with the lowest
+// modelled time (or, if none fits, the one with the smallest maximum).
+static int greedy_order(Plan& plan, const std::vector<GNode>& init, double cap, int trials, uint64_t seed,
+                        std::vector<std::pair<int, int>>& best_order, std::string& err) {
+  double best_cost = 1e300, best_max = 1e300;
+  bool best_fits = false;
+  std::mt19937_64 rng(seed);
+  std::uniform_real_distribution<double> ud(1e-12, 1.0);
+  for (int trial = 0; trial < std::max(1, trials); ++trial) {
+    const double alpha = trial == 0 ? 1.0 : 0.3 + 1.2 * ud(rng);
+    const double tau = trial == 0 ? 0.0 : 0.05 + 0.6 * ud(rng);
+    std::vector<GNode> g = init;
+    std::vector<std::pair<int, int>> order;
+    double cost = 0, mx = 0;
+    int alive = 0;
+    for (auto& x : g) {
+      alive += x.alive;
+      mx = std::max(mx, x.lsz);
+    }
+    std::unordered_map<int, std::vector<int>> owners;
+    for (size_t i = 0; i < g.size(); ++i)
+      if (g[i].alive)
+        for (int l : g[i].legs)
+          if (plan.legs[l].kind == LEG_BOND) owners[l].push_back((int)i);
+    while (alive > 1) {
+      std::set<std::pair<int, int>> cand;
+      for (auto& kv : owners)
+        if (kv.second.size() == 2) {
+          int a = std::min(kv.second[0], kv.second[1]), b = std::max(kv.second[0], kv.second[1]);
+          cand.insert({a, b});
+        }
+      int bi = -1, bj = -1;
+      double bs = 1e300;
+      for (auto& pr : cand) {
+        const GNode &A = g[pr.first], &B = g[pr.second];
+        std::vector<int> cl = sym_diff_bond(A.legs, B.legs);
+        double lc = std::log2((double)plan.book.count(A.tq | B.tq)) + (double)cl.size();
+        // prefer pairs under the cap; among those the greedy score
+        double score = std::exp2(lc) - alpha * (std::exp2(A.lsz) + std::exp2(B.lsz));
+        // log-domain key keeps the noise scale-free
+        double key = (score >= 0 ? std::log2(1.0 + score) : -std::log2(1.0 - score));
+        if (tau > 0) key -= tau * std::log(-std::log(ud(rng)));
+        if (lc > cap + 1e-9) key += 1e6 + lc;
+        if (key < bs) { bs = key; bi = pr.first; bj = pr.second; }
+      }
+      if (bi < 0) {
+        // disconnected: outer product of the two smallest
+        std::vector<int> al;
+        for (size_t i = 0; i < g.size(); ++i)
+          if (g[i].alive) al.push_back((int)i);
+        std::sort(al.begin(), al.end(), [&](int a, int b) { return g[a].lsz < g[b].lsz; });
+        bi = std::min(al[0], al[1]);
+        bj = std::max(al[0], al[1]);
+      }
+      GNode &A = g[bi], &B = g[bj];
+      int nk = shared_count(A.legs, B.legs);
+      std::vector<int> cl = sym_diff_bond(A.legs, B.legs);
+      GNode C;
+      C.legs = cl;
+      C.tq = A.tq | B.tq;
+      C.lsz = std::log2((double)plan.book.count(C.tq)) + (double)cl.size();
+      mx = std::max(mx, C.lsz);
+      int nn_small = (int)((A.lsz <= B.lsz ? A.legs.size() : B.legs.size())) - nk;
+      cost += step_time_model(A.lsz, B.lsz, C.lsz, nk, nn_small, plan.gemm_engine != TN_GEMM_SIMT_FP32);
+      // update owners: legs of B move to slot bi, shared legs vanish
+      for (int l : A.legs)
+        if (plan.legs[l].kind == LEG_BOND) {
+          auto& v = owners[l];
+          v.erase(std::remove(v.begin(), v.end(), bi), v.end());
+          if (v.empty()) owners.erase(l);
+        }
+      for (int l : B.legs)
+        if (plan.legs[l].kind == LEG_BOND) {
+          auto& v = owners[l];
+          v.erase(std::remove(v.begin(), v.end(), bj), v.end());
+          if (v.empty()) owners.erase(l);
+        }
+      for (int l : C.legs)
+        if (plan.legs[l].kind == LEG_BOND) owners[l].push_back(bi);
+      order.push_back({bi, bj});
+      g[bi] = C;
+      g[bj].alive = false;
+      --alive;
+    }
+    const bool fits = mx <= cap + 1e-9;
+    bool better;
+    if (fits != best_fits) better = fits;
+    else if (fits) better = cost < best_cost;
+    else better = mx < best_max || (mx == best_max && cost < best_cost);
+    if (better || best_order.empty()) {
+      best_fits = fits;
+      best_cost = cost;
+      best_max = mx;
+      best_order = order;
+    }
+  }
+  if (!best_fits) {
+    err = "no contraction order found keeps every intermediate under the size cap (best 2^" +
+          std::to_string(best_max) + " elements); slice more edges or raise the cap";
+    return TN_ERR_OOM;
+  }
+  return TN_OK;
+}
+
+// ---------------------------------------------------------------- step layout
+
+static int64_t meta_push(Plan& plan, const std::vector<uint32_t>& v) {
+  while (plan.meta.size() % 4) plan.meta.push_back(0);
+  int64_t off = (int64_t)plan.meta.size();
+  plan.meta.insert(plan.meta.end(), v.begin(), v.end());
+  return off;
+}
+
+static int new_buf(Plan& plan, int64_t bytes, int step) {
+  BufInfo b;
+  b.bytes = (bytes + 255) / 256 * 256;
+  b.first = step;
+  b.last = step;
+  plan.bufs.push_back(b);
+  return (int)plan.bufs.size() - 1;
+}
+
+static void touch(Plan& plan, const Ref& r, int step) {
+  if (r.kind == 1) plan.bufs[r.id].last = std::max(plan.bufs[r.id].last, step);
+}
+
+static int64_t vt_elems(const VTensor& v) { return v.P * (1LL << v.legs.size()); }
+
+// Pattern maps of C's pattern axis onto an operand's.
+static void set_map(Plan& plan, const VTensor& X, const VTensor& C, int& mode, int64_t& off) {
+  if (X.tq == 0) { mode = 1; off = 0; return; }
+  if (X.tq == C.tq) { mode = 0; off = 0; return; }
+  const auto& pc = plan.book.get(C.tq);
+  const auto& px = plan.book.get(X.tq);
+  std::vector<uint32_t> m(pc.size());
+  for (size_t p = 0; p < pc.size(); ++p) m[p] = (uint32_t)pat_index(px, pc[p] & X.tq);
+  mode = 2;
+  off = meta_push(plan, m);
+}
+
+static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& target, Ref out, int ci) {
+  Step s;
+  s.kind = ST_PERMUTE;
+  s.a = X.ref;
+  s.c = out;
+  s.contraction = ci;
+  const int r = (int)X.legs.size();
+  s.rA = s.rC = r;
+  s.PA = s.PC = X.P;
+  std::vector<int> in_pos(r), inv(r);  // in_pos[o] = input position of output position o
+  for (int o = 0; o < r; ++o) in_pos[o] = find_pos(X.legs, target[o]);
+  for (int o = 0; o < r; ++o) inv[in_pos[o]] = o;
+  const int a = std::min(r, 5), bq = std::min(r, 5);
+  std::vector<int> Tin;
+  for (int x = 0; x < a; ++x) Tin.push_back(x);
+  for (int o = 0; o < bq; ++o)
+    if (std::find(Tin.begin(), Tin.end(), in_pos[o]) == Tin.end()) Tin.push_back(in_pos[o]);
+  std::sort(Tin.begin(), Tin.end());
+  const int t = (int)Tin.size();
+  std::vector<int> Tout;
+  for (int x : Tin) Tout.push_back(inv[x]);
+  std::sort(Tout.begin(), Tout.end());
+  const int nt = 1 << t;
+  std::vector<uint32_t> tab(3 * (size_t)nt);
+  for (int i = 0; i < nt; ++i) {
+    uint32_t io = 0, oo = 0, sl = 0;
+    for (int u = 0; u < t; ++u)
+      if ((i >> u) & 1) {
+        io |= 1u << Tin[u];
+        oo |= 1u << Tout[u];
+        int ip = in_pos[Tout[u]];
+        int slot_bit = (int)(std::find(Tin.begin(), Tin.end(), ip) - Tin.begin());
+        sl |= 1u << slot_bit;
+      }
+    tab[i] = io;
+    tab[nt + i] = oo;
+    tab[2 * nt + i] = sl;
+  }
+  s.t_bits = t;
+  s.tab_off = meta_push(plan, tab);
+  s.n_rest = 0;
+  for (int x = 0; x < r; ++x)
+    if (std::find(Tin.begin(), Tin.end(), x) == Tin.end()) {
+      s.rest_in[s.n_rest] = (uint8_t)x;
+      s.rest_out[s.n_rest] = (uint8_t)inv[x];
+      ++s.n_rest;
+    }
+  s.bytes = 16.0 * (double)vt_elems(X);
+  plan.steps.push_back(s);
+}
+
+static int layout_steps(Plan& plan, std::string& err) {
+  plan.steps.clear();
+  plan.bufs.clear();
+  int ci = 0;
+  for (auto& pr : plan.order) {
+    const int i = pr.first, j = pr.second;
+    VTensor A = plan.vts[i], B = plan.vts[j];
+    std::vector<int> shared;
+    for (int l : A.legs)
+      if (find_pos(B.legs, l) >= 0) shared.push_back(l);
+    // roles: big operand streams (rows), small operand is the "gate"
+    const VTensor& big = vt_elems(A) >= vt_elems(B) ? A : B;
+    const VTensor& sml = vt_elems(A) >= vt_elems(B) ? B : A;
+    std::vector<int> K, M, N;
+    for (int l : big.legs)
+      if (find_pos(shared, l) >= 0) K.push_back(l); else M.push_back(l);
+    for (int l : sml.legs)
+      if (find_pos(shared, l) < 0) N.push_back(l);
+    const int nk = (int)K.size(), nm = (int)M.size(), nn = (int)N.size();
+    VTensor C;
+    C.tq = A.tq | B.tq;
+    C.P = plan.book.count(C.tq);
+    int mapA_mode, mapB_mode;
+    int64_t mapA_off, mapB_off;
+    C.legs.clear();
+    std::vector<int> cl;
+    const bool use_small = nk <= plan.small_max_bits && nn <= plan.small_max_bits;
+    if (use_small) {
+      for (int l : M) cl.push_back(l);
+      for (int l : N) cl.push_back(l);
+    } else {
+      for (int l : N) cl.push_back(l);
+      for (int l : M) cl.push_back(l);
+    }
+    C.legs = cl;
+    const double lc = std::log2((double)C.P) + (double)cl.size();
+    if (lc > plan.cap_log2 + 1e-9) {
+      err = "contraction " + std::to_string(ci) + " exceeds the size cap (2^" + std::to_string(lc) + " elements)";
+      return TN_ERR_OOM;
+    }
+    plan.max_log2 = std::max(plan.max_log2, lc);
+    set_map(plan, big, C, mapA_mode, mapA_off);
+    set_map(plan, sml, C, mapB_mode, mapB_off);
+    const int64_t eC = vt_elems(C);
+    const double macs = (double)C.P * std::exp2((double)(nm + nn + nk));
+    plan.tc_macs += macs;
+    plan.alg_bytes += 8.0 * (double)(vt_elems(big) + vt_elems(sml) + eC);
+
+    std::vector<uint32_t> bk(1u << nk), bn(1u << nn);
+    for (uint32_t k = 0; k < bk.size(); ++k) {
+      uint32_t o = 0;
+      for (int q = 0; q < nk; ++q)
+        if ((k >> q) & 1) o |= 1u << find_pos(sml.legs, K[q]);
+      bk[k] = o;
+    }
+    for (uint32_t n = 0; n < bn.size(); ++n) {
+      uint32_t o = 0;
+      for (int q = 0; q < nn; ++q)
+        if ((n >> q) & 1) o |= 1u << find_pos(sml.legs, N[q]);
+      bn[n] = o;
+    }
+
+    if (use_small) {
+      Step s;
+      s.kind = ST_SMALL;
+      s.contraction = ci;
+      s.a = big.ref;
+      s.b = sml.ref;
+      s.rA = (int)big.legs.size();
+      s.rB = (int)sml.legs.size();
+      s.rC = (int)cl.size();
+      s.PA = big.P; s.PB = sml.P; s.PC = C.P;
+      s.nk = nk; s.nm = nm; s.nn = nn;
+      s.mapA_mode = mapA_mode; s.mapA_off = mapA_off;
+      s.mapB_mode = mapB_mode; s.mapB_off = mapB_off;
+      for (int q = 0; q < nk; ++q) s.kposA[q] = find_pos(big.legs, K[q]);
+      for (size_t k = 0; k < bk.size(); ++k) s.boffK[k] = bk[k];
+      for (size_t n = 0; n < bn.size(); ++n) s.boffN[n] = bn[n];
+      s.macs = macs;
+      s.bytes = 8.0 * (double)(vt_elems(big) + vt_elems(sml) + eC);
+      const int st = (int)plan.steps.size();
+      touch(plan, s.a, st);
+      touch(plan, s.b, st);
+      s.c = Ref{1, new_buf(plan, eC * 8, st)};
+      C.ref = s.c;
+      plan.steps.push_back(s);
+    } else {
+      // A' = big permuted to [K][M] (K legs low) unless already so
+      std::vector<int> target;
+      for (int l : K) target.push_back(l);
+      for (int l : M) target.push_back(l);
+      Ref aref = big.ref;
+      if (target != big.legs) {
+        const int st = (int)plan.steps.size();
+        touch(plan, big.ref, st);
+        Ref out{1, new_buf(plan, vt_elems(big) * 8, st)};
+        add_permute(plan, big, target, out, ci);
+        aref = out;
+      }
+      const bool tc = plan.gemm_engine != TN_GEMM_SIMT_FP32 && nk >= 1;
+      // B' prep
+      Step p;
+      p.kind = tc ? ST_BPREP_TC : ST_BPREP_C;
+      p.contraction = ci;
+      p.a = sml.ref;
+      p.rA = (int)sml.legs.size();
+      p.PA = sml.P;
+      p.nk = nk; p.nn = nn;
+      p.bk_off = meta_push(plan, bk);
+      p.bn_off = meta_push(plan, bn);
+      const int64_t bprep_bytes = tc ? 2LL * sml.P * (2LL << nn) * (2LL << nk) * 4 : sml.P * (1LL << (nk + nn)) * 8;
+      {
+        const int st = (int)plan.steps.size();
+        touch(plan, sml.ref, st);
+        p.c = Ref{1, new_buf(plan, bprep_bytes, st)};
+        p.bytes = 8.0 * (double)vt_elems(sml) + (double)bprep_bytes;
+        plan.steps.push_back(p);
+      }
+      Step g;
+      g.kind = tc ? ST_GEMM_TC : ST_GEMM_SIMT;
+      g.contraction = ci;
+      g.a = aref;
+      g.b = p.c;
+      g.rA = (int)big.legs.size();
+      g.rB = (int)sml.legs.size();
+      g.rC = (int)cl.size();
+      g.PA = big.P; g.PB = sml.P; g.PC = C.P;
+      g.nk = nk; g.nm = nm; g.nn = nn;
+      g.mapA_mode = mapA_mode; g.mapA_off = mapA_off;
+      g.mapB_mode = mapB_mode; g.mapB_off = mapB_off;
+      g.macs = macs;
+      g.bytes = 8.0 * (double)(vt_elems(big) + eC) + (double)bprep_bytes;
+      const int st = (int)plan.steps.size();
+      touch(plan, g.a, st);
+      touch(plan, g.b, st);
+      g.c = Ref{1, new_buf(plan, eC * 8, st)};
+      C.ref = g.c;
+      plan.steps.push_back(g);
+    }
+    for (auto& s : plan.steps)
+      if (s.contraction == ci) { s.vt_a = i; s.vt_b = j; s.vt_c = (int)plan.vts.size(); }
+    plan.vts.push_back(C);
+    plan.vts[i].alive = false;
+    plan.vts[j].alive = false;
+    // the result lives at slot i: keep a pointer from i to the new tensor
+    // (the order refers to slots, see build_plan)
+    ++ci;
+  }
+  plan.n_contractions = ci;
+  return TN_OK;
+}
+
+static void plan_arena(Plan& plan) {
+  std::vector<int> idx(plan.bufs.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+    if (plan.bufs[a].bytes != plan.bufs[b].bytes) return plan.bufs[a].bytes > plan.bufs[b].bytes;
+    return a < b;
+  });
+  std::vector<int> placed;
+  int64_t peak = 0;
+  for (int b : idx) {
+    BufInfo& B = plan.bufs[b];
+    std::vector<std::pair<int64_t, int64_t>> busy;
+    for (int o : placed) {
+      const BufInfo& O = plan.bufs[o];
+      if (O.last < B.first || B.last < O.first) continue;
+      busy.push_back({O.off, O.off + O.bytes});
+    }
+    std::sort(busy.begin(), busy.end());
+    int64_t off = 0;
+    for (auto& iv : busy) {
+      if (off + B.bytes <= iv.first) break;
+      off = std::max(off, iv.second);
+    }
+    B.off = off;
+    peak = std::max(peak, off + B.bytes);
+    placed.push_back(b);
+  }
+  plan.workspace_bytes = peak;
+}
+
+// --------------------------------------------------------------------- driver
+
+int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
+  const int n = in.n_qubits;
+  if (n < 1 || n > 64) { err = "n_qubits must be in [1, 64]"; return TN_ERR_INVALID; }
+  if (in.n_gates < 0) { err = "n_gates < 0"; return TN_ERR_INVALID; }
+  for (int g = 0; g < in.n_gates; ++g) {
+    const int ar = in.arity[g];
+    if (ar != 1 && ar != 2) { err = "gate " + std::to_string(g) + ": arity must be 1 or 2"; return TN_ERR_INVALID; }
+    if (in.q0[g] < 0 || in.q0[g] >= n || (ar == 2 && (in.q1[g] < 0 || in.q1[g] >= n || in.q1[g] == in.q0[g]))) {
+      err = "gate " + std::to_string(g) + ": bad qubit";
+      return TN_ERR_INVALID;
+    }
+  }
+  plan.n_qubits = n;
+  plan.open_qubits = in.open_qubits;
+  if ((int)in.open_qubits.size() > 30) { err = "at most 30 open qubits"; return TN_ERR_INVALID; }
+  plan.open_mask = 0;
+  for (int q : in.open_qubits) {
+    if (q < 0 || q >= n) { err = "open qubit out of range"; return TN_ERR_INVALID; }
+    if ((plan.open_mask >> q) & 1) { err = "duplicate open qubit"; return TN_ERR_INVALID; }
+    plan.open_mask |= 1ULL << q;
+  }
+  const uint64_t full = n == 64 ? ~0ULL : ((1ULL << n) - 1);
+  plan.tail_mask = full & ~plan.open_mask;
+  if (in.tails.empty()) { err = "n_tails must be >= 1"; return TN_ERR_INVALID; }
+  plan.tails_raw = in.tails;
+  plan.book.tails.clear();
+  for (uint64_t t : in.tails) plan.book.tails.push_back(t & plan.tail_mask);
+  plan.cap_log2 = in.cap_log2;
+  plan.gemm_engine = in.gemm_engine;
+  plan.small_max_bits = in.small_max_bits;
+
+  // edges
+  std::set<std::pair<int, int>> seen;
+  int k = 0, pins = 0;
+  for (auto& e : in.edges) {
+    if (e.gate < 0 || e.gate >= in.n_gates) { err = "edge: gate out of range"; return TN_ERR_INVALID; }
+    if (e.leg < 0 || e.leg >= in.arity[e.gate]) { err = "edge: leg out of range"; return TN_ERR_INVALID; }
+    if (!seen.insert({e.gate, e.leg}).second) { err = "edge listed twice"; return TN_ERR_INVALID; }
+    if (e.kind == TN_EDGE_SLICE) ++k;
+    else if (e.kind == TN_EDGE_PIN) {
+      if (e.value != 0 && e.value != 1) { err = "pin value must be 0 or 1"; return TN_ERR_INVALID; }
+      ++pins;
+    } else if (e.kind == TN_EDGE_COMPANION) {
+      err = "companion edges are not implemented";
+      return TN_ERR_UNSUPPORTED;
+    } else { err = "edge: unknown kind"; return TN_ERR_INVALID; }
+  }
+  if (k > 40) { err = "at most 40 sliced edges"; return TN_ERR_INVALID; }
+  plan.n_sliced = k;
+  plan.n_pinned = pins;
+
+  Builder b(plan);
+  int rc = build_network(in, plan, b, err);
+  if (rc) return rc;
+  simplify(plan, b.T, in.absorb_log2);
+
+  // leaves
+  plan.leaves.clear();
+  for (auto& t : b.T)
+    if (t.alive) plan.leaves.push_back(t);
+  plan.leaf_info.clear();
+  plan.leaf_arena.clear();
+  plan.vts.clear();
+  for (auto& t : plan.leaves) {
+    LeafInfo li;
+    std::vector<int> half_pos;
+    std::vector<int> dev_legs;
+    for (size_t p = 0; p < t.legs.size(); ++p) {
+      if (plan.legs[t.legs[p]].kind == LEG_HALF) {
+        half_pos.push_back((int)p);
+        li.var_slice_bits.push_back(plan.legs[t.legs[p]].slice_bit);
+      } else dev_legs.push_back(t.legs[p]);
+    }
+    li.size = t.P() * (1LL << dev_legs.size());
+    // align each leaf to 16 complex elements (128 bytes)
+    while (plan.leaf_arena.size() % 16) plan.leaf_arena.push_back(cd(0, 0));
+    li.off = (int64_t)plan.leaf_arena.size();
+    const int nh = (int)half_pos.size();
+    for (int v = 0; v < (1 << nh); ++v) {
+      HostTensor x = t;
+      for (int hh = nh - 1; hh >= 0; --hh) select_leg(x, half_pos[hh], (v >> hh) & 1);
+      plan.leaf_arena.insert(plan.leaf_arena.end(), x.data.begin(), x.data.end());
+    }
+    plan.leaf_info.push_back(li);
+    VTensor vt;
+    vt.legs = dev_legs;
+    vt.tq = t.tq;
+    vt.P = t.P();
+    vt.ref = Ref{0, (int)plan.leaf_info.size() - 1};
+    plan.vts.push_back(vt);
+  }
+  const int nleaf = (int)plan.leaves.size();
+
+  // order over slots 0..nleaf-1 (result of (i, j) stored at slot i)
+  std::vector<std::pair<int, int>> slot_order;
+  if (in.order) {
+    std::vector<char> alive(nleaf, 1);
+    for (int64_t p = 0; p < in.n_pairs; ++p) {
+      int i = in.order[2 * p], j = in.order[2 * p + 1];
+      if (i < 0 || j < 0 || i >= nleaf || j >= nleaf || i == j || !alive[i] || !alive[j]) {
+        err = "order: pair " + std::to_string(p) + " names a bad or consumed tensor";
+        return TN_ERR_INVALID;
+      }
+      alive[j] = 0;
+      slot_order.push_back({i, j});
+    }
+    // finish with outer products if tensors remain
+    std::vector<int> rest;
+    for (int i = 0; i < nleaf; ++i)
+      if (alive[i]) rest.push_back(i);
+    for (size_t r = 1; r < rest.size(); ++r) slot_order.push_back({rest[0], rest[r]});
+  } else {
+    std::vector<GNode> init(nleaf);
+    for (int i = 0; i < nleaf; ++i) {
+      init[i].legs = plan.vts[i].legs;
+      init[i].tq = plan.vts[i].tq;
+      init[i].lsz = std::log2((double)plan.vts[i].P) + (double)plan.vts[i].legs.size();
+    }
+    rc = greedy_order(plan, init, plan.cap_log2, in.order_trials, in.order_seed, slot_order, err);
+    if (rc) return rc;
+  }
+  // translate slot pairs to virtual-tensor pairs
+  std::vector<int> slot_vt(nleaf);
+  for (int i = 0; i < nleaf; ++i) slot_vt[i] = i;
+  plan.order.clear();
+  std::vector<std::pair<int, int>> vt_pairs;
+  for (auto& pr : slot_order) {
+    vt_pairs.push_back({slot_vt[pr.first], slot_vt[pr.second]});
+    slot_vt[pr.first] = nleaf + (int)vt_pairs.size() - 1;
+  }
+  // keep the user-visible order in slot form
+  std::vector<std::pair<int, int>> saved_slots = slot_order;
+  plan.order = vt_pairs;
+  plan.max_log2 = 0;
+  for (auto& v : plan.vts) plan.max_log2 = std::max(plan.max_log2, std::log2((double)v.P) + (double)v.legs.size());
+  plan.tc_macs = 0;
+  plan.alg_bytes = 0;
+  rc = layout_steps(plan, err);
+  if (rc) return rc;
+  plan.order = saved_slots;
+
+  // final tensor
+  int fvt = nleaf == 1 && slot_order.empty() ? 0 : (int)plan.vts.size() - 1;
+  if (nleaf == 0) { err = "empty network"; return TN_ERR_INVALID; }
+  const VTensor& F = plan.vts[fvt];
+  // the final tensor must carry exactly the open legs and every tail projector
+  for (int l : F.legs)
+    if (plan.legs[l].kind != LEG_OPEN) { err = "internal: final tensor has a non-open leg"; return TN_ERR_INVALID; }
+  if ((int)F.legs.size() != (int)plan.open_qubits.size()) { err = "internal: open legs missing"; return TN_ERR_INVALID; }
+  if (F.tq != plan.tail_mask) { err = "internal: tail projectors missing"; return TN_ERR_INVALID; }
+  plan.fin.ref = F.ref;
+  plan.fin.vt = fvt;
+  plan.fin.rF = (int)F.legs.size();
+  plan.fin.PF = F.P;
+  for (size_t p = 0; p < F.legs.size(); ++p) plan.fin.open_pos[plan.legs[F.legs[p]].open_index] = (int)p;
+  const auto& fp = plan.book.get(plan.tail_mask);
+  plan.n_patterns_final = (int64_t)fp.size();
+  std::vector<uint32_t> pidx(plan.book.tails.size());
+  for (size_t g = 0; g < pidx.size(); ++g) pidx[g] = (uint32_t)pat_index(fp, plan.book.tails[g]);
+  plan.fin.pidx_off = meta_push(plan, pidx);
+  touch(plan, F.ref, (int)plan.steps.size());
+  plan_arena(plan);
+  return TN_OK;
+}
+
+// ------------------------------------------------------------------- describe
+
+std::string describe_plan(const Plan& plan, bool with_data) {
+  std::ostringstream o;
+  o.precision(17);
+  o << "{\"n_qubits\":" << plan.n_qubits << ",\"n_sliced\":" << plan.n_sliced << ",\"n_pinned\":" << plan.n_pinned;
+  o << ",\"tail_mask\":" << plan.tail_mask << ",\"open_mask\":" << plan.open_mask;
+  o << ",\"legs\":[";
+  for (size_t l = 0; l < plan.legs.size(); ++l) {
+    if (l) o << ",";
+    o << "[" << plan.legs[l].kind << "," << plan.legs[l].slice_bit << "," << plan.legs[l].open_index << "]";
+  }
+  o << "],\"leaves\":[";
+  for (size_t i = 0; i < plan.leaves.size(); ++i) {
+    const auto& t = plan.leaves[i];
+    const auto& li = plan.leaf_info[i];
+    if (i) o << ",";
+    o << "{\"legs\":[";
+    for (size_t p = 0; p < t.legs.size(); ++p) o << (p ? "," : "") << t.legs[p];
+    o << "],\"dev_legs\":[";
+    bool first = true;
+    for (int l : plan.vts[i].legs) { o << (first ? "" : ",") << l; first = false; }
+    o << "],\"tq\":" << t.tq << ",\"P\":" << t.P() << ",\"var_slice_bits\":[";
+    for (size_t p = 0; p < li.var_slice_bits.size(); ++p) o << (p ? "," : "") << li.var_slice_bits[p];
+    o << "],\"size\":" << li.size;
+    if (with_data) {
+      o << ",\"re\":[";
+      const int64_t nv = li.size << li.var_slice_bits.size();
+      for (int64_t e = 0; e < nv; ++e) o << (e ? "," : "") << plan.leaf_arena[(size_t)(li.off + e)].real();
+      o << "],\"im\":[";
+      for (int64_t e = 0; e < nv; ++e) o << (e ? "," : "") << plan.leaf_arena[(size_t)(li.off + e)].imag();
+      o << "]";
+    }
+    o << "}";
+  }
+  o << "],\"vts\":[";
+  for (size_t v = 0; v < plan.vts.size(); ++v) {
+    if (v) o << ",";
+    o << "{\"legs\":[";
+    for (size_t p = 0; p < plan.vts[v].legs.size(); ++p) o << (p ? "," : "") << plan.vts[v].legs[p];
+    o << "],\"tq\":" << plan.vts[v].tq << ",\"P\":" << plan.vts[v].P << "}";
+  }
+  o << "],\"order\":[";
+  for (size_t p = 0; p < plan.order.size(); ++p) o << (p ? "," : "") << "[" << plan.order[p].first << "," << plan.order[p].second << "]";
+  o << "],\"steps\":[";
+  for (size_t s = 0; s < plan.steps.size(); ++s) {
+    const Step& st = plan.steps[s];
+    if (s) o << ",";
+    o << "{\"kind\":" << st.kind << ",\"contraction\":" << st.contraction << ",\"vt_a\":" << st.vt_a << ",\"vt_b\":"
+      << st.vt_b << ",\"vt_c\":" << st.vt_c << ",\"nk\":" << st.nk << ",\"nm\":" << st.nm << ",\"nn\":" << st.nn
+      << ",\"PA\":" << st.PA << ",\"PB\":" << st.PB << ",\"PC\":" << st.PC << ",\"macs\":" << st.macs
+      << ",\"bytes\":" << st.bytes << "}";
+  }
+  o << "],\"final\":{\"vt\":" << plan.fin.vt << ",\"open_pos\":[";
+  for (size_t j = 0; j < plan.open_qubits.size(); ++j) o << (j ? "," : "") << plan.fin.open_pos[j];
+  o << "]},\"tc_macs\":" << plan.tc_macs << ",\"alg_bytes\":" << plan.alg_bytes << ",\"max_log2\":" << plan.max_log2
+    << ",\"workspace_bytes\":" << plan.workspace_bytes << "}";
+  return o.str();
+}
+
+}  // namespace tn

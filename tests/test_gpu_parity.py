@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: the complex64 contraction must match the complex128 oracle to
+relative L2 <= 1e-5 over the whole head tensor (and every element to within
+2e-5 of the largest amplitude); integer work (lookup, sampling decisions) is
+bit-exact except where an FP64 prefix sum sits within rounding of a draw.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import circuit_inputs as ci
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2111_03011_gb300 as m
+    return m
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def contract_all(tn, cfg, slice_range=None, **plan_kw):
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], **plan_kw)
+    head = tn.tn_head_create(plan)
+    k = tn.tn_plan_get_stats(plan)["n_sliced"]
+    b, e = slice_range if slice_range else (0, 1 << k)
+    tn.tn_contract_slices(plan, b, e, head)
+    return plan, head
+
+
+def read_head(tn, plan, head, cfg):
+    """All L x 2^h amplitudes through tn_amplitudes (complex128 out)."""
+    tails, oq = cfg["tails"], cfg["open_qubits"]
+    h = len(oq)
+    bits = np.array([O.bitstring_index(int(t), oq, mu) for t in tails for mu in range(1 << h)], dtype=np.uint64)
+    out = tn.tn_amplitudes(head, bits)
+    return out.reshape(len(tails), 1 << h)
+
+
+def oracle_head(cfg, slice_range=None):
+    se = [(g, l) for (g, l, k, v) in cfg["edges"] if k == ci.EDGE_SLICE]
+    pins = [(g, l, v) for (g, l, k, v) in cfg["edges"] if k == ci.EDGE_PIN]
+    psi = O.sliced_statevector(cfg["circuit"], se, pins=pins, slice_range=slice_range)
+    return O.sparse_state_from_vector(psi, cfg["open_qubits"], cfg["tails"])
+
+
+def assert_close(H, ref):
+    assert rel_l2(H, ref) <= REL_L2, rel_l2(H, ref)
+    assert np.abs(H - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+ENGINES = [dict(gemm=0), dict(gemm=2), dict(gemm=0, small_max_bits=-1), dict(gemm=2, small_max_bits=-1),
+           dict(gemm=0, small_max_bits=2)]
+
+
+@pytest.mark.parametrize("eng", ENGINES, ids=["tc", "simt", "tc-allgemm", "simt-allgemm", "tc-small2"])
+def test_tiny_grid_all_amplitudes(tn, eng):
+    """12-qubit 3x4 grid, 8 cycles, all qubits open: every amplitude."""
+    cfg = ci.config_tiny()
+    plan, head = contract_all(tn, cfg, **eng)
+    H = read_head(tn, plan, head, cfg)
+    ref = O.statevector(cfg["circuit"]).reshape(1, -1)
+    assert_close(H, ref)
+
+
+CASES = [dict(r=3, c=4, m=6, seed=5, n_open=4, L=6, cut=1),
+         dict(r=4, c=4, m=8, seed=11, n_open=6, L=8, cut=2),
+         dict(r=2, c=4, m=8, seed=6, n_open=0, L=5, cut=1),
+         dict(r=4, c=5, m=10, seed=13, n_open=8, L=24, cut=2),
+         dict(r=3, c=5, m=12, seed=17, n_open=5, L=64, cut=3)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c['r']}x{c['c']}m{c['m']}L{c['L']}" for c in CASES])
+@pytest.mark.parametrize("eng", ENGINES, ids=["tc", "simt", "tc-allgemm", "simt-allgemm", "tc-small2"])
+def test_sliced_sparse_state_parity(tn, case, eng):
+    cfg = ci.config_small(case["r"], case["c"], case["m"], seed=case["seed"], n_open=case["n_open"], L=case["L"],
+                          n_cut_gates=case["cut"])
+    plan, head = contract_all(tn, cfg, **eng)
+    H = read_head(tn, plan, head, cfg)
+    assert_close(H, oracle_head(cfg))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_generic_two_qubit_gates_all_gemm(tn, seed):
+    """Random (non-symmetric) 2q unitaries on random pairs, both orientations."""
+    c = ci.make_random_2q_circuit(10, 4, seed=seed)
+    twoq = c.two_qubit_gates()
+    oq = [1, 4, 7]
+    tails = ci.draw_tails(10, oq, 16, seed=seed)
+    edges = [(twoq[5], 0, 0, 0), (twoq[9], 1, 0, 0), (twoq[12], 0, 1, 1)]
+    cfg = dict(circuit=c, open_qubits=oq, tails=tails, edges=edges)
+    for eng in (dict(gemm=0, small_max_bits=-1), dict(gemm=0)):
+        plan, head = contract_all(tn, cfg, **eng)
+        H = read_head(tn, plan, head, cfg)
+        assert_close(H, oracle_head(cfg))
+
+
+def test_slice_ranges_additive_and_fidelity(tn):
+    cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)   # 16 slices
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    head = tn.tn_head_create(plan)
+    tn.tn_contract_slices(plan, 0, 4, head)
+    f, done = tn.tn_head_fidelity(head)
+    assert done == 4 and math.isclose(f, 4 / 16)
+    H = read_head(tn, plan, head, cfg)
+    assert_close(H, oracle_head(cfg, (0, 4)))
+    with pytest.raises(tn.TNError):
+        tn.tn_contract_slices(plan, 3, 6, head)          # overlaps [0, 4)
+    tn.tn_contract_slices(plan, 9, 16, head)
+    tn.tn_contract_slices(plan, 4, 9, head)
+    H = read_head(tn, plan, head, cfg)
+    assert_close(H, oracle_head(cfg))
+    with pytest.raises(tn.TNError):
+        tn.tn_contract_slices(plan, 0, 17, head)
+
+
+def test_amplitudes_lookup_dtypes_and_missing(tn):
+    import torch
+    cfg = ci.config_small(3, 4, 6, seed=5, n_open=4, L=6, n_cut_gates=1)
+    plan, head = contract_all(tn, cfg)
+    ref = oracle_head(cfg)
+    rng = np.random.default_rng(0)
+    g = rng.integers(0, 6, 100)
+    mu = rng.integers(0, 16, 100)
+    bits = np.array([O.bitstring_index(int(cfg["tails"][a]), cfg["open_qubits"], int(b)) for a, b in zip(g, mu)],
+                    dtype=np.uint64)
+    out128 = tn.tn_amplitudes(head, bits, dtype=tn.TN_C128)
+    out64 = tn.tn_amplitudes(head, bits, dtype=tn.TN_C64)
+    exp = ref[g, mu]
+    assert np.abs(out128 - exp).max() <= 2e-5 * np.abs(ref).max()
+    assert np.array_equal(out64, out128.astype(np.complex64))
+    # device input and output
+    dbits = torch.from_numpy(bits.view(np.int64)).cuda()
+    dout = torch.zeros(100, dtype=torch.complex128, device="cuda")
+    tn.tn_amplitudes(head, dbits, out=dout, dtype=tn.TN_C128)
+    assert np.array_equal(dout.cpu().numpy(), out128)
+    # a bitstring outside the sparse state
+    bad = bits.copy()
+    all_tails = set(int(t) for t in cfg["tails"])
+    x = 0
+    while (x & ~sum(1 << q for q in cfg["open_qubits"])) in all_tails:
+        x += 1
+    bad[37] = x
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_amplitudes(head, bad)
+    assert e.value.code == tn.TN_ERR_NOT_IN_STATE and "37" in str(e.value)
+
+
+def _synthetic_head(tn, L, h, seed, n_qubits=30):
+    import torch
+    oq = list(range(n_qubits - h, n_qubits))
+    tails = ci.draw_tails(n_qubits, oq, L, seed=seed)
+    c = ci.make_grid_circuit(2, 2, 1, seed=1)       # plan only carries the sparse-state layout here
+    c.n_qubits = n_qubits
+    plan = tn.tn_plan(c, oq, tails)
+    H = ci.synthetic_head(L, h, seed)
+    buf = torch.from_numpy(H.copy()).cuda()
+    head = tn.tn_head_create(plan, buf)              # zeroes the buffer
+    buf.copy_(torch.from_numpy(H))
+    torch.cuda.synchronize()
+    return plan, head, buf, H, tails, oq
+
+
+def test_norms_fp64(tn):
+    plan, head, buf, H, tails, oq = _synthetic_head(tn, 64, 10, seed=3)
+    N, Z = tn.tn_head_norm(head, with_groups=True)
+    w = np.abs(H) ** 2
+    assert abs(N - w.sum()) <= 1e-12 * w.sum()
+    assert np.allclose(Z, w.sum(axis=1), rtol=1e-13, atol=0)
+
+
+def _match_with_boundaries(s_gpu, s_ref, H, tails, oq, seed, n):
+    """Samples must agree; a disagreement is allowed only where the draw lies
+    within 1e-12 (relative) of the boundary between the two members."""
+    bad = np.nonzero(s_gpu != s_ref)[0]
+    L = H.shape[0]
+    for i in bad:
+        g = i % L
+        w = np.abs(H[g]) ** 2
+        cdf = np.cumsum(w)
+        r = O.philox4x32_10((i & 0xFFFFFFFF, i >> 32, 0, 0), (seed & 0xFFFFFFFF, seed >> 32))
+        u = (((r[3] << 32) | r[2]) >> 11) * 2.0 ** -53
+        t = u * cdf[-1]
+        assert np.min(np.abs(cdf - t)) <= 1e-12 * cdf[-1], (i, s_gpu[i], s_ref[i])
+    return len(bad)
+
+
+@pytest.mark.parametrize("L,h,n", [(64, 10, 64), (64, 10, 1000), (300, 6, 300), (1, 12, 5000)])
+def test_sampler_matches_oracle(tn, L, h, n):
+    plan, head, buf, H, tails, oq = _synthetic_head(tn, L, h, seed=L + h)
+    seed = 0x1234_5678_9ABC
+    s = tn.tn_sample(head, n, 0.0, seed)
+    ref = O.sample_groups(H, tails, oq, 30, n, 0.0, 1.0, seed)
+    assert _match_with_boundaries(s, ref, H, tails, oq, seed, n) <= 1
+
+
+def test_sampler_uniform_mixing_matches_oracle(tn):
+    plan, head, buf, H, tails, oq = _synthetic_head(tn, 64, 10, seed=9)
+    tn.tn_head_set_fidelity(head, 0.5)
+    seed = 77
+    s = tn.tn_sample(head, 4000, 0.2, seed)
+    ref = O.sample_groups(H, tails, oq, 30, 4000, 0.2, 0.5, seed)
+    assert _match_with_boundaries(s, ref, H, tails, oq, seed, 4000) <= 1
+    with pytest.raises(tn.TNError):
+        tn.tn_sample(head, 10, 0.9, 1)
+
+
+def test_tiny_grid_sampling_xeb(tn):
+    """10^4 samples of the exact 12-qubit state: XEB within 3 sigma of the
+    exact expectation 2^n sum P^2 - 1 (validation section's XEB)."""
+    cfg = ci.config_tiny()
+    plan, head = contract_all(tn, cfg)
+    f, done = tn.tn_head_fidelity(head)
+    assert f == 1.0 and done == 1
+    s = tn.tn_sample(head, cfg["n_samples"], 0.0, cfg["sample_seed"])
+    psi = O.statevector(cfg["circuit"])
+    P = np.abs(psi) ** 2
+    x = 2 ** 12 * P[s.astype(np.int64)]
+    expect = 2 ** 12 * (P * P).sum() - 1
+    assert abs(x.mean() - 1 - expect) < 3 * x.std() / math.sqrt(x.size)
+
+
+def test_sliced30_full_size_properties(tn):
+    """The 30-qubit, 14-cycle, 64-slice workload at full size: the exact sparse
+    state (all slices) is normalised like a Porter-Thomas sample (E|psi|^2 =
+    2^-n), the partial sums track the kept fraction, and amplitudes are
+    consistent between the tensor-core and CUDA-core engines."""
+    cfg = ci.config_sliced30()
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], order_trials=512)
+    head = tn.tn_head_create(plan)
+    tn.tn_contract_slices(plan, 0, 16, head)
+    N16 = tn.tn_head_norm(head)
+    tn.tn_contract_slices(plan, 16, 64, head)
+    N = tn.tn_head_norm(head)
+    l = 2 ** 10 * 64
+    x = N * 2 ** 30 / l
+    assert 0.9 < x < 1.1, x
+    assert 0.15 < N16 / N < 0.4
+    H = read_head(tn, plan, head, cfg)
+    p = np.abs(H) ** 2 * 2 ** 30
+    assert O.porter_thomas_ks(p / p.mean()) < 0.02

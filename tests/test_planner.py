@@ -1,0 +1,156 @@
+"""Host planner (no GPU): the plan replayed on the CPU matches the oracle.
+
+The library is built for sm_103a and loaded; plans are made host_only, so no
+device call is made.
+"""
+import numpy as np
+import pytest
+
+import circuit_inputs as ci
+import oracle as O
+from tests.plan_emulator import emulate
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import paper_2111_03011_gb300 as m
+    return m
+
+
+def _edges(cfg):
+    return [(g, l, k, v) for (g, l, k, v) in cfg["edges"]]
+
+
+def _oracle_H(cfg, slice_range=None, pins=()):
+    se = [(g, l) for (g, l, k, v) in cfg["edges"] if k == 0]
+    psi = O.sliced_statevector(cfg["circuit"], se, pins=pins, slice_range=slice_range)
+    return O.sparse_state_from_vector(psi, cfg["open_qubits"], cfg["tails"])
+
+
+def test_library_exports_every_declared_symbol(tn):
+    import re
+    import os
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "tn_gb300.h")).read()
+    declared = set(re.findall(r"\b(tn_[a-z_]+)\s*\(", hdr))
+    for name in declared:
+        assert hasattr(tn.lib, name), name
+    assert declared == set(tn.EXPORTED)
+
+
+@pytest.mark.parametrize("case", [
+    dict(r=3, c=4, m=6, seed=5, n_open=4, L=6, cut=1),
+    dict(r=3, c=3, m=8, seed=8, n_open=9, L=1, cut=0),
+    dict(r=2, c=4, m=8, seed=6, n_open=0, L=5, cut=1),
+    dict(r=4, c=4, m=8, seed=11, n_open=6, L=8, cut=2),
+])
+@pytest.mark.parametrize("absorb", [0, 2])
+def test_plan_replay_matches_oracle(tn, case, absorb):
+    cfg = ci.config_small(case["r"], case["c"], case["m"], seed=case["seed"], n_open=case["n_open"],
+                          L=case["L"], n_cut_gates=case["cut"])
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True,
+                      max_host_absorb_log2=absorb)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    k = d["n_sliced"]
+    H = emulate(d, cfg["tails"], cfg["open_qubits"], range(1 << k))
+    ref = _oracle_H(cfg)
+    assert np.abs(H - ref).max() < 1e-12
+    st = tn.tn_plan_get_stats(plan)
+    assert st["n_sliced"] == k and st["n_tails"] == case["L"]
+    assert st["tc_macs"] > 0 or st["n_contractions"] == 0
+
+
+def test_slice_range_and_pins_replay(tn):
+    c = ci.make_grid_circuit(3, 4, 8, seed=2)
+    cut = ci.mid_circuit_cut_edges(c, 2)            # 4 edges on 2 gates
+    open_q = [8, 9, 10, 11]
+    tails = ci.draw_tails(12, open_q, 4, seed=3)
+    edges = [cut[0], cut[1], (cut[2][0], cut[2][1], tn.TN_EDGE_PIN, 1), (cut[3][0], cut[3][1], tn.TN_EDGE_PIN, 0)]
+    plan = tn.tn_plan(c, open_q, tails, edges, host_only=True)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    assert d["n_sliced"] == 2 and d["n_pinned"] == 2
+    H = emulate(d, tails, open_q, [1, 2])
+    psi = O.sliced_statevector(c, [(cut[0][0], cut[0][1]), (cut[1][0], cut[1][1])],
+                               pins=[(cut[2][0], cut[2][1], 1), (cut[3][0], cut[3][1], 0)], slice_range=(1, 3))
+    ref = O.sparse_state_from_vector(psi, open_q, tails)
+    assert np.abs(H - ref).max() < 1e-13
+
+
+def test_hole_is_removed_exactly(tn):
+    """Both inputs of an fSim pinned to 0: the host splits the rank-one
+    remainder into two vectors (Method case (i)); the result is exact."""
+    c = ci.make_grid_circuit(3, 3, 6, seed=12)
+    gi = ci.mid_circuit_cut_edges(c, 1)[0][0]
+    edges = [(gi, 0, tn.TN_EDGE_PIN, 0), (gi, 1, tn.TN_EDGE_PIN, 0)]
+    open_q = list(range(9))
+    tails = np.zeros(1, np.uint64)
+    plan = tn.tn_plan(c, open_q, tails, edges, host_only=True)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    H = emulate(d, tails, open_q, [0])
+    psi = O.statevector(c, [(gi, 0, 0), (gi, 1, 0)])
+    assert np.abs(H[0] - psi).max() < 1e-13
+
+
+def test_user_order_roundtrip_and_random_order(tn):
+    cfg = ci.config_small(3, 4, 6, seed=5, n_open=4, L=6, n_cut_gates=1)
+    p1 = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True)
+    order = tn.tn_plan_order(p1)
+    p2 = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), order=order, host_only=True)
+    assert (tn.tn_plan_order(p2) == order).all()
+    d1 = tn.tn_plan_describe(p1)
+    n_leaves = len(d1["leaves"])
+    # a different valid order: contract leaf 0 with every other leaf in turn
+    o = np.array([[0, j] for j in range(1, n_leaves)], dtype=np.int32)
+    p3 = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), order=o, host_only=True,
+                    max_log2_elements=30)
+    d3 = tn.tn_plan_describe(p3, with_data=True)
+    H = emulate(d3, cfg["tails"], cfg["open_qubits"], range(4))
+    assert np.abs(H - _oracle_H(cfg)).max() < 1e-12
+    with pytest.raises(tn.TNError):
+        tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), order=[[0, 0]], host_only=True)
+
+
+def test_sparse_state_worked_example_patterns(tn):
+    """Supplement worked example: targets {111, 010, 000}; merging the final
+    legs of qubits 2 and 3 (0-based 1 and 2) keeps the 3 patterns {11, 10, 00}."""
+    import json, os
+    ex = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))["sparse_state_example"]
+    c = ci.make_random_2q_circuit(3, 2, seed=1)
+    tails = np.array([int(t[::-1], 2) for t in ex["targets"]], dtype=np.uint64)
+    plan0 = tn.tn_plan(c, [], tails, host_only=True, max_host_absorb_log2=1)
+    d0 = tn.tn_plan_describe(plan0)
+    ids = {lf["tq"]: i for i, lf in enumerate(d0["leaves"]) if lf["tq"] in (2, 4)}
+    assert set(ids) == {2, 4}
+    plan = tn.tn_plan(c, [], tails, order=[[ids[2], ids[4]]], host_only=True, max_host_absorb_log2=1)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    merged = [v for v in d["vts"] if v["tq"] == 6]
+    assert merged and merged[0]["P"] == 3
+    pats = sorted(set(int(t) & 6 for t in tails))
+    assert [format(p >> 1, "02b")[::-1] for p in pats] == sorted(ex["unique_patterns"], key=lambda s: int(s[::-1], 2))
+    H = emulate(d, tails, [], [0])
+    psi = O.statevector(c)
+    assert np.abs(H[:, 0] - psi[tails.astype(np.int64)]).max() < 1e-13
+
+
+def test_invalid_inputs_rejected(tn):
+    c = ci.make_grid_circuit(2, 2, 2, seed=1)
+    t = np.zeros(1, np.uint64)
+    for kw in [dict(open_qubits=[5]), dict(open_qubits=[0, 0])]:
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_plan(c, kw["open_qubits"], t, host_only=True)
+        assert e.value.code == tn.TN_ERR_INVALID
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(c, [0], t, [(0, 0, 0, 0), (0, 0, 0, 0)], host_only=True)
+    assert e.value.code == tn.TN_ERR_INVALID
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(c, [0], t, [(4, 1, tn.TN_EDGE_COMPANION, 0)], host_only=True)
+    assert e.value.code == tn.TN_ERR_UNSUPPORTED
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(c, [0], np.zeros(0, np.uint64), host_only=True)
+    assert e.value.code == tn.TN_ERR_INVALID
+
+
+def test_size_cap_enforced(tn):
+    cfg = ci.config_small(4, 4, 8, seed=11, n_open=16, L=1, n_cut_gates=0)
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], host_only=True, max_log2_elements=10)
+    assert e.value.code == tn.TN_ERR_OOM
