@@ -1,0 +1,362 @@
+"""Benchmark of the sliced sparse-state contraction + sampling on GB300.
+
+One step = the whole hot path over one batch: contract every kept slice of the
+workload into the head tensor (FP64 accumulation), look up all L x 2^h
+amplitudes, normalise (FP64 norms) and draw one sample per group.
+
+Workload (default): 30-qubit 5x6 grid, 14 cycles, seeded Sycamore-like gates,
+10 open qubits x 64 tails = 65,536 amplitudes, 6 sliced edges (2^6 slices, all
+summed), largest intermediate <= 2^28 elements.  Synthetic inputs (the paper's
+circuit files are not used).
+
+Prints one JSON line (rank 0).  `value` is slice TFLOP/s = 8 T_c(slice) x
+slices / step time (the paper's efficiency convention, 8 real flops per
+complex multiply-add, T_c the plan's algorithmic count), device-resident
+inputs; `e2e` is the same metric through the C ABI with host buffers.
+`--impl reference` times the CPU oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import circuit_inputs as ci  # noqa: E402
+
+KIND_NAMES = {0: "small_operand", 1: "permute", 2: "bprep_tc", 3: "gemm_tc_3xtf32", 4: "bprep_simt",
+              5: "gemm_simt_fp32", -1: "accumulate"}
+ORDER_TRIALS = 512
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _workload(name):
+    if name == "sliced30":
+        return ci.config_sliced30()
+    if name == "tiny":
+        return ci.config_tiny()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return None
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        if not sm:
+            return None
+        mx = float(rows[0][2])
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2111_03011_gb300 as tn
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cfg = _workload(args.workload)
+    gemm = {"tc": tn.TN_GEMM_TC_3XTF32, "simt": tn.TN_GEMM_SIMT_FP32}[args.engine]
+    t0 = time.time()
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=gemm,
+                      order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0)
+    plan_s = time.time() - t0
+    st = tn.tn_plan_get_stats(plan)
+    k = st["n_sliced"]
+    n_slices = 1 << k
+    if args.slices:
+        n_slices = min(n_slices, args.slices)     # profiling runs only: fewer launches per step
+    L, h = int(st["n_tails"]), int(st["n_open"])
+    n_amp = L << h
+    n_samples = L
+    oq, tails = cfg["open_qubits"], cfg["tails"]
+    mask = 0
+    for q in oq:
+        mask |= 1 << q
+    base = (tails.astype(np.uint64) & np.uint64(~mask & ((1 << 64) - 1)))
+    mu = np.arange(1 << h, dtype=np.uint64)
+    dep = np.zeros(1 << h, dtype=np.uint64)
+    for j, q in enumerate(oq):
+        dep |= ((mu >> np.uint64(j)) & np.uint64(1)) << np.uint64(q)
+    bits_host = (base[:, None] | dep[None, :]).reshape(-1)
+    bits_pinned = torch.from_numpy(bits_host.view(np.int64)).pin_memory()
+    bits_dev = bits_pinned.to(dev)
+    amp_dev = torch.empty(n_amp, dtype=torch.complex128, device=dev)
+    smp_dev = torch.empty(n_samples, dtype=torch.int64, device=dev)
+    amp_host = torch.empty(n_amp, dtype=torch.complex128).pin_memory()
+    smp_host = torch.empty(n_samples, dtype=torch.int64).pin_memory()
+    head = tn.tn_head_create(plan)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    n_launch = int(st["n_launches"])
+    step_ms_acc = np.zeros(n_launch)
+
+    def step(host_io, profile):
+        tn.tn_head_reset(head, stream)
+        if profile:
+            step_ms_acc[:] += tn.tn_profile_slices(plan, 0, n_slices, head, stream)
+        else:
+            tn.tn_contract_slices(plan, 0, n_slices, head, stream)
+        if host_io:
+            tn.tn_amplitudes(head, bits_pinned, out=amp_host, dtype=tn.TN_C128, stream=stream)
+            tn.tn_head_norm(head, stream=stream)
+            tn.tn_sample(head, n_samples, 0.0, 12345, out=smp_host, stream=stream)
+        else:
+            tn.tn_amplitudes(head, bits_dev, out=amp_dev, dtype=tn.TN_C128, stream=stream)
+            tn.tn_head_norm(head, stream=stream)
+            tn.tn_sample(head, n_samples, 0.0, 12345, out=smp_dev, stream=stream)
+
+    def timed(host_io, profile):
+        for _ in range(args.warmup):
+            step(host_io, False)
+        torch.cuda.synchronize(dev)
+        _barrier(ws)
+        torch.cuda.synchronize(dev)
+        total = 0.0
+        for _ in range(args.steps):
+            flush.zero_()                       # L2 flush between timed iterations (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(host_io, profile)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        torch.cuda.synchronize(dev)
+        _barrier(ws)
+        return _max(ws, total / args.steps)
+
+    with Clocks(local) as clk:
+        ms = timed(False, True)
+    ms_e2e = timed(True, False)
+    clocks = clk.summary()
+
+    flops_step = 8.0 * st["tc_macs"] * n_slices
+    value = ws * flops_step / (ms * 1e-3) / 1e12
+    e2e = ws * flops_step / (ms_e2e * 1e-3) / 1e12
+    peaks, peak_src = _peaks()
+    # dominant launch over the timed steps
+    per_launch = step_ms_acc / args.steps / n_slices      # ms per launch (per slice)
+    i_dom = int(np.argmax(per_launch))
+    kind, macs, abytes = tn.tn_plan_step_info(plan, i_dom)
+    t_dom = per_launch[i_dom] * 1e-3
+    kind_totals = {}
+    for i in range(n_launch):
+        kk, _, _ = tn.tn_plan_step_info(plan, i)
+        kind_totals[KIND_NAMES[kk]] = kind_totals.get(KIND_NAMES[kk], 0.0) + per_launch[i]
+    tot = sum(kind_totals.values())
+    if kind in (3,):
+        tf32 = peaks["bf16_tflops_sustained"] * (1.1 / 2.25)
+        peak = tf32 / 3.0
+        achieved = 8.0 * macs / t_dom / 1e12
+        roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": KIND_NAMES[kind],
+                "peak_note": f"{peak_src} sustained bf16 x 1.1/2.25 (tf32) / 3 (3xTF32 issues 3 MMAs per product)"}
+    elif kind == 5:
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        achieved = 8.0 * macs / t_dom / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": KIND_NAMES[kind],
+                "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    else:
+        peak = peaks["hbm_gbs"]
+        achieved = abytes / t_dom / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": KIND_NAMES[kind],
+                "peak_note": f"{peak_src} hbm_gbs"}
+    roof["dominant_launch_ms"] = round(per_launch[i_dom], 4)
+    roof["kernel_time_share"] = {k2: round(v / tot, 4) for k2, v in sorted(kind_totals.items(), key=lambda x: -x[1])}
+
+    out = {
+        "metric": "slice TFLOP/s",
+        "value": round(value, 3),
+        "unit": "TFLOP/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64",
+        "data": "synthetic (seeded Sycamore-like circuit; paper's circuit files not used)",
+        "config": {"workload": cfg["name"], "qubits": st["n_qubits"], "cycles": cfg["circuit"].cycles,
+                   "open_qubits": h, "groups": L, "amplitudes": n_amp, "sliced_edges": k, "slices": n_slices,
+                   "max_log2_elements": round(st["max_log2_elements"], 2), "gemm_engine": args.engine,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "flushed between timed steps (512 MiB write); intermediates up to 2 GiB exceed L2",
+                   "plan_seconds": round(plan_s, 2), "order_trials": ORDER_TRIALS,
+                   "partial_slices_for_profiling": bool(args.slices)},
+        "amplitudes_per_s": round(ws * n_amp / (ms * 1e-3), 1),
+        "slices_per_s": round(ws * n_slices / (ms * 1e-3), 2),
+        "tc_macs_per_slice": st["tc_macs"],
+        "alg_bytes_per_slice": st["alg_bytes"],
+        "e2e": {"value": round(e2e, 3), "unit": "TFLOP/s", "ms_per_step": round(ms_e2e, 3),
+                "h2d_bytes_per_step": int(n_amp * 8), "d2h_bytes_per_step": int(n_amp * 16 + n_samples * 8 + 8)},
+        "gpu_launches": int(args.steps * (n_slices * n_launch + 4)),
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, st)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(cfg, st, repeats=1):
+    """The oracle (O2 tensordot contraction) on one group of one slice of the
+    same workload; scaled to slice TFLOP/s with the plan's algorithmic flops
+    per (slice, group)."""
+    import oracle as O
+    se = [(g, l) for (g, l, k, v) in cfg["edges"] if k == ci.EDGE_SLICE]
+    t0 = time.time()
+    for r in range(repeats):
+        O.network_amplitudes(cfg["circuit"], cfg["open_qubits"], cfg["tails"], se, slice_range=(r, r + 1),
+                             groups=[r])
+    dt = (time.time() - t0) / repeats
+    L = int(st["n_tails"])
+    flops_unit = 8.0 * st["tc_macs"] / L
+    return {"value": round(flops_unit / dt / 1e12, 6), "unit": "TFLOP/s", "cores": os.cpu_count(),
+            "kind": "oracle", "seconds_per_unit": round(dt, 2),
+            "sample": f"one group x one slice ({1 << len(cfg['open_qubits'])} amplitude contributions) of "
+                      f"{cfg['name']}, complex128 numpy tensordot; flops = plan T_c per slice / L groups"}
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import paper_2111_03011_gb300 as tn
+    cfg = _workload(args.workload)
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True,
+                      order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0)
+    st = tn.tn_plan_get_stats(plan)
+    import oracle as O
+    se = [(g, l) for (g, l, k, v) in cfg["edges"] if k == ci.EDGE_SLICE]
+    L = int(st["n_tails"])
+    k = len(se)
+
+    def unit(i):
+        O.network_amplitudes(cfg["circuit"], cfg["open_qubits"], cfg["tails"], se,
+                             slice_range=(i % (1 << k), i % (1 << k) + 1), groups=[i % L])
+
+    for i in range(args.warmup):
+        unit(i)
+    t0 = time.time()
+    for i in range(args.steps):
+        unit(args.warmup + i)
+    dt = (time.time() - t0) / args.steps
+    v = 8.0 * st["tc_macs"] / L / dt / 1e12
+    sample = (f"one group x one slice of {cfg['name']} per step (complex128 numpy tensordot); "
+              f"flops = plan T_c per slice / L groups")
+    out = {"impl": "reference", "metric": "slice TFLOP/s", "value": round(v, 6), "unit": "TFLOP/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic", "config": {"workload": cfg["name"]},
+           "cpu_baseline": {"value": round(v, 6), "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(v, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sliced30", choices=["sliced30", "tiny"])
+    ap.add_argument("--engine", default="tc", choices=["tc", "simt"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="contract only the first N slices per step (for ncu launch lists; not a bench number)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -132,6 +132,8 @@ const char* tn_plan_describe(tn_plan_t* plan, int with_data);
 int  tn_head_create(tn_plan_t* plan, void* dev_c128, tn_head_t** out);
 void tn_head_free(tn_head_t* head);
 void* tn_head_data(tn_head_t* head);  /* device pointer of H */
+/* Zero H (asynchronously on `stream`) and forget the accumulated slices. */
+int  tn_head_reset(tn_head_t* head, void* stream);
 /* F_est = 2^-n_pinned * slices_done / 2^k (fidelity-estimate equation). */
 int  tn_head_fidelity(const tn_head_t* head, double* f_est, int64_t* slices_done);
 /* Override F_est for a head filled by the caller (not by contraction). */
@@ -162,6 +164,18 @@ int  tn_sample(tn_head_t* head, int64_t n, double target_fidelity, uint64_t seed
 /* Squared norm N = sum |H|^2 (FP64) and, if group_norms != NULL, the L
  * per-group sums (host memory).  Synchronises `stream`. */
 int  tn_head_norm(tn_head_t* head, double* norm, double* group_norms, void* stream);
+
+/* Tracing: like tn_contract_slices, but times every launch with CUDA events
+ * on `stream` (synchronising after each slice) and returns in step_ms[i] the
+ * summed milliseconds of launch i over the range (i < n_launches of
+ * tn_plan_stats; the last entry is the slice accumulation).  Accumulates
+ * into the head like tn_contract_slices. */
+int  tn_profile_slices(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, void* stream,
+                       double* step_ms, int64_t n_entries);
+/* Kind (tn step kind: 0 small-operand, 1 permute, 2 B prep (tensor core),
+ * 3 tensor-core GEMM, 4 B prep (SIMT), 5 SIMT GEMM, -1 accumulation) and the
+ * algorithmic complex multiply-adds and HBM bytes of launch i of one slice. */
+int  tn_plan_step_info(const tn_plan_t* plan, int64_t i, int* kind, double* macs, double* bytes);
 
 const char* tn_last_error(void);
 const char* tn_version(void);

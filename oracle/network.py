@@ -5,8 +5,8 @@ Test infrastructure (see the package docstring); never imported by the library.
 Builds the network of the Method section from scratch -- |0> vectors on the
 initial boundary, a matrix per single-qubit gate, a four-way tensor per
 two-qubit gate -- with every cut edge (value v) replaced by the projector
-|v><v| inserted on that wire (the edge-breaking matrix E of the Method
-section).  The final boundary of one group is the product of basis vectors
+|v><v| on that wire, written as the pair of vectors <v| and |v> (the
+edge-breaking insertion E = (1,0) x (1,0) of the Method section for v = 0).  The final boundary of one group is the product of basis vectors
 |tail bit> on the tail qubits, with the open qubits' final wires left open:
 the batch contraction of the Supplement's simulation taxonomy, run once per
 group, which is the plain definition the sparse-state contraction has to
@@ -51,11 +51,14 @@ def _build(circ, cuts, open_qubits, tail):
         by_gate.setdefault(int(g), []).append((int(leg), int(v)))
     for gi, gate in enumerate(circ.gates):
         for (leg, v) in by_gate.get(gi, ()):
+            # |v><v| on the wire written as its two factors: the wire ends in
+            # <v| and a fresh wire starts from |v> (E = (1,0) x (1,0) for v = 0)
             q = gate.q0 if leg == 0 else gate.q1
-            P = np.zeros((2, 2))
-            P[v, v] = 1.0
+            vec = np.zeros(2)
+            vec[v] = 1.0
+            net.add(vec, [wire[q]])
             e = net.label()
-            net.add(P, [e, wire[q]])               # [out, in]
+            net.add(vec.copy(), [e])
             wire[q] = e
         if gate.arity == 1:
             e = net.label()

@@ -89,16 +89,20 @@ def _load():
     lib.tn_head_free.restype = None
     lib.tn_head_data.argtypes = [vp]
     lib.tn_head_data.restype = vp
+    lib.tn_head_reset.argtypes = [vp, vp]
     lib.tn_head_fidelity.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64)]
     lib.tn_head_set_fidelity.argtypes = [vp, C.c_double]
     lib.tn_contract_slices.argtypes = [vp, tn_range, vp, vp]
     lib.tn_amplitudes.argtypes = [vp, vp, i64, vp, C.c_int, vp]
     lib.tn_sample.argtypes = [vp, i64, C.c_double, C.c_uint64, vp, vp]
     lib.tn_head_norm.argtypes = [vp, C.POINTER(C.c_double), vp, vp]
+    lib.tn_profile_slices.argtypes = [vp, tn_range, vp, vp, C.POINTER(C.c_double), i64]
+    lib.tn_plan_step_info.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.tn_last_error.restype = C.c_char_p
     lib.tn_version.restype = C.c_char_p
     for name in ("tn_plan", "tn_plan_get_stats", "tn_plan_order", "tn_head_create", "tn_head_fidelity",
-                 "tn_head_set_fidelity", "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm"):
+                 "tn_head_set_fidelity", "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm",
+                 "tn_profile_slices", "tn_plan_step_info", "tn_head_reset"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -107,8 +111,9 @@ _lib = _load()
 lib = _lib
 
 EXPORTED = ["tn_plan", "tn_plan_free", "tn_plan_get_stats", "tn_plan_order", "tn_plan_describe",
-            "tn_head_create", "tn_head_free", "tn_head_data", "tn_head_fidelity", "tn_head_set_fidelity",
-            "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm", "tn_last_error", "tn_version"]
+            "tn_head_create", "tn_head_free", "tn_head_data", "tn_head_reset", "tn_head_fidelity", "tn_head_set_fidelity",
+            "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm", "tn_profile_slices",
+            "tn_plan_step_info", "tn_last_error", "tn_version"]
 
 
 def _check(rc):
@@ -236,6 +241,10 @@ def tn_head_data(head: Head) -> int:
     return _lib.tn_head_data(head.handle)
 
 
+def tn_head_reset(head: Head, stream=None):
+    _check(_lib.tn_head_reset(head.handle, _stream(stream)))
+
+
 def tn_head_fidelity(head: Head):
     f = C.c_double()
     n = C.c_int64()
@@ -276,6 +285,24 @@ def tn_head_norm(head: Head, with_groups=False, stream=None):
     Z = np.zeros(L, dtype=np.float64) if with_groups else None
     _check(_lib.tn_head_norm(head.handle, C.byref(N), _ptr(Z) if Z is not None else None, _stream(stream)))
     return (N.value, Z) if with_groups else N.value
+
+
+def tn_profile_slices(plan: Plan, begin: int, end: int, head: Head, stream=None) -> np.ndarray:
+    """Contract [begin, end) into head, returning summed ms per launch."""
+    n = int(tn_plan_get_stats(plan)["n_launches"])
+    ms = np.zeros(n, dtype=np.float64)
+    _check(_lib.tn_profile_slices(plan.handle, tn_range(int(begin), int(end)), head.handle, _stream(stream),
+                                  ms.ctypes.data_as(C.POINTER(C.c_double)), n))
+    return ms
+
+
+def tn_plan_step_info(plan: Plan, i: int):
+    """(kind, algorithmic complex MACs, algorithmic HBM bytes) of launch i."""
+    k = C.c_int()
+    m = C.c_double()
+    b = C.c_double()
+    _check(_lib.tn_plan_step_info(plan.handle, int(i), C.byref(k), C.byref(m), C.byref(b)))
+    return k.value, m.value, b.value
 
 
 def tn_last_error() -> str:

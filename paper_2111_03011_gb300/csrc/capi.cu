@@ -292,6 +292,16 @@ extern "C" void tn_head_free(tn_head_t* h) {
 
 extern "C" void* tn_head_data(tn_head_t* h) { return h ? (void*)h->H : nullptr; }
 
+extern "C" int tn_head_reset(tn_head_t* h, void* stream) {
+  if (!h) return fail(TN_ERR_INVALID, "NULL head");
+  const int64_t elems = (int64_t)h->plan->P.tails_raw.size() << h->plan->P.open_qubits.size();
+  CUDA_TRY(cudaMemsetAsync(h->H, 0, (size_t)elems * sizeof(double2), (cudaStream_t)stream));
+  h->done.clear();
+  h->slices_done = 0;
+  h->f_override = false;
+  return TN_OK;
+}
+
 extern "C" int tn_head_fidelity(const tn_head_t* h, double* f_est, int64_t* slices_done) {
   if (!h) return fail(TN_ERR_INVALID, "NULL head");
   const tn::Plan& P = h->plan->P;
@@ -325,10 +335,12 @@ static inline float2* buf_ptr(const tn_plan_t* p, const tn::Ref& r) {
   return (float2*)(p->d_arena + p->P.bufs[r.id].off);
 }
 
-static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st) {
+static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const tn::Plan& P = p->P;
+  int si = 0;
   for (const tn::Step& x : P.steps) {
     cudaError_t e = cudaSuccess;
+    if (ev) cudaEventRecord(ev[2 * si], st);
     switch (x.kind) {
       case tn::ST_SMALL: {
         tn::SmallParams sp;
@@ -404,7 +416,10 @@ static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st) {
         return fail(TN_ERR_INVALID, "internal: unknown step kind");
     }
     if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    if (ev) cudaEventRecord(ev[2 * si + 1], st);
+    ++si;
   }
+  if (ev) cudaEventRecord(ev[2 * si], st);
   tn::AccumParams ap;
   ap.F = ref_ptr(p, P.fin.ref, s);
   ap.H = H;
@@ -415,30 +430,89 @@ static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st) {
   for (int j = 0; j < ap.h && j < 32; ++j) ap.open_pos[j] = P.fin.open_pos[j];
   cudaError_t e = tn::launch_accum(ap, st);
   if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("accumulate launch: ") + cudaGetErrorString(e));
+  if (ev) cudaEventRecord(ev[2 * si + 1], st);
+  return TN_OK;
+}
+
+static int check_range(tn_plan_t* plan, tn_range r, tn_head_t* head) {
+  if (!plan || !head) return fail(TN_ERR_INVALID, "NULL argument");
+  if (head->plan != plan) return fail(TN_ERR_INVALID, "head belongs to another plan");
+  if (!plan->on_device) return fail(TN_ERR_INVALID, "plan was made host_only");
+  const int64_t ns = 1LL << plan->P.n_sliced;
+  if (r.begin < 0 || r.end > ns || r.begin > r.end) return fail(TN_ERR_INVALID, "slice range outside [0, 2^k)");
+  auto it = head->done.upper_bound(r.begin);
+  if (it != head->done.begin()) {
+    auto pv = std::prev(it);
+    if (pv->second > r.begin && r.begin < r.end)
+      return fail(TN_ERR_INVALID, "slice range overlaps slices already accumulated");
+  }
+  if (it != head->done.end() && it->first < r.end)
+    return fail(TN_ERR_INVALID, "slice range overlaps slices already accumulated");
+  return TN_OK;
+}
+
+static void mark_done(tn_head_t* head, tn_range r) {
+  head->done[r.begin] = r.end;
+  head->slices_done += r.end - r.begin;
+}
+
+extern "C" int tn_profile_slices(tn_plan_t* plan, tn_range r, tn_head_t* head, void* stream, double* step_ms,
+                                 int64_t n_entries) {
+  int rc = check_range(plan, r, head);
+  if (rc) return rc;
+  const int64_t ns = (int64_t)plan->P.steps.size() + 1;
+  if (!step_ms || n_entries < ns) return fail(TN_ERR_INVALID, "step_ms needs n_launches entries");
+  for (int64_t i = 0; i < ns; ++i) step_ms[i] = 0.0;
+  if (r.begin == r.end) return TN_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<cudaEvent_t> ev(2 * ns);
+  for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+  int status = TN_OK;
+  for (int64_t s = r.begin; s < r.end && status == TN_OK; ++s) {
+    status = run_slice(plan, s, head->H, st, ev.data());
+    if (status) break;
+    cudaError_t e = cudaEventSynchronize(ev[2 * ns - 1]);
+    if (e != cudaSuccess) { status = fail(TN_ERR_CUDA, cudaGetErrorString(e)); break; }
+    for (int64_t i = 0; i < ns; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+      step_ms[i] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (status == TN_OK) mark_done(head, r);
+  return status;
+}
+
+extern "C" int tn_plan_step_info(const tn_plan_t* plan, int64_t i, int* kind, double* macs, double* bytes) {
+  if (!plan) return fail(TN_ERR_INVALID, "NULL plan");
+  const int64_t ns = (int64_t)plan->P.steps.size();
+  if (i < 0 || i > ns) return fail(TN_ERR_INVALID, "step index out of range");
+  if (i == ns) {
+    const tn::Plan& P = plan->P;
+    const double L = (double)P.tails_raw.size(), l = std::ldexp(1.0, (int)P.open_qubits.size());
+    if (kind) *kind = -1;
+    if (macs) *macs = 0.0;
+    if (bytes) *bytes = L * l * (8.0 + 32.0);   // read F (c64), read+write H (c128)
+    return TN_OK;
+  }
+  const tn::Step& x = plan->P.steps[i];
+  if (kind) *kind = x.kind;
+  if (macs) *macs = x.macs;
+  if (bytes) *bytes = x.bytes;
   return TN_OK;
 }
 
 extern "C" int tn_contract_slices(tn_plan_t* plan, tn_range r, tn_head_t* head, void* stream) {
-  if (!plan || !head) return fail(TN_ERR_INVALID, "NULL argument");
-  if (head->plan != plan) return fail(TN_ERR_INVALID, "head belongs to another plan");
-  const int64_t ns = 1LL << plan->P.n_sliced;
-  if (r.begin < 0 || r.end > ns || r.begin > r.end) return fail(TN_ERR_INVALID, "slice range outside [0, 2^k)");
+  int rc = check_range(plan, r, head);
+  if (rc) return rc;
   if (r.begin == r.end) return TN_OK;
-  // reject overlap with accumulated ranges
-  auto it = head->done.upper_bound(r.begin);
-  if (it != head->done.begin()) {
-    auto pv = std::prev(it);
-    if (pv->second > r.begin) return fail(TN_ERR_INVALID, "slice range overlaps slices already accumulated");
-  }
-  if (it != head->done.end() && it->first < r.end)
-    return fail(TN_ERR_INVALID, "slice range overlaps slices already accumulated");
   cudaStream_t st = (cudaStream_t)stream;
   for (int64_t s = r.begin; s < r.end; ++s) {
-    int rc = run_slice(plan, s, head->H, st);
+    rc = run_slice(plan, s, head->H, st);
     if (rc) return rc;
   }
-  head->done[r.begin] = r.end;
-  head->slices_done += r.end - r.begin;
+  mark_done(head, r);
   return TN_OK;
 }
 

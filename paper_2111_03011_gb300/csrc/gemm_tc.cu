@@ -9,11 +9,19 @@
 // hi = round-to-tf32, lo = x - hi.  The A split is done in shared memory by
 // four converter warps right after the TMA load; B arrives pre-split.
 //
-// Roles (192 threads): warps 0-3 convert A tiles and run the epilogue
-// (TMEM -> registers -> global), warp 4 issues TMA loads, warp 5 owns TMEM
-// and issues the MMAs.  One CTA computes a 128 x BN tile of C_r.  Every
-// mbarrier wait is bounded; on timeout the CTA records a status code and
-// leaves its loops instead of hanging.
+// Accumulation: the tensor cores' own FP32 accumulation is not round-to-
+// nearest, so a long K loop accumulated in place drifts (the error grows
+// linearly with K; see Ootomo and Yokota, "Recovering single precision
+// accuracy from Tensor Cores while surpassing the FP32 theoretical peak
+// performance", 2022).  The K loop is therefore cut into chunks of CH k-blocks:
+// each chunk accumulates in a fresh TMEM buffer (two, ping-pong) and four
+// drain warps fold it into a TMEM running sum with ordinary FP32 adds.
+//
+// Roles (320 threads): warps 0-3 convert A tiles, warp 4 issues TMA loads,
+// warp 5 owns TMEM and issues the MMAs, warps 6-9 drain chunk accumulators
+// into the running sum and write the tile out.  One CTA computes a 128 x BN
+// tile of C_r.  Every mbarrier wait is bounded; on timeout the CTA records a
+// status code and leaves its loops instead of hanging.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -28,7 +36,8 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 32;                  // fp32 per 128-byte swizzle row
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
+constexpr int CH = 1;                   // k-blocks per TMEM chunk (32 reduction terms)
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -106,6 +115,23 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -119,7 +145,7 @@ struct Layout {
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // A hi (in place), A lo, B hi, B lo
   static constexpr int DATA = STAGES * STAGE;
   static constexpr int TOTAL = DATA + 1024 /*align*/ + 256 /*barriers*/;
-  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  static constexpr uint32_t TMEM_COLS = 512;  // two chunk buffers + the running sum (BN <= 128)
 };
 
 template <int BN, int STAGES>
@@ -135,9 +161,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* full = bars;
   uint64_t* conv = bars + STAGES;
   uint64_t* empty = bars + 2 * STAGES;
-  uint64_t* accum = bars + 3 * STAGES;
-  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 3 * STAGES + 1);
-  volatile int* abort_flag = (volatile int*)(bars + 3 * STAGES + 2);
+  uint64_t* accf = bars + 3 * STAGES;       // chunk accumulated (MMA -> drain), per buffer
+  uint64_t* acce = bars + 3 * STAGES + 2;   // chunk buffer drained (drain -> MMA), per buffer
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 3 * STAGES + 4);
+  volatile int* abort_flag = (volatile int*)(bars + 3 * STAGES + 5);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tile = blockIdx.x;
@@ -154,7 +181,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&conv[s], 128);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -186,24 +216,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_tf32<BN>();
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES, r = kb / STAGES;
+        const int c = kb / CH, b = c & 1;
+        const bool first = (kb % CH) == 0;
+        const bool last = (kb % CH) == CH - 1 || kb == nkb - 1;
+        if (first && !mbar_wait(&acce[b], (uint32_t)(((c >> 1) & 1) ^ 1), abort_flag)) break;
         if (!mbar_wait(&conv[s], (uint32_t)(r & 1), abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t d = tmem + (uint32_t)(b * BN);
         const uint32_t st = smem_u32(smem + s * Lay::STAGE);
         const uint32_t a_hi = st, a_lo = st + Lay::A_BYTES;
         const uint32_t b_hi = st + 2 * Lay::A_BYTES, b_lo = b_hi + Lay::B_BYTES;
+        // small correction products first, so that the accumulator is still
+        // small while they are added; the hi x hi products come last
 #pragma unroll
         for (int kk = 0; kk < BK / 8; ++kk) {
           const uint32_t o = kk * 32;  // 8 tf32 = 32 bytes along K
-          const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-          mma_tf32(tmem, sdesc(a_hi + o), sdesc(b_hi + o), idesc, acc);
-          mma_tf32(tmem, sdesc(a_hi + o), sdesc(b_lo + o), idesc, 1u);
-          mma_tf32(tmem, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
+          mma_tf32(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, (!first || kk > 0) ? 1u : 0u);
+          mma_tf32(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK / 8; ++kk) {
+          const uint32_t o = kk * 32;
+          mma_tf32(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
         }
         mma_commit(&empty[s]);
+        if (last) mma_commit(&accf[b]);
       }
-      mma_commit(accum);
     }
-  } else {
+  } else if (warp < 4) {
     // converter warps: split the A tile into tf32 hi (in place) and lo
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES, r = kb / STAGES;
@@ -222,34 +262,60 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&conv[s]);
     }
-    // epilogue
-    const bool ok = mbar_wait(accum, 0u, abort_flag);
-    asm volatile("tcgen05.fence::after_thread_sync;");
+  } else {
+    // drain warps 6-9: TMEM lane quarter = warp % 4
+    const int q = warp & 3;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const uint32_t sum_col = 2u * BN;
+    const int nch = (nkb + CH - 1) / CH;
+    bool ok = true;
+    for (int c = 0; c < nch && ok; ++c) {
+      const int b = c & 1;
+      ok = mbar_wait(&accf[b], (uint32_t)((c >> 1) & 1), abort_flag);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (nch > 1) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          uint32_t v[16], w[16];
+          tmem_ld16(tmem + lane_base + (uint32_t)(b * BN + c0), v);
+          if (c > 0) {
+            tmem_ld16(tmem + lane_base + sum_col + (uint32_t)c0, w);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
+          } else {
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          }
+          tmem_st16(tmem + lane_base + sum_col + (uint32_t)c0, v);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mbar_arrive(&acce[b]);
+    }
     if (ok) {
-      const int64_t row = tm * BM + warp * 32 + lane;
+      // write the tile: from the running sum, or straight from buffer 0 for one chunk
+      const uint32_t src = nch > 1 ? sum_col : 0u;
+      const int64_t row = tm * BM + q * 32 + lane;
       float* crow = C + (pc * M + row) * N2;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
+        tmem_ld16(tmem + lane_base + src + (uint32_t)c0, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int64_t col = tn_ * BN + c0;
         if (row < M) {
           if (col + 16 <= N2) {
             float4* dst = (float4*)(crow + col);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              dst[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                   __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            for (int j = 0; j < 4; ++j)
+              dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                   __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
           } else {
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
-              if (col + q < N2) crow[col + q] = __uint_as_float(v[q]);
+            for (int j = 0; j < 16; ++j)
+              if (col + j < N2) crow[col + j] = __uint_as_float(v[j]);
           }
         }
       }
@@ -330,8 +396,7 @@ cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream
   if (N2 <= 16) return tc::run<16, 4>(p, status, s);
   if (N2 <= 32) return tc::run<32, 4>(p, status, s);
   if (N2 <= 64) return tc::run<64, 4>(p, status, s);
-  if (N2 <= 128) return tc::run<128, 3>(p, status, s);
-  return tc::run<256, 2>(p, status, s);
+  return tc::run<128, 3>(p, status, s);
 }
 
 }  // namespace tn

@@ -97,13 +97,22 @@ cudaError_t launch_small(const SmallParams& p, cudaStream_t s) {
 // ---------------------------------------------------------------------- K1
 // Bit-permutation transpose.  A tile covers the input's low bits and the
 // preimages of the output's low bits (<= 10 bits); it is read with the input's
-// contiguous order and written with the output's, through shared memory.
+// contiguous order and written with the output's, through shared memory.  The
+// tile is padded by one element per 32 so that the strided reads of the write
+// phase fall into different banks.
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+
 __global__ void __launch_bounds__(256) k_permute(PermParams p) {
   extern __shared__ float2 tile[];
   const int nt = 1 << p.t;
-  const uint32_t* in_off = p.tab;
-  const uint32_t* out_off = p.tab + nt;
-  const uint32_t* slot = p.tab + 2 * nt;
+  uint32_t* s_in = (uint32_t*)(tile + pad32(nt));
+  uint32_t* s_out = s_in + nt;
+  uint32_t* s_slot = s_out + nt;
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    s_in[i] = __ldg(p.tab + i);
+    s_out[i] = __ldg(p.tab + nt + i);
+    s_slot[i] = (uint32_t)pad32((int)__ldg(p.tab + 2 * nt + i));
+  }
   const int64_t nrest = 1LL << p.n_rest;
   for (int64_t blk = blockIdx.x; blk < nrest * p.P; blk += gridDim.x) {
     const int64_t pp = blk / nrest, b = blk % nrest;
@@ -113,16 +122,19 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
     const float2* __restrict__ src = p.in + pp * p.pstride + bi;
     float2* __restrict__ dst = p.out + pp * p.pstride + bo;
     __syncthreads();
-    for (int i = threadIdx.x; i < nt; i += blockDim.x) tile[i] = __ldg(src + __ldg(in_off + i));
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) tile[pad32(i)] = __ldg(src + s_in[i]);
     __syncthreads();
-    for (int j = threadIdx.x; j < nt; j += blockDim.x) dst[__ldg(out_off + j)] = tile[__ldg(slot + j)];
+#pragma unroll 4
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) dst[s_out[j]] = tile[s_slot[j]];
   }
 }
 
 cudaError_t launch_permute(const PermParams& p, cudaStream_t s) {
   const int64_t blocks = (1LL << p.n_rest) * p.P;
   const int64_t grid = std::min<int64_t>(blocks, (int64_t)kSMs * 16);
-  const size_t smem = sizeof(float2) << p.t;
+  const int nt = 1 << p.t;
+  const size_t smem = sizeof(float2) * (size_t)(nt + (nt >> 5) + 1) + 3 * sizeof(uint32_t) * (size_t)nt;
   k_permute<<<(unsigned)grid, 256, smem, s>>>(p);
   return cudaGetLastError();
 }

@@ -250,3 +250,37 @@ def test_sliced30_full_size_properties(tn):
     H = read_head(tn, plan, head, cfg)
     p = np.abs(H) ** 2 * 2 ** 30
     assert O.porter_thomas_ks(p / p.mean()) < 0.02
+
+
+def test_sliced30_full_size_sampled_groups_vs_oracle(tn):
+    """Full-size workload in the bench's launch configuration (same plan, same
+    kernels): one slice contracted for all 64 groups; two sampled groups
+    checked element by element against the O2 network oracle."""
+    cfg = ci.config_sliced30()
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], order_trials=512)
+    head = tn.tn_head_create(plan)
+    s = 5
+    tn.tn_contract_slices(plan, s, s + 1, head)
+    H = read_head(tn, plan, head, cfg)
+    se = [(g, l) for (g, l, k, v) in cfg["edges"]]
+    groups = [0, 37]
+    ref = O.network_amplitudes(cfg["circuit"], cfg["open_qubits"], cfg["tails"], se, slice_range=(s, s + 1),
+                               groups=groups)
+    for i, g in enumerate(groups):
+        assert_close(H[g:g + 1], ref[i:i + 1])
+
+
+def test_profile_and_reset(tn):
+    cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    head = tn.tn_head_create(plan)
+    ms = tn.tn_profile_slices(plan, 0, 16, head)
+    st = tn.tn_plan_get_stats(plan)
+    assert ms.shape == (st["n_launches"],) and (ms > 0).all()
+    assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg))
+    tn.tn_head_reset(head)
+    assert tn.tn_head_fidelity(head) == (0.0, 0)
+    tn.tn_contract_slices(plan, 0, 16, head)
+    assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg))
+    kinds = [tn.tn_plan_step_info(plan, i)[0] for i in range(st["n_launches"])]
+    assert kinds[-1] == -1 and set(kinds[:-1]) <= {0, 1, 2, 3, 4, 5}
