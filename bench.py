@@ -49,6 +49,8 @@ def _workload(name):
         return ci.config_sliced30()
     if name == "tiny":
         return ci.config_tiny()
+    if name == "grid25":
+        return ci.config_grid25()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -344,7 +346,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sliced30", choices=["sliced30", "tiny"])
+    ap.add_argument("--workload", default="sliced30", choices=["sliced30", "tiny", "grid25"])
     ap.add_argument("--engine", default="tc", choices=["tc", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slices", type=int, default=0,

@@ -231,6 +231,14 @@ def config_sliced30():
                 sample_seed=4, name="grid5x6_m14_open10_L64_k6")
 
 
+def config_grid25():
+    """25-qubit 5x5 grid, 10 cycles, all qubits open, one group, no slicing: a
+    small case with the same step kernels (operands above L2, ~2 GB on device)."""
+    circ = make_grid_circuit(5, 5, 10, seed=21)
+    return dict(circuit=circ, open_qubits=list(range(25)), tails=np.zeros(1, dtype=np.uint64), edges=[],
+                n_samples=1000, sample_seed=6, name="grid5x5_m10_open25")
+
+
 def config_small(rows=4, cols=4, cycles=8, seed=11, n_open=6, L=8, n_cut_gates=2, tail_seed=12):
     """Scaled-down sliced sparse-state case used by parity tests."""
     circ = make_grid_circuit(rows, cols, cycles, seed=seed)
