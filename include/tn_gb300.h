@@ -177,6 +177,29 @@ int  tn_profile_slices(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, v
  * algorithmic complex multiply-adds and HBM bytes of launch i of one slice. */
 int  tn_plan_step_info(const tn_plan_t* plan, int64_t i, int* kind, double* macs, double* bytes);
 
+/* Largest group count tn_head_norm_noalloc accepts (its fixed scratch: 1 MiB). */
+#define TN_NOALLOC_MAX_GROUPS 131072
+
+/* tn_head_norm for callers that cannot allocate device memory -- for example
+ * code running inside another framework that owns all device memory through
+ * its own allocator, or a latency-critical loop where a cudaMalloc (which may
+ * synchronise the device) is not allowed.  The paper has no counterpart; it is
+ * an integration aid.
+ *
+ * Computes *norm_out = sum |H|^2 (FP64, same kernels and summation order as
+ * tn_head_norm) for a complex128 head H[n_groups][2^n_open] in device memory.
+ * norm_out is a device pointer; the call is asynchronous on `stream` and
+ * allocates nothing (no cudaMalloc, no cudaFree, no allocating library call).
+ * The per-group partial sums live in one fixed device array of
+ * TN_NOALLOC_MAX_GROUPS doubles inside the library, which every GPU that loads
+ * the library holds until the process exits; larger n_groups are rejected with
+ * TN_ERR_INVALID.  The first call on a device looks up that array's device
+ * address (once per device, with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents: calls whose kernels overlap on the GPU (different streams,
+ * or different host threads) race on it, so serialise them. */
+int  tn_head_norm_noalloc(const void* head_c128, int64_t n_groups, int n_open, double* norm_out, void* stream);
+
 const char* tn_last_error(void);
 const char* tn_version(void);
 

@@ -98,11 +98,12 @@ def _load():
     lib.tn_head_norm.argtypes = [vp, C.POINTER(C.c_double), vp, vp]
     lib.tn_profile_slices.argtypes = [vp, tn_range, vp, vp, C.POINTER(C.c_double), i64]
     lib.tn_plan_step_info.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.tn_head_norm_noalloc.argtypes = [vp, i64, C.c_int, vp, vp]
     lib.tn_last_error.restype = C.c_char_p
     lib.tn_version.restype = C.c_char_p
     for name in ("tn_plan", "tn_plan_get_stats", "tn_plan_order", "tn_head_create", "tn_head_fidelity",
                  "tn_head_set_fidelity", "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm",
-                 "tn_profile_slices", "tn_plan_step_info", "tn_head_reset"):
+                 "tn_profile_slices", "tn_plan_step_info", "tn_head_reset", "tn_head_norm_noalloc"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -113,7 +114,7 @@ lib = _lib
 EXPORTED = ["tn_plan", "tn_plan_free", "tn_plan_get_stats", "tn_plan_order", "tn_plan_describe",
             "tn_head_create", "tn_head_free", "tn_head_data", "tn_head_reset", "tn_head_fidelity", "tn_head_set_fidelity",
             "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm", "tn_profile_slices",
-            "tn_plan_step_info", "tn_last_error", "tn_version"]
+            "tn_plan_step_info", "tn_head_norm_noalloc", "tn_last_error", "tn_version"]
 
 
 def _check(rc):
@@ -303,6 +304,13 @@ def tn_plan_step_info(plan: Plan, i: int):
     b = C.c_double()
     _check(_lib.tn_plan_step_info(plan.handle, int(i), C.byref(k), C.byref(m), C.byref(b)))
     return k.value, m.value, b.value
+
+
+def tn_head_norm_noalloc(head_buffer, n_groups: int, n_open: int, norm_out, stream=None):
+    """FP64 squared norm of a device complex128 head buffer into the device
+    double `norm_out`, with no device allocation (asynchronous on `stream`)."""
+    _check(_lib.tn_head_norm_noalloc(_ptr(head_buffer), int(n_groups), int(n_open), _ptr(norm_out),
+                                     _stream(stream)))
 
 
 def tn_last_error() -> str:

@@ -72,6 +72,11 @@ struct tn_head {
 
 static const char* kVersion = "tn_gb300 0.1 (sm_103a)";
 
+namespace tn {
+// Lets other translation units of the library report through tn_last_error.
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace tn
+
 extern "C" const char* tn_last_error(void) { return g_err.c_str(); }
 extern "C" const char* tn_version(void) { return kVersion; }
 
