@@ -381,6 +381,7 @@ static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaE
         std::memcpy(pp.rest_in, x.rest_in, sizeof(pp.rest_in));
         std::memcpy(pp.rest_out, x.rest_out, sizeof(pp.rest_out));
         pp.tab = p->d_meta + x.tab_off;
+        pp.split = x.split;
         e = tn::launch_permute(pp, st);
         break;
       }

@@ -3,25 +3,27 @@
 // C[p][m][n] = sum_k A[mapA(p)][m][k] * B[mapB(p)][k][n] in complex64 is run as
 // one real GEMM on interleaved data (the 4M real embedding):
 //     C_r[m][j] = sum_i A_r[m][i] * Bt[j][i],  A_r = A viewed as fp32 [M][2K],
-//     Bt = the real-embedded B, [2N][2K] K-major (prepared by k_bprep_tc).
+//     Bt = the real embedding of B, [2N][2K] K-major (built by k_bprep_tc).
 // FP32 accuracy from TF32 tensor cores by the 3xTF32 split
 //     A_r Bt ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
-// hi = round-to-tf32, lo = x - hi.  The A split is done in shared memory by
-// four converter warps right after the TMA load; B arrives pre-split.
+// hi = round-to-tf32, lo = x - hi.  Both operands arrive pre-split in global
+// memory (A by the split-mode permute, B by k_bprep_tc), so the kernel is a
+// plain TMA -> MMA pipeline.
 //
 // Accumulation: the tensor cores' own FP32 accumulation is not round-to-
 // nearest, so a long K loop accumulated in place drifts (the error grows
 // linearly with K; see Ootomo and Yokota, "Recovering single precision
 // accuracy from Tensor Cores while surpassing the FP32 theoretical peak
-// performance", 2022).  The K loop is therefore cut into chunks of CH k-blocks:
-// each chunk accumulates in a fresh TMEM buffer (two, ping-pong) and four
-// drain warps fold it into a TMEM running sum with ordinary FP32 adds.
+// performance", 2022).  The K loop is therefore cut into chunks of one k-block
+// (32 reduction terms): each accumulates in a fresh TMEM buffer (two,
+// ping-pong) and four drain warps fold it into a TMEM running sum with
+// ordinary FP32 adds.
 //
-// Roles (320 threads): warps 0-3 convert A tiles, warp 4 issues TMA loads,
-// warp 5 owns TMEM and issues the MMAs, warps 6-9 drain chunk accumulators
-// into the running sum and write the tile out.  One CTA computes a 128 x BN
-// tile of C_r.  Every mbarrier wait is bounded; on timeout the CTA records a
-// status code and leaves its loops instead of hanging.
+// Roles (192 threads): warps 0-3 drain chunk accumulators into the running sum
+// and write the tile out, warp 4 issues TMA loads, warp 5 owns TMEM and issues
+// the MMAs.  One CTA computes a 128 x BN tile of C_r.  Every mbarrier wait is
+// bounded; on timeout the CTA records a status code and leaves its loops
+// instead of hanging.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -36,8 +38,7 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 32;                  // fp32 per 128-byte swizzle row
-constexpr int kThreads = 320;
-constexpr int CH = 1;                   // k-blocks per TMEM chunk (32 reduction terms)
+constexpr int kThreads = 192;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -140,37 +141,60 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 template <int BN, int STAGES>
 struct Layout {
-  static constexpr int A_BYTES = BM * BK * 4;
-  static constexpr int B_BYTES = BN * BK * 4;
-  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // A hi (in place), A lo, B hi, B lo
+  static constexpr int A_BYTES = BM * BK * 4;          // one 128 x 32 fp32 tile
+  static constexpr int B_BYTES = BN * BK * 4;          // one BN x 32 fp32 tile
+  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // A hi, A lo, B hi, B lo
   static constexpr int DATA = STAGES * STAGE;
   static constexpr int TOTAL = DATA + 1024 /*align*/ + 256 /*barriers*/;
-  static constexpr uint32_t TMEM_COLS = 512;  // two chunk buffers + the running sum (BN <= 128)
+  static constexpr uint32_t TMEM_COLS = 512;           // two chunk buffers + the running sum (BN <= 128)
 };
+
+// Tile order: groups of GROUP_M m-tiles; inside a group n-tiles and (when A is
+// shared by every pattern) patterns vary before the next group, so the A rows
+// of a group and the B tiles of a wave stay in L2.
+constexpr int64_t GROUP_M = 8;
+
+__device__ __forceinline__ void tile_coords(int64_t t, int64_t tilesM, int64_t tilesN, int64_t PC, bool a_shared,
+                                            int64_t& pc, int64_t& tm, int64_t& tn) {
+  const int64_t P_in = a_shared ? PC : 1;
+  int64_t outer = 0;
+  if (!a_shared) {
+    outer = t / (tilesM * tilesN);
+    t -= outer * tilesM * tilesN;
+  }
+  const int64_t per_full = GROUP_M * tilesN * P_in;
+  const int64_t mg = t / per_full;
+  int64_t r = t - mg * per_full;
+  const int64_t gm = min(GROUP_M, tilesM - mg * GROUP_M);
+  const int64_t mi = r % gm;
+  r /= gm;
+  tn = r % tilesN;
+  const int64_t pin = r / tilesN;
+  tm = mg * GROUP_M + mi;
+  pc = a_shared ? pin : outer;
+}
 
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
-              const __grid_constant__ CUtensorMap tmBlo, float* __restrict__ C, int64_t M, int64_t N2, int64_t K2,
-              int64_t tilesM, int64_t tilesN, const uint32_t* __restrict__ mapA, const uint32_t* __restrict__ mapB,
-              int mapA_mode, int mapB_mode, unsigned int* status) {
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+              const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+              float* __restrict__ C, int64_t M, int64_t N2, int64_t K2, int64_t tilesM, int64_t tilesN, int64_t PC,
+              const uint32_t* __restrict__ mapA, const uint32_t* __restrict__ mapB, int mapA_mode, int mapB_mode,
+              unsigned int* status) {
   using Lay = Layout<BN, STAGES>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + Lay::DATA);
-  uint64_t* full = bars;
-  uint64_t* conv = bars + STAGES;
-  uint64_t* empty = bars + 2 * STAGES;
-  uint64_t* accf = bars + 3 * STAGES;       // chunk accumulated (MMA -> drain), per buffer
-  uint64_t* acce = bars + 3 * STAGES + 2;   // chunk buffer drained (drain -> MMA), per buffer
-  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 3 * STAGES + 4);
-  volatile int* abort_flag = (volatile int*)(bars + 3 * STAGES + 5);
+  uint64_t* full = bars;                    // stage loaded   [STAGES]
+  uint64_t* empty = bars + STAGES;          // stage consumed [STAGES]
+  uint64_t* accf = bars + 2 * STAGES;       // chunk accumulated (MMA -> drain) [2]
+  uint64_t* acce = bars + 2 * STAGES + 2;   // chunk drained (drain -> MMA)     [2]
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * STAGES + 4);
+  volatile int* abort_flag = (volatile int*)(bars + 2 * STAGES + 5);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tile = blockIdx.x;
-  const int64_t pc = tile / (tilesM * tilesN);
-  const int64_t rem = tile % (tilesM * tilesN);
-  const int64_t tm = rem / tilesN, tn_ = rem % tilesN;
+  int64_t pc, tm, tn_;
+  tile_coords(blockIdx.x, tilesM, tilesN, PC, mapA_mode == 1 && PC > 1, pc, tm, tn_);
   const int64_t pa = mapA_mode == 0 ? pc : (mapA_mode == 1 ? 0 : (int64_t)mapA[pc]);
   const int64_t pb = mapB_mode == 0 ? pc : (mapB_mode == 1 ? 0 : (int64_t)mapB[pc]);
   const int nkb = (int)((K2 + BK - 1) / BK);
@@ -178,7 +202,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 128);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -205,8 +228,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = kb % STAGES, r = kb / STAGES;
         if (!mbar_wait(&empty[s], (uint32_t)((r & 1) ^ 1), abort_flag)) break;
         uint8_t* st = smem + s * Lay::STAGE;
-        mbar_expect_tx(&full[s], (uint32_t)(Lay::A_BYTES + 2 * Lay::B_BYTES));
-        tma_load_3d(st, &tmA, &full[s], kb * BK, (int)(tm * BM), (int)pa);
+        mbar_expect_tx(&full[s], (uint32_t)Lay::STAGE);
+        tma_load_3d(st, &tmAhi, &full[s], kb * BK, (int)(tm * BM), (int)pa);
+        tma_load_3d(st + Lay::A_BYTES, &tmAlo, &full[s], kb * BK, (int)(tm * BM), (int)pa);
         tma_load_3d(st + 2 * Lay::A_BYTES, &tmBhi, &full[s], kb * BK, (int)(tn_ * BN), (int)pb);
         tma_load_3d(st + 2 * Lay::A_BYTES + Lay::B_BYTES, &tmBlo, &full[s], kb * BK, (int)(tn_ * BN), (int)pb);
       }
@@ -215,12 +239,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       const uint32_t idesc = idesc_tf32<BN>();
       for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES, r = kb / STAGES;
-        const int c = kb / CH, b = c & 1;
-        const bool first = (kb % CH) == 0;
-        const bool last = (kb % CH) == CH - 1 || kb == nkb - 1;
-        if (first && !mbar_wait(&acce[b], (uint32_t)(((c >> 1) & 1) ^ 1), abort_flag)) break;
-        if (!mbar_wait(&conv[s], (uint32_t)(r & 1), abort_flag)) break;
+        // one k-block per TMEM chunk: buffer b alternates
+        const int s = kb % STAGES, r = kb / STAGES, b = kb & 1;
+        if (!mbar_wait(&acce[b], (uint32_t)(((kb >> 1) & 1) ^ 1), abort_flag)) break;
+        if (!mbar_wait(&full[s], (uint32_t)(r & 1), abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t d = tmem + (uint32_t)(b * BN);
         const uint32_t st = smem_u32(smem + s * Lay::STAGE);
@@ -231,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < BK / 8; ++kk) {
           const uint32_t o = kk * 32;  // 8 tf32 = 32 bytes along K
-          mma_tf32(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, (!first || kk > 0) ? 1u : 0u);
+          mma_tf32(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, kk > 0 ? 1u : 0u);
           mma_tf32(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
         }
 #pragma unroll
@@ -240,41 +262,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           mma_tf32(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
         }
         mma_commit(&empty[s]);
-        if (last) mma_commit(&accf[b]);
+        mma_commit(&accf[b]);
       }
-    }
-  } else if (warp < 4) {
-    // converter warps: split the A tile into tf32 hi (in place) and lo
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, r = kb / STAGES;
-      if (!mbar_wait(&full[s], (uint32_t)(r & 1), abort_flag)) break;
-      float4* a = (float4*)(smem + s * Lay::STAGE);
-      float4* lo = (float4*)(smem + s * Lay::STAGE + Lay::A_BYTES);
-#pragma unroll
-      for (int i = 0; i < Lay::A_BYTES / 16 / 128; ++i) {
-        const int idx = threadIdx.x + 128 * i;
-        float4 v = a[idx];
-        float4 h;
-        h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
-        a[idx] = h;
-        lo[idx] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&conv[s]);
     }
   } else {
-    // drain warps 6-9: TMEM lane quarter = warp % 4
+    // drain warps 0-3: TMEM lane quarter = warp
     const int q = warp & 3;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const uint32_t sum_col = 2u * BN;
-    const int nch = (nkb + CH - 1) / CH;
     bool ok = true;
-    for (int c = 0; c < nch && ok; ++c) {
+    for (int c = 0; c < nkb && ok; ++c) {
       const int b = c & 1;
       ok = mbar_wait(&accf[b], (uint32_t)((c >> 1) & 1), abort_flag);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      if (nch > 1) {
+      if (nkb > 1) {
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
           uint32_t v[16], w[16];
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (ok) {
       // write the tile: from the running sum, or straight from buffer 0 for one chunk
-      const uint32_t src = nch > 1 ? sum_col : 0u;
+      const uint32_t src = nkb > 1 ? sum_col : 0u;
       const int64_t row = tm * BM + q * 32 + lane;
       float* crow = C + (pc * M + row) * N2;
 #pragma unroll 1
@@ -373,18 +375,22 @@ static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s
     attr_set = true;
   }
   const int64_t K2 = 2 * p.K, N2 = 2 * p.N;
-  CUtensorMap ta, tbh, tbl;
+  // A: hi plane then lo plane, each fp32 [PA][M][2K]; B: hi plane then lo plane, each [PB][2N][2K]
+  const float* ahi = (const float*)p.A;
+  const float* alo = ahi + p.PA * p.M * K2;
   const float* bhi = (const float*)p.B;
   const float* blo = bhi + p.PB * N2 * K2;
-  if (!encode3d(&ta, p.A, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BK, BM)) return cudaErrorInvalidValue;
+  CUtensorMap tah, tal, tbh, tbl;
+  if (!encode3d(&tah, ahi, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BK, BM)) return cudaErrorInvalidValue;
+  if (!encode3d(&tal, alo, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BK, BM)) return cudaErrorInvalidValue;
   if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BK, BN)) return cudaErrorInvalidValue;
   if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BK, BN)) return cudaErrorInvalidValue;
   const int64_t tilesM = (p.M + BM - 1) / BM, tilesN = (N2 + BN - 1) / BN;
   const int64_t grid = tilesM * tilesN * p.PC;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_gemm_tc<BN, STAGES><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(ta, tbh, tbl, (float*)p.C, p.M, N2, K2, tilesM,
-                                                                      tilesN, p.mapA, p.mapB, p.mapA_mode,
-                                                                      p.mapB_mode, status);
+  k_gemm_tc<BN, STAGES><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(tah, tal, tbh, tbl, (float*)p.C, p.M, N2, K2,
+                                                                      tilesM, tilesN, p.PC, p.mapA, p.mapB,
+                                                                      p.mapA_mode, p.mapB_mode, status);
   return cudaGetLastError();
 }
 
@@ -393,8 +399,8 @@ static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s
 cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   if (p.K < 2) return cudaErrorInvalidValue;  // row pitch 2K*4 bytes must be a multiple of 16
   const int64_t N2 = 2 * p.N;
-  if (N2 <= 16) return tc::run<16, 4>(p, status, s);
-  if (N2 <= 32) return tc::run<32, 4>(p, status, s);
+  if (N2 <= 16) return tc::run<16, 6>(p, status, s);
+  if (N2 <= 32) return tc::run<32, 5>(p, status, s);
   if (N2 <= 64) return tc::run<64, 4>(p, status, s);
   return tc::run<128, 3>(p, status, s);
 }

@@ -96,46 +96,88 @@ cudaError_t launch_small(const SmallParams& p, cudaStream_t s) {
 
 // ---------------------------------------------------------------------- K1
 // Bit-permutation transpose.  A tile covers the input's low bits and the
-// preimages of the output's low bits (<= 10 bits); it is read with the input's
-// contiguous order and written with the output's, through shared memory.  The
-// tile is padded by one element per 32 so that the strided reads of the write
-// phase fall into different banks.
+// preimages of the output's low bits (grown to 10 bits with further input
+// bits); it is read with the input's contiguous order and written with the
+// output's, through shared memory.  The tile is padded by one element per 32 so
+// that the strided reads of the write phase fall into different banks.  The
+// tile's base addresses (the remaining "rest" bits of the tile index scattered
+// to their positions) come from four 256-entry tables per direction.
+// SPLIT: the output is written as two fp32 planes, tf32-rounded hi and the
+// remainder lo, the operand format of the tensor-core GEMM.
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <bool SPLIT>
 __global__ void __launch_bounds__(256) k_permute(PermParams p) {
   extern __shared__ float2 tile[];
   const int nt = 1 << p.t;
-  uint32_t* s_in = (uint32_t*)(tile + pad32(nt));
+  uint32_t* s_in = (uint32_t*)(tile + pad32(nt) + 1);
   uint32_t* s_out = s_in + nt;
   uint32_t* s_slot = s_out + nt;
+  uint64_t* r_in = (uint64_t*)(((uintptr_t)(s_slot + nt) + 7) & ~(uintptr_t)7);   // [4][256]
+  uint64_t* r_out = r_in + 1024;
   for (int i = threadIdx.x; i < nt; i += blockDim.x) {
     s_in[i] = __ldg(p.tab + i);
     s_out[i] = __ldg(p.tab + nt + i);
     s_slot[i] = (uint32_t)pad32((int)__ldg(p.tab + 2 * nt + i));
   }
-  const int64_t nrest = 1LL << p.n_rest;
-  for (int64_t blk = blockIdx.x; blk < nrest * p.P; blk += gridDim.x) {
-    const int64_t pp = blk / nrest, b = blk % nrest;
-    int64_t bi = 0, bo = 0;
-    for (int v = 0; v < p.n_rest; ++v)
-      if ((b >> v) & 1) { bi |= 1LL << p.rest_in[v]; bo |= 1LL << p.rest_out[v]; }
+  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+    const int level = e >> 8, v = e & 255;
+    uint64_t bi = 0, bo = 0;
+    for (int k = 0; k < 8; ++k) {
+      const int bit = level * 8 + k;
+      if (bit < p.n_rest && ((v >> k) & 1)) {
+        bi |= 1ULL << p.rest_in[bit];
+        bo |= 1ULL << p.rest_out[bit];
+      }
+    }
+    r_in[e] = bi;
+    r_out[e] = bo;
+  }
+  __syncthreads();  // the tables are read below before the tile loop's own barrier
+  const uint64_t nrest_mask = (1ULL << p.n_rest) - 1;
+  const uint64_t total_tiles = (uint64_t)p.P << p.n_rest;
+  float2* __restrict__ out_lo = p.out + p.P * p.pstride;
+  for (uint64_t blk = blockIdx.x; blk < total_tiles; blk += gridDim.x) {
+    const uint64_t pp = blk >> p.n_rest, b = blk & nrest_mask;
+    const uint64_t bi = r_in[b & 255] | r_in[256 + ((b >> 8) & 255)] | r_in[512 + ((b >> 16) & 255)] |
+                        r_in[768 + ((b >> 24) & 255)];
+    const uint64_t bo = r_out[b & 255] | r_out[256 + ((b >> 8) & 255)] | r_out[512 + ((b >> 16) & 255)] |
+                        r_out[768 + ((b >> 24) & 255)];
     const float2* __restrict__ src = p.in + pp * p.pstride + bi;
-    float2* __restrict__ dst = p.out + pp * p.pstride + bo;
+    const int64_t dofs = (int64_t)(pp * p.pstride + bo);
     __syncthreads();
 #pragma unroll 4
     for (int i = threadIdx.x; i < nt; i += blockDim.x) tile[pad32(i)] = __ldg(src + s_in[i]);
     __syncthreads();
 #pragma unroll 4
-    for (int j = threadIdx.x; j < nt; j += blockDim.x) dst[s_out[j]] = tile[s_slot[j]];
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+      const float2 v = tile[s_slot[j]];
+      if (SPLIT) {
+        const float2 h = make_float2(tf32_rn(v.x), tf32_rn(v.y));
+        p.out[dofs + s_out[j]] = h;
+        out_lo[dofs + s_out[j]] = make_float2(v.x - h.x, v.y - h.y);
+      } else {
+        p.out[dofs + s_out[j]] = v;
+      }
+    }
   }
 }
 
 cudaError_t launch_permute(const PermParams& p, cudaStream_t s) {
+  if (p.n_rest > 32) return cudaErrorInvalidValue;
   const int64_t blocks = (1LL << p.n_rest) * p.P;
-  const int64_t grid = std::min<int64_t>(blocks, (int64_t)kSMs * 16);
+  const int64_t grid = std::min<int64_t>(blocks, (int64_t)kSMs * 8);
   const int nt = 1 << p.t;
-  const size_t smem = sizeof(float2) * (size_t)(nt + (nt >> 5) + 1) + 3 * sizeof(uint32_t) * (size_t)nt;
-  k_permute<<<(unsigned)grid, 256, smem, s>>>(p);
+  const size_t smem = sizeof(float2) * (size_t)(nt + (nt >> 5) + 2) + 3 * sizeof(uint32_t) * (size_t)nt + 8 +
+                      2 * 1024 * sizeof(uint64_t);
+  if (p.split) k_permute<true><<<(unsigned)grid, 256, smem, s>>>(p);
+  else k_permute<false><<<(unsigned)grid, 256, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -159,7 +201,8 @@ __device__ __forceinline__ float tf32_round(float x) {
 
 // Real embedding of B for C_r = A_r B_r with interleaved complex rows:
 // Bt[j][i] (j = 2n + jc output column, i = 2k + ic reduction index) is
-// [[re, -im], [im, re]] in (jc, ic); stored K-major, split into tf32 hi + lo.
+// [[re, -im], [im, re]] in (jc, ic); stored K-major, split into tf32 hi + lo
+// planes.
 __global__ void k_bprep_tc(BPrepParams p) {
   const int64_t K2 = 2LL << p.nk, N2 = 2LL << p.nn;
   const int64_t per = K2 * N2;

@@ -27,6 +27,7 @@ struct PermParams {
   int n_rest;
   uint8_t rest_in[64], rest_out[64];
   const uint32_t* tab;   // in_off[2^t], out_off[2^t], slot[2^t]
+  int split;             // 1: write tf32 hi plane then lo plane (fp32 pairs)
 };
 
 struct BPrepParams {
@@ -60,7 +61,8 @@ cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s);
 cudaError_t launch_gemm_simt(const GemmParams& p, cudaStream_t s);
 cudaError_t launch_accum(const AccumParams& p, cudaStream_t s);
 
-// Tensor-core GEMM (gemm_tc.cu).  B = real-embedded [PB][2N][2K] fp32 hi then lo.
+// Tensor-core GEMM (gemm_tc.cu).  A = hi then lo fp32 planes [PA][M][2K];
+// B = real-embedded hi then lo planes [PB][2N][2K].
 // `status` receives a nonzero code if a bounded wait gave up.
 cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s);
 

@@ -463,9 +463,11 @@ static void set_map(Plan& plan, const VTensor& X, const VTensor& C, int& mode, i
   off = meta_push(plan, m);
 }
 
-static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& target, Ref out, int ci) {
+static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& target, Ref out, int ci,
+                        bool split) {
   Step s;
   s.kind = ST_PERMUTE;
+  s.split = split ? 1 : 0;
   s.a = X.ref;
   s.c = out;
   s.contraction = ci;
@@ -480,6 +482,9 @@ static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& ta
   for (int x = 0; x < a; ++x) Tin.push_back(x);
   for (int o = 0; o < bq; ++o)
     if (std::find(Tin.begin(), Tin.end(), in_pos[o]) == Tin.end()) Tin.push_back(in_pos[o]);
+  // grow small tiles with further input bits (longer contiguous runs, fewer tiles)
+  for (int x = 0; x < r && (int)Tin.size() < 10; ++x)
+    if (std::find(Tin.begin(), Tin.end(), x) == Tin.end()) Tin.push_back(x);
   std::sort(Tin.begin(), Tin.end());
   const int t = (int)Tin.size();
   std::vector<int> Tout;
@@ -510,7 +515,7 @@ static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& ta
       s.rest_out[s.n_rest] = (uint8_t)inv[x];
       ++s.n_rest;
     }
-  s.bytes = 16.0 * (double)vt_elems(X);
+  s.bytes = (split ? 24.0 : 16.0) * (double)vt_elems(X);
   plan.steps.push_back(s);
 }
 
@@ -606,14 +611,16 @@ static int layout_steps(Plan& plan, std::string& err) {
       for (int l : K) target.push_back(l);
       for (int l : M) target.push_back(l);
       Ref aref = big.ref;
-      if (target != big.legs) {
+      const bool tc = plan.gemm_engine != TN_GEMM_SIMT_FP32 && nk >= 1;
+      if (tc || target != big.legs) {
+        // the tensor-core GEMM reads A as tf32 hi/lo planes: always a (possibly
+        // identity) permute in split mode
         const int st = (int)plan.steps.size();
         touch(plan, big.ref, st);
-        Ref out{1, new_buf(plan, vt_elems(big) * 8, st)};
-        add_permute(plan, big, target, out, ci);
+        Ref out{1, new_buf(plan, vt_elems(big) * 8 * (tc ? 2 : 1), st)};
+        add_permute(plan, big, target, out, ci, tc);
         aref = out;
       }
-      const bool tc = plan.gemm_engine != TN_GEMM_SIMT_FP32 && nk >= 1;
       // B' prep
       Step p;
       p.kind = tc ? ST_BPREP_TC : ST_BPREP_C;
@@ -914,11 +921,38 @@ std::string describe_plan(const Plan& plan, bool with_data) {
     o << "{\"kind\":" << st.kind << ",\"contraction\":" << st.contraction << ",\"vt_a\":" << st.vt_a << ",\"vt_b\":"
       << st.vt_b << ",\"vt_c\":" << st.vt_c << ",\"nk\":" << st.nk << ",\"nm\":" << st.nm << ",\"nn\":" << st.nn
       << ",\"PA\":" << st.PA << ",\"PB\":" << st.PB << ",\"PC\":" << st.PC << ",\"macs\":" << st.macs
-      << ",\"bytes\":" << st.bytes << "}";
+      << ",\"bytes\":" << st.bytes << ",\"rA\":" << st.rA << ",\"rB\":" << st.rB << ",\"rC\":" << st.rC
+      << ",\"a\":[" << st.a.kind << "," << st.a.id << "],\"b\":[" << st.b.kind << "," << st.b.id << "],\"c\":["
+      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split
+      << ",\"tab_off\":" << st.tab_off << ",\"n_rest\":" << st.n_rest << ",\"rest_in\":[";
+    for (int v = 0; v < st.n_rest; ++v) o << (v ? "," : "") << (int)st.rest_in[v];
+    o << "],\"rest_out\":[";
+    for (int v = 0; v < st.n_rest; ++v) o << (v ? "," : "") << (int)st.rest_out[v];
+    o << "],\"kposA\":[" << st.kposA[0] << "," << st.kposA[1] << "," << st.kposA[2] << "," << st.kposA[3]
+      << "],\"boffK\":[";
+    for (int v = 0; v < 16; ++v) o << (v ? "," : "") << st.boffK[v];
+    o << "],\"boffN\":[";
+    for (int v = 0; v < 16; ++v) o << (v ? "," : "") << st.boffN[v];
+    o << "],\"mapA\":[" << st.mapA_mode << "," << st.mapA_off << "],\"mapB\":[" << st.mapB_mode << ","
+      << st.mapB_off << "],\"bk_off\":" << st.bk_off << ",\"bn_off\":" << st.bn_off << "}";
   }
   o << "],\"final\":{\"vt\":" << plan.fin.vt << ",\"open_pos\":[";
   for (size_t j = 0; j < plan.open_qubits.size(); ++j) o << (j ? "," : "") << plan.fin.open_pos[j];
-  o << "]},\"tc_macs\":" << plan.tc_macs << ",\"alg_bytes\":" << plan.alg_bytes << ",\"max_log2\":" << plan.max_log2
+  o << "],\"rF\":" << plan.fin.rF << ",\"PF\":" << plan.fin.PF << ",\"ref\":[" << plan.fin.ref.kind << ","
+    << plan.fin.ref.id << "],\"pidx_off\":" << plan.fin.pidx_off << "}";
+  o << ",\"bufs\":[";
+  for (size_t b = 0; b < plan.bufs.size(); ++b)
+    o << (b ? "," : "") << "[" << plan.bufs[b].off << "," << plan.bufs[b].bytes << "," << plan.bufs[b].first << ","
+      << plan.bufs[b].last << "]";
+  o << "],\"leaf_arena_elems\":" << plan.leaf_arena.size();
+  if (with_data) {
+    o << ",\"meta\":[";
+    for (size_t m = 0; m < plan.meta.size(); ++m) o << (m ? "," : "") << plan.meta[m];
+    o << "],\"leaf_info\":[";
+    for (size_t l = 0; l < plan.leaf_info.size(); ++l) o << (l ? "," : "") << "[" << plan.leaf_info[l].off << "," << plan.leaf_info[l].size << "," << plan.leaf_info[l].var_slice_bits.size() << "]";
+    o << "]";
+  }
+  o << ",\"tc_macs\":" << plan.tc_macs << ",\"alg_bytes\":" << plan.alg_bytes << ",\"max_log2\":" << plan.max_log2
     << ",\"workspace_bytes\":" << plan.workspace_bytes << "}";
   return o.str();
 }
