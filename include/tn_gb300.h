@@ -51,7 +51,12 @@ enum {
 
 enum { TN_EDGE_SLICE = 0, TN_EDGE_PIN = 1, TN_EDGE_COMPANION = 2 };
 enum { TN_C64 = 0, TN_C128 = 1 };
-enum { TN_GEMM_AUTO = 0, TN_GEMM_TC_3XTF32 = 1, TN_GEMM_SIMT_FP32 = 2 };
+/* GEMM-step engines: AUTO = TC_3XTF32.  TC_3XTF32: tcgen05, tf32 hi/lo split,
+ * FP32-accurate (complex64 path, relative L2 <= 1e-5).  SIMT_FP32: CUDA-core
+ * FP32 (the plain complex64 reference engine).  TC_BF16X3: tcgen05 kind::f16,
+ * bf16 hi/lo split with FP32 accumulation, relative L2 <= 1e-4 (a precision
+ * form with twice the tensor rate). */
+enum { TN_GEMM_AUTO = 0, TN_GEMM_TC_3XTF32 = 1, TN_GEMM_SIMT_FP32 = 2, TN_GEMM_TC_BF16X3 = 3 };
 
 /* One gate, in time order.  arity 1: re/im[0..3] hold the 2x2 matrix
  * (row-major, row = output); arity 2: re/im[0..15] hold the 4x4 matrix. */

@@ -20,7 +20,7 @@ from .buildlib import LIBPATH, build
 TN_OK, TN_ERR_INVALID, TN_ERR_OOM, TN_ERR_NOT_IN_STATE, TN_ERR_TIMEOUT, TN_ERR_CUDA, TN_ERR_UNSUPPORTED = range(7)
 TN_EDGE_SLICE, TN_EDGE_PIN, TN_EDGE_COMPANION = 0, 1, 2
 TN_C64, TN_C128 = 0, 1
-TN_GEMM_AUTO, TN_GEMM_TC_3XTF32, TN_GEMM_SIMT_FP32 = 0, 1, 2
+TN_GEMM_AUTO, TN_GEMM_TC_3XTF32, TN_GEMM_SIMT_FP32, TN_GEMM_TC_BF16X3 = 0, 1, 2, 3
 
 
 class TNError(RuntimeError):

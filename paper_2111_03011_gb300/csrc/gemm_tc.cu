@@ -6,7 +6,9 @@
 //     Bt = the real embedding of B, [2N][2K] K-major (built by k_bprep_tc).
 // FP32 accuracy from TF32 tensor cores by the 3xTF32 split
 //     A_r Bt ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
-// hi = round-to-tf32, lo = x - hi.  Both operands arrive pre-split in global
+// hi = round-to-tf32, lo = x - hi (or, in the BF16 engine, the same three
+// products of bf16 hi/lo parts on kind::f16: ~2^-16 relative per product, at
+// twice the tensor rate).  Both operands arrive pre-split in global
 // memory (A by the split-mode permute, B by k_bprep_tc), so the kernel is a
 // plain TMA -> MMA pipeline.
 //
@@ -37,7 +39,7 @@ namespace tn {
 namespace tc {
 
 constexpr int BM = 128;
-constexpr int BK = 32;                  // fp32 per 128-byte swizzle row
+constexpr int BK_BYTES = 128;           // one 128-byte swizzle row of K per k-block
 constexpr int kThreads = 192;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -98,17 +100,27 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = BN.
-template <int BN>
-__device__ __forceinline__ uint32_t idesc_tf32() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: D f32, A/B tf32 (format 2) or bf16 (format 1), both
+// K-major, M = 128, N = BN.
+template <int BN, bool BF16>
+__device__ __forceinline__ uint32_t idesc_mma() {
+  const uint32_t f = BF16 ? 1u : 2u;
+  return (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+// One MMA: K = 8 (tf32) or 16 (bf16), i.e. 32 bytes of each operand row.
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (BF16)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -141,8 +153,8 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 template <int BN, int STAGES>
 struct Layout {
-  static constexpr int A_BYTES = BM * BK * 4;          // one 128 x 32 fp32 tile
-  static constexpr int B_BYTES = BN * BK * 4;          // one BN x 32 fp32 tile
+  static constexpr int A_BYTES = BM * BK_BYTES;        // one 128-row tile, 128 bytes of K per row
+  static constexpr int B_BYTES = BN * BK_BYTES;        // one BN-row tile
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // A hi, A lo, B hi, B lo
   static constexpr int DATA = STAGES * STAGE;
   static constexpr int TOTAL = DATA + 1024 /*align*/ + 256 /*barriers*/;
@@ -174,7 +186,7 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t tilesM, int64_t t
   pc = a_shared ? pin : outer;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool BF16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
               const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
@@ -197,7 +209,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   tile_coords(blockIdx.x, tilesM, tilesN, PC, mapA_mode == 1 && PC > 1, pc, tm, tn_);
   const int64_t pa = mapA_mode == 0 ? pc : (mapA_mode == 1 ? 0 : (int64_t)mapA[pc]);
   const int64_t pb = mapB_mode == 0 ? pc : (mapB_mode == 1 ? 0 : (int64_t)mapB[pc]);
-  const int nkb = (int)((K2 + BK - 1) / BK);
+  constexpr int BKE = BF16 ? 64 : 32;     // K elements per k-block
+  const int nkb = (int)((K2 + BKE - 1) / BKE);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -229,15 +242,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(&empty[s], (uint32_t)((r & 1) ^ 1), abort_flag)) break;
         uint8_t* st = smem + s * Lay::STAGE;
         mbar_expect_tx(&full[s], (uint32_t)Lay::STAGE);
-        tma_load_3d(st, &tmAhi, &full[s], kb * BK, (int)(tm * BM), (int)pa);
-        tma_load_3d(st + Lay::A_BYTES, &tmAlo, &full[s], kb * BK, (int)(tm * BM), (int)pa);
-        tma_load_3d(st + 2 * Lay::A_BYTES, &tmBhi, &full[s], kb * BK, (int)(tn_ * BN), (int)pb);
-        tma_load_3d(st + 2 * Lay::A_BYTES + Lay::B_BYTES, &tmBlo, &full[s], kb * BK, (int)(tn_ * BN), (int)pb);
+        tma_load_3d(st, &tmAhi, &full[s], kb * BKE, (int)(tm * BM), (int)pa);
+        tma_load_3d(st + Lay::A_BYTES, &tmAlo, &full[s], kb * BKE, (int)(tm * BM), (int)pa);
+        tma_load_3d(st + 2 * Lay::A_BYTES, &tmBhi, &full[s], kb * BKE, (int)(tn_ * BN), (int)pb);
+        tma_load_3d(st + 2 * Lay::A_BYTES + Lay::B_BYTES, &tmBlo, &full[s], kb * BKE, (int)(tn_ * BN), (int)pb);
       }
     }
   } else if (warp == 5) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_tf32<BN>();
+      const uint32_t idesc = idesc_mma<BN, BF16>();
       for (int kb = 0; kb < nkb; ++kb) {
         // one k-block per TMEM chunk: buffer b alternates
         const int s = kb % STAGES, r = kb / STAGES, b = kb & 1;
@@ -251,15 +264,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         // small correction products first, so that the accumulator is still
         // small while they are added; the hi x hi products come last
 #pragma unroll
-        for (int kk = 0; kk < BK / 8; ++kk) {
-          const uint32_t o = kk * 32;  // 8 tf32 = 32 bytes along K
-          mma_tf32(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, kk > 0 ? 1u : 0u);
-          mma_tf32(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t o = kk * 32;  // one MMA's K = 32 bytes of each operand row
+          mma<BF16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, kk > 0 ? 1u : 0u);
+          mma<BF16>(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
         }
 #pragma unroll
-        for (int kk = 0; kk < BK / 8; ++kk) {
+        for (int kk = 0; kk < 4; ++kk) {
           const uint32_t o = kk * 32;
-          mma_tf32(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
+          mma<BF16>(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
         }
         mma_commit(&empty[s]);
         mma_commit(&accf[b]);
@@ -352,57 +365,67 @@ static EncodeTiledFn get_encode() {
 }
 
 static bool encode3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
-                     uint32_t b1) {
+                     uint32_t b1, bool bf16) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[3] = {d0, d1, d2};
-  cuuint64_t strides[2] = {d0 * 4, d0 * d1 * 4};
+  const uint64_t es_bytes = bf16 ? 2 : 4;
+  cuuint64_t strides[2] = {d0 * es_bytes, d0 * d1 * es_bytes};
   cuuint32_t box[3] = {b0, b1, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool BF16>
 static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   using Lay = Layout<BN, STAGES>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int64_t K2 = 2 * p.K, N2 = 2 * p.N;
-  // A: hi plane then lo plane, each fp32 [PA][M][2K]; B: hi plane then lo plane, each [PB][2N][2K]
-  const float* ahi = (const float*)p.A;
-  const float* alo = ahi + p.PA * p.M * K2;
-  const float* bhi = (const float*)p.B;
-  const float* blo = bhi + p.PB * N2 * K2;
+  const uint32_t BKE = BF16 ? 64 : 32;
+  const int64_t es = BF16 ? 2 : 4;
+  // A: hi plane then lo plane, each [PA][M][2K]; B: hi plane then lo plane, each [PB][2N][2K]
+  const char* ahi = (const char*)p.A;
+  const char* alo = ahi + p.PA * p.M * K2 * es;
+  const char* bhi = (const char*)p.B;
+  const char* blo = bhi + p.PB * N2 * K2 * es;
   CUtensorMap tah, tal, tbh, tbl;
-  if (!encode3d(&tah, ahi, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BK, BM)) return cudaErrorInvalidValue;
-  if (!encode3d(&tal, alo, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BK, BM)) return cudaErrorInvalidValue;
-  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BK, BN)) return cudaErrorInvalidValue;
-  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BK, BN)) return cudaErrorInvalidValue;
+  if (!encode3d(&tah, ahi, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, BF16)) return cudaErrorInvalidValue;
+  if (!encode3d(&tal, alo, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, BF16)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, BF16)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, BF16)) return cudaErrorInvalidValue;
   const int64_t tilesM = (p.M + BM - 1) / BM, tilesN = (N2 + BN - 1) / BN;
   const int64_t grid = tilesM * tilesN * p.PC;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_gemm_tc<BN, STAGES><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(tah, tal, tbh, tbl, (float*)p.C, p.M, N2, K2,
-                                                                      tilesM, tilesN, p.PC, p.mapA, p.mapB,
-                                                                      p.mapA_mode, p.mapB_mode, status);
+  k_gemm_tc<BN, STAGES, BF16><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(tah, tal, tbh, tbl, (float*)p.C, p.M, N2,
+                                                                            K2, tilesM, tilesN, p.PC, p.mapA, p.mapB,
+                                                                            p.mapA_mode, p.mapB_mode, status);
   return cudaGetLastError();
+}
+
+template <bool BF16>
+static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStream_t s) {
+  const int64_t N2 = 2 * p.N;
+  if (N2 <= 16) return run<16, 6, BF16>(p, status, s);
+  if (N2 <= 32) return run<32, 5, BF16>(p, status, s);
+  if (N2 <= 64) return run<64, 4, BF16>(p, status, s);
+  return run<128, 3, BF16>(p, status, s);
 }
 
 }  // namespace tc
 
 cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s) {
-  if (p.K < 2) return cudaErrorInvalidValue;  // row pitch 2K*4 bytes must be a multiple of 16
-  const int64_t N2 = 2 * p.N;
-  if (N2 <= 16) return tc::run<16, 6>(p, status, s);
-  if (N2 <= 32) return tc::run<32, 5>(p, status, s);
-  if (N2 <= 64) return tc::run<64, 4>(p, status, s);
-  return tc::run<128, 3>(p, status, s);
+  // row pitch of A (2K elements) must be a multiple of 16 bytes
+  if (p.K < (p.bf16 ? 4 : 2)) return cudaErrorInvalidValue;
+  return p.bf16 ? tc::dispatch<true>(p, status, s) : tc::dispatch<false>(p, status, s);
 }
 
 }  // namespace tn

@@ -1,6 +1,8 @@
 // Streaming kernels of the contraction path (HBM-bound steps), the plain
 // FP32 CUDA-core complex GEMM, slice accumulation, amplitude lookup, norms and
 // the group sampler.
+#include <cuda_bf16.h>
+
 #include <cstdio>
 
 #include "kernels.h"
@@ -102,8 +104,9 @@ cudaError_t launch_small(const SmallParams& p, cudaStream_t s) {
 // that the strided reads of the write phase fall into different banks.  The
 // tile's base addresses (the remaining "rest" bits of the tile index scattered
 // to their positions) come from four 256-entry tables per direction.
-// SPLIT: the output is written as two fp32 planes, tf32-rounded hi and the
-// remainder lo, the operand format of the tensor-core GEMM.
+// SPLIT 1: the output is written as two fp32 planes, tf32-rounded hi and the
+// remainder lo; SPLIT 2: two bf16 planes, bf16 hi and the bf16-rounded
+// remainder -- the operand formats of the two tensor-core GEMM engines.
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
 __device__ __forceinline__ float tf32_rn(float x) {
@@ -112,7 +115,7 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(r);
 }
 
-template <bool SPLIT>
+template <int SPLIT>
 __global__ void __launch_bounds__(256) k_permute(PermParams p) {
   extern __shared__ float2 tile[];
   const int nt = 1 << p.t;
@@ -158,10 +161,17 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
 #pragma unroll 4
     for (int j = threadIdx.x; j < nt; j += blockDim.x) {
       const float2 v = tile[s_slot[j]];
-      if (SPLIT) {
+      if (SPLIT == 1) {
         const float2 h = make_float2(tf32_rn(v.x), tf32_rn(v.y));
         p.out[dofs + s_out[j]] = h;
         out_lo[dofs + s_out[j]] = make_float2(v.x - h.x, v.y - h.y);
+      } else if (SPLIT == 2) {
+        __nv_bfloat162* bh = (__nv_bfloat162*)p.out;
+        __nv_bfloat162* bl = bh + p.P * p.pstride;
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        const float2 hf = __bfloat1622float2(h);
+        bh[dofs + s_out[j]] = h;
+        bl[dofs + s_out[j]] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
       } else {
         p.out[dofs + s_out[j]] = v;
       }
@@ -176,8 +186,9 @@ cudaError_t launch_permute(const PermParams& p, cudaStream_t s) {
   const int nt = 1 << p.t;
   const size_t smem = sizeof(float2) * (size_t)(nt + (nt >> 5) + 2) + 3 * sizeof(uint32_t) * (size_t)nt + 8 +
                       2 * 1024 * sizeof(uint64_t);
-  if (p.split) k_permute<true><<<(unsigned)grid, 256, smem, s>>>(p);
-  else k_permute<false><<<(unsigned)grid, 256, smem, s>>>(p);
+  if (p.split == 1) k_permute<1><<<(unsigned)grid, 256, smem, s>>>(p);
+  else if (p.split == 2) k_permute<2><<<(unsigned)grid, 256, smem, s>>>(p);
+  else k_permute<0><<<(unsigned)grid, 256, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -221,6 +232,25 @@ __global__ void k_bprep_tc(BPrepParams p) {
   }
 }
 
+// The same embedding as bf16 hi/lo planes for the bf16 engine.
+__global__ void k_bprep_tc_bf16(BPrepParams p) {
+  const int64_t K2 = 2LL << p.nk, N2 = 2LL << p.nn;
+  const int64_t per = K2 * N2;
+  const int64_t total = p.PB * per;
+  __nv_bfloat16* hi = (__nv_bfloat16*)p.out;
+  __nv_bfloat16* lo = hi + total;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pb = e / per, r = e % per;
+    const int64_t j = r / K2, i = r % K2;
+    const float2 b = p.B[pb * p.b_pstride + p.bk[i >> 1] + p.bn[j >> 1]];
+    const int jc = (int)(j & 1), ic = (int)(i & 1);
+    const float v = jc == 0 ? (ic == 0 ? b.x : -b.y) : (ic == 0 ? b.y : b.x);
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
 cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s) {
   const int64_t total = p.PB << (p.nk + p.nn);
   const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 8);
@@ -231,7 +261,8 @@ cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s) {
 cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s) {
   const int64_t total = p.PB << (p.nk + p.nn + 2);
   const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 8);
-  k_bprep_tc<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
+  if (p.bf16) k_bprep_tc_bf16<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
+  else k_bprep_tc<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

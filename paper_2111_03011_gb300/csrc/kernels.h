@@ -27,7 +27,7 @@ struct PermParams {
   int n_rest;
   uint8_t rest_in[64], rest_out[64];
   const uint32_t* tab;   // in_off[2^t], out_off[2^t], slot[2^t]
-  int split;             // 1: write tf32 hi plane then lo plane (fp32 pairs)
+  int split;             // 1: write tf32 hi plane then lo plane (fp32 pairs); 2: bf16 planes
 };
 
 struct BPrepParams {
@@ -35,6 +35,7 @@ struct BPrepParams {
   int64_t b_pstride, PB;
   int nk, nn;
   const uint32_t* bk; const uint32_t* bn;
+  int bf16;              // tensor-core B: 0 tf32 planes, 1 bf16 planes
 };
 
 // C[p][m][n] = sum_k A[mapA(p)][m][k] B[mapB(p)][k][n]
@@ -44,6 +45,7 @@ struct GemmParams {
   int64_t PA, PB, PC;
   const uint32_t* mapA; const uint32_t* mapB;
   int mapA_mode, mapB_mode;
+  int bf16;              // tensor-core engine: operands are bf16 hi/lo planes
 };
 
 struct AccumParams {

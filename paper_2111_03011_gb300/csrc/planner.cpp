@@ -464,10 +464,10 @@ static void set_map(Plan& plan, const VTensor& X, const VTensor& C, int& mode, i
 }
 
 static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& target, Ref out, int ci,
-                        bool split) {
+                        int split) {
   Step s;
   s.kind = ST_PERMUTE;
-  s.split = split ? 1 : 0;
+  s.split = split;
   s.a = X.ref;
   s.c = out;
   s.contraction = ci;
@@ -515,7 +515,7 @@ static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& ta
       s.rest_out[s.n_rest] = (uint8_t)inv[x];
       ++s.n_rest;
     }
-  s.bytes = (split ? 24.0 : 16.0) * (double)vt_elems(X);
+  s.bytes = (split == 1 ? 24.0 : 16.0) * (double)vt_elems(X);
   plan.steps.push_back(s);
 }
 
@@ -611,19 +611,22 @@ static int layout_steps(Plan& plan, std::string& err) {
       for (int l : K) target.push_back(l);
       for (int l : M) target.push_back(l);
       Ref aref = big.ref;
+      // bf16 operands need K >= 4 (16-byte rows); K = 2 steps use the tf32 kernel
+      const bool bf16 = plan.gemm_engine == TN_GEMM_TC_BF16X3 && nk >= 2;
       const bool tc = plan.gemm_engine != TN_GEMM_SIMT_FP32 && nk >= 1;
       if (tc || target != big.legs) {
-        // the tensor-core GEMM reads A as tf32 hi/lo planes: always a (possibly
+        // the tensor-core GEMM reads A as hi/lo planes: always a (possibly
         // identity) permute in split mode
         const int st = (int)plan.steps.size();
         touch(plan, big.ref, st);
-        Ref out{1, new_buf(plan, vt_elems(big) * 8 * (tc ? 2 : 1), st)};
-        add_permute(plan, big, target, out, ci, tc);
+        Ref out{1, new_buf(plan, vt_elems(big) * 8 * (tc && !bf16 ? 2 : 1), st)};
+        add_permute(plan, big, target, out, ci, tc ? (bf16 ? 2 : 1) : 0);
         aref = out;
       }
       // B' prep
       Step p;
       p.kind = tc ? ST_BPREP_TC : ST_BPREP_C;
+      p.bf16 = bf16 ? 1 : 0;
       p.contraction = ci;
       p.a = sml.ref;
       p.rA = (int)sml.legs.size();
@@ -631,7 +634,8 @@ static int layout_steps(Plan& plan, std::string& err) {
       p.nk = nk; p.nn = nn;
       p.bk_off = meta_push(plan, bk);
       p.bn_off = meta_push(plan, bn);
-      const int64_t bprep_bytes = tc ? 2LL * sml.P * (2LL << nn) * (2LL << nk) * 4 : sml.P * (1LL << (nk + nn)) * 8;
+      const int64_t bprep_bytes =
+          tc ? 2LL * sml.P * (2LL << nn) * (2LL << nk) * (bf16 ? 2 : 4) : sml.P * (1LL << (nk + nn)) * 8;
       {
         const int st = (int)plan.steps.size();
         touch(plan, sml.ref, st);
@@ -641,6 +645,7 @@ static int layout_steps(Plan& plan, std::string& err) {
       }
       Step g;
       g.kind = tc ? ST_GEMM_TC : ST_GEMM_SIMT;
+      g.bf16 = bf16 ? 1 : 0;
       g.contraction = ci;
       g.a = aref;
       g.b = p.c;
@@ -923,7 +928,7 @@ std::string describe_plan(const Plan& plan, bool with_data) {
       << ",\"PA\":" << st.PA << ",\"PB\":" << st.PB << ",\"PC\":" << st.PC << ",\"macs\":" << st.macs
       << ",\"bytes\":" << st.bytes << ",\"rA\":" << st.rA << ",\"rB\":" << st.rB << ",\"rC\":" << st.rC
       << ",\"a\":[" << st.a.kind << "," << st.a.id << "],\"b\":[" << st.b.kind << "," << st.b.id << "],\"c\":["
-      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split
+      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"bf16\":" << st.bf16
       << ",\"tab_off\":" << st.tab_off << ",\"n_rest\":" << st.n_rest << ",\"rest_in\":[";
     for (int v = 0; v < st.n_rest; ++v) o << (v ? "," : "") << (int)st.rest_in[v];
     o << "],\"rest_out\":[";

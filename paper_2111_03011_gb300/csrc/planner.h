@@ -88,7 +88,8 @@ struct Step {
   uint32_t boffK[16] = {0}, boffN[16] = {0};
   // PERMUTE: tile bits t; tables in meta: in_off[2^t], out_off[2^t], slot[2^t]
   int t_bits = 0;
-  int split = 0;           // PERMUTE: write tf32 hi/lo planes (tensor-core GEMM operand)
+  int split = 0;           // PERMUTE: 1 tf32 hi/lo planes, 2 bf16 hi/lo planes (tensor-core GEMM operand)
+  int bf16 = 0;            // BPREP_TC / GEMM_TC: bf16 operand planes
   int64_t tab_off = 0;
   int n_rest = 0;
   uint8_t rest_in[64] = {0}, rest_out[64] = {0};
