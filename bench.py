@@ -312,6 +312,76 @@ def cpu_baseline(cfg, st, repeats=1):
                       f"{cfg['name']}, complex128 numpy tensordot; flops = plan T_c per slice / L groups"}
 
 
+def run_serve(args):
+    """Serving form: a Poisson stream of amplitude-batch and sampling requests
+    on a mix of circuits through the library's request server; p50/p99
+    latency and throughput, tensor-core engine vs the plain complex64 engine."""
+    import torch
+
+    import paper_2111_03011_gb300 as tn
+    torch.cuda.set_device(0)
+    mix = ci.serving_mix()
+    reqs = ci.poisson_requests(args.requests, args.rate, len(mix))
+    rng = np.random.default_rng(11)
+    bits_of = []
+    for q in reqs:
+        cfg = mix[q["circuit"]]
+        if q["kind"] == 0:
+            oq, tails = cfg["open_qubits"], cfg["tails"]
+            g = rng.integers(0, len(tails), q["n"])
+            mu = rng.integers(0, 1 << len(oq), q["n"]).astype(np.uint64)
+            mask = np.uint64(sum(1 << x for x in oq))
+            b = tails[g].astype(np.uint64) & ~mask
+            for j, x in enumerate(oq):
+                b |= ((mu >> np.uint64(j)) & np.uint64(1)) << np.uint64(x)
+            bits_of.append(b)
+        else:
+            bits_of.append(None)
+    results = {}
+    for engine, gemm in (("tc", tn.TN_GEMM_TC_3XTF32), ("simt", tn.TN_GEMM_SIMT_FP32)):
+        plans = [tn.tn_plan(c["circuit"], c["open_qubits"], c["tails"], c["edges"], gemm=gemm, order_trials=16)
+                 for c in mix]
+        sv = tn.tn_server_create(n_slots=8, hbm_budget_bytes=8 << 30)
+        for p in plans:
+            k = tn.tn_plan_get_stats(p)["n_sliced"]
+            tn.tn_server_add_circuit(sv, p, 0, 1 << k)
+        # warm-up: build every head once, outside the measurement
+        for cid in range(len(mix)):
+            tn.tn_server_wait(sv, tn.tn_server_submit(sv, cid, tn.TN_REQ_SAMPLE, 8, seed=1))
+        base = tn.tn_server_get_stats(sv)["completed"]
+        t0 = time.time()
+        tickets = []
+        lat = []
+        for q, b in zip(reqs, bits_of):
+            dt = q["t"] - (time.time() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            if q["kind"] == 0:
+                tickets.append(tn.tn_server_submit(sv, q["circuit"], tn.TN_REQ_AMPLITUDES, 0, bitstrings=b))
+            else:
+                tickets.append(tn.tn_server_submit(sv, q["circuit"], tn.TN_REQ_SAMPLE, q["n"], seed=q["seed"]))
+        for t in tickets:
+            lat.append(tn.tn_server_wait(sv, t)[1])
+        wall = time.time() - t0
+        st = tn.tn_server_get_stats(sv)
+        lat = np.sort(np.array(lat))
+        n_amp = sum(q["n"] for q in reqs if q["kind"] == 0)
+        results[engine] = {"p50_ms": round(float(np.percentile(lat, 50)) / 1e3, 3),
+                           "p99_ms": round(float(np.percentile(lat, 99)) / 1e3, 3),
+                           "requests_per_s": round(len(reqs) / wall, 1),
+                           "amplitudes_per_s": round(n_amp / wall, 1),
+                           "completed": st["completed"] - base, "evictions": st["evictions"]}
+        tn.tn_server_free(sv)
+    out = {"metric": "p99 request latency", "value": results["tc"]["p99_ms"], "unit": "ms",
+           "higher_is_better": False, "n_gpus": 1, "mode": "serving",
+           "config": {"workload": "poisson mix of 6 circuits (20-25 qubits, 8-12 cycles, 6-8 open, 32-256 tails)",
+                      "requests": args.requests, "rate_per_s": args.rate, "slots": 8,
+                      "sizes": "amplitude batches 1e3-1e5 (log-uniform), samples 1e2-1e4"},
+           "tc_3xtf32": results["tc"], "plain_c64_simt": results["simt"],
+           "p99_vs_plain_c64": round(results["tc"]["p99_ms"] / results["simt"]["p99_ms"], 3)}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -356,9 +426,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sliced30", choices=["sliced30", "tiny", "grid25"])
+    ap.add_argument("--workload", default="sliced30", choices=["sliced30", "tiny", "grid25", "serve"])
     ap.add_argument("--engine", default="tc", choices=["tc", "simt", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=300, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--slices", type=int, default=0,
                     help="contract only the first N slices per step (for ncu launch lists; not a bench number)")
     args = ap.parse_args()
@@ -366,6 +438,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -239,6 +239,37 @@ def config_grid25():
                 n_samples=1000, sample_seed=6, name="grid5x5_m10_open25")
 
 
+def serving_mix(seed=5, n_circuits=6):
+    """Seeded mix of 20-25 qubit grid circuits (8-12 cycles, 6-8 open qubits,
+    32-256 tails, 0-2 cut gates) for the serving workload."""
+    rng = np.random.default_rng(seed)
+    shapes = [(4, 5), (4, 6), (5, 5), (4, 5), (5, 5), (4, 6)]
+    out = []
+    for i in range(n_circuits):
+        r, c = shapes[i % len(shapes)]
+        m = int(rng.integers(8, 13))
+        h = int(rng.integers(6, 9))
+        L = int(2 ** rng.integers(5, 9))
+        cut = int(rng.integers(0, 3))
+        cfg = config_small(r, c, m, seed=100 + i, n_open=h, L=L, n_cut_gates=cut, tail_seed=200 + i)
+        cfg["name"] = f"grid{r}x{c}_m{m}_h{h}_L{L}_k{2 * cut}"
+        out.append(cfg)
+    return out
+
+
+def poisson_requests(n_requests, rate_per_s, n_circuits, seed=9):
+    """Seeded request stream: arrival times (Poisson), circuit ids, kinds
+    (70 % amplitude batches, 30 % sampling) and log-uniform sizes."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, n_requests))
+    circ = rng.integers(0, n_circuits, n_requests)
+    kind = (rng.random(n_requests) < 0.3).astype(int)
+    size = np.where(kind == 0, 10 ** rng.uniform(3, 5, n_requests), 10 ** rng.uniform(2, 4, n_requests)).astype(int)
+    seeds = rng.integers(0, 1 << 40, n_requests)
+    return [dict(t=float(t[i]), circuit=int(circ[i]), kind=int(kind[i]), n=int(size[i]), seed=int(seeds[i]))
+            for i in range(n_requests)]
+
+
 def config_small(rows=4, cols=4, cycles=8, seed=11, n_open=6, L=8, n_cut_gates=2, tail_seed=12):
     """Scaled-down sliced sparse-state case used by parity tests."""
     circ = make_grid_circuit(rows, cols, cycles, seed=seed)

@@ -75,8 +75,12 @@ typedef struct {
  * PIN:   fixed at `value` for every slice -- an edge broken by inserting
  *        E = (1,0)x(1,0) (value 0), each halving the fidelity estimate
  *        (Method, edge breaking); both inputs of one fSim pinned drill a hole.
- * COMPANION: rank-one companion cut (Method case (ii)); not implemented, rejected
- *        with TN_ERR_UNSUPPORTED. */
+ * COMPANION: slice the input leg like SLICE (it takes its slice bit) and, in the
+ *        same slice, fix the partner qubit's output of the same two-qubit gate
+ *        to the same value: the rank-one companion cut of Method case (ii)
+ *        (pinning input a of an fSim to v keeps the partner output at v; the
+ *        supplement's singular values of the sliced fSim).  It multiplies F_est
+ *        by the kept norm fraction, (1 + sin^2 theta)/2 for an fSim. */
 typedef struct { int gate; int leg; int kind; int value; } tn_edge;
 typedef struct { int64_t begin, end; } tn_range;
 
@@ -139,7 +143,8 @@ void tn_head_free(tn_head_t* head);
 void* tn_head_data(tn_head_t* head);  /* device pointer of H */
 /* Zero H (asynchronously on `stream`) and forget the accumulated slices. */
 int  tn_head_reset(tn_head_t* head, void* stream);
-/* F_est = 2^-n_pinned * slices_done / 2^k (fidelity-estimate equation). */
+/* F_est = 2^-n_pinned * slices_done / 2^k * prod over companion cuts of
+ * their kept norm fraction (fidelity-estimate equation). */
 int  tn_head_fidelity(const tn_head_t* head, double* f_est, int64_t* slices_done);
 /* Override F_est for a head filled by the caller (not by contraction). */
 int  tn_head_set_fidelity(tn_head_t* head, double f_est);
@@ -148,6 +153,19 @@ int  tn_head_set_fidelity(tn_head_t* head, double f_est);
  * on `stream`.  A slice already accumulated into this head is rejected
  * (TN_ERR_INVALID) -- ranges are additive and may come from several calls. */
 int  tn_contract_slices(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, void* stream);
+
+/* Batched form.  tn_contract_slices_graph: the same result as
+ * tn_contract_slices, but the range's launches are captured once into a CUDA
+ * graph (cached per plan, range and head buffer) and replayed on `stream`.
+ * tn_contract_batch: items (plans[i], ranges[i], heads[i]) as parallel
+ * branches of one graph (items of the same plan share a branch, since they
+ * share its workspace), so many small contractions overlap on the GPU; the
+ * last batch's graph is cached per thread and replayed when the same batch is
+ * submitted again.  Both asynchronous on `stream`; both reject slices already
+ * accumulated into a head, and a batch rejects a head listed twice. */
+int  tn_contract_slices_graph(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, void* stream);
+int  tn_contract_batch(tn_plan_t* const* plans, const tn_range* ranges, tn_head_t* const* heads, int n,
+                       void* stream);
 
 /* out[i] = H[g(s_i)][mu(s_i)] for n bitstrings.  `bitstrings` and `out` may be
  * host or device pointers; dtype TN_C64 or TN_C128.  Synchronises `stream`.
@@ -165,6 +183,65 @@ int  tn_amplitudes(tn_head_t* head, const uint64_t* bitstrings, int64_t n,
  * out_bitstrings may be host or device memory; synchronises `stream`. */
 int  tn_sample(tn_head_t* head, int64_t n, double target_fidelity, uint64_t seed,
                uint64_t* out_bitstrings, void* stream);
+
+/* Sampling methods of tn_sample_ex.
+ *   EXACT: as tn_sample (exact in-group categorical draw).
+ *   METROPOLIS: the paper's in-group Markov chain (Method, last paragraph;
+ *     Supplement, validation): start at member 0, param proposals mu' uniform
+ *     over the group (Philox counter (i, 2, t)), accept when u*w(mu) < w(mu'),
+ *     w = |H|^2; param = 0 means l = 2^h proposals.
+ *   FRUGAL: rejection sampling valid under Porter-Thomas (Supplement, bitstring
+ *     choice): a uniform member (counter (i, 3, t)) is accepted when
+ *     u*M*Z < w(mu)*l, Z the group's sum; at most 64*M rounds, the last
+ *     candidate kept; param = M (0 means 10).
+ * Uniform mixing for target_fidelity applies to every method as in tn_sample. */
+enum { TN_SAMPLE_EXACT = 0, TN_SAMPLE_METROPOLIS = 1, TN_SAMPLE_FRUGAL = 2 };
+int  tn_sample_ex(tn_head_t* head, int64_t n, double target_fidelity, uint64_t seed, int method, int64_t param,
+                  uint64_t* out_bitstrings, void* stream);
+
+/* ------------------------------------------------------------------ serving
+ * A request server with continuous admission.  Circuits (a plan and its kept
+ * slice range) are registered first.  Requests -- amplitude lookups or
+ * samples on one circuit -- are queued by tn_server_submit and admitted by a
+ * dispatcher thread into one of n_slots slots (each its own CUDA stream) as
+ * soon as a slot is free and the circuit's head fits the HBM budget, so
+ * requests arriving while others run overlap with them on the device.  The
+ * first request on a circuit contracts its head (cached in HBM afterwards;
+ * idle heads are evicted least-recently-used when a new one does not fit);
+ * other requests on it wait for the head on the device.  Request buffers are
+ * host memory and must stay valid until tn_server_wait returns.  Results are
+ * those of tn_amplitudes / tn_sample_ex on the same head.  Plans registered
+ * with a server must not be used by other calls while it runs. */
+typedef struct { int n_slots; int64_t hbm_budget_bytes; } tn_server_opts;   /* 0: 8 slots, 64 GiB */
+typedef struct tn_server tn_server_t;
+enum { TN_REQ_AMPLITUDES = 0, TN_REQ_SAMPLE = 1 };
+typedef struct {
+  int circuit;                 /* id from tn_server_add_circuit */
+  int kind;                    /* TN_REQ_* */
+  const uint64_t* bitstrings;  /* amplitudes: n bitstrings (host) */
+  int64_t n;                   /* bitstrings, or samples */
+  void* out;                   /* host: n amplitudes (dtype) or n uint64 samples */
+  int dtype;                   /* amplitudes: TN_C64 / TN_C128 */
+  double target_fidelity;      /* samples: as tn_sample */
+  uint64_t seed;               /* samples */
+  int method;                  /* samples: TN_SAMPLE_* */
+  int64_t param;               /* samples: as tn_sample_ex */
+} tn_request;
+typedef struct { int status; double latency_us; double queue_us; } tn_request_result;
+typedef struct {
+  int64_t completed, failed, in_flight, queued;
+  double p50_us, p99_us, mean_us;   /* submit -> result in the caller's buffer */
+  int64_t heads_cached, head_bytes, evictions;
+  double wall_s;
+} tn_server_stats;
+int  tn_server_create(const tn_server_opts* opts, tn_server_t** out);
+int  tn_server_add_circuit(tn_server_t* server, tn_plan_t* plan, tn_range kept, int* circuit_id);
+int  tn_server_submit(tn_server_t* server, const tn_request* request, uint64_t* ticket);
+/* Blocks until the request is done; returns its status (TN_ERR_NOT_IN_STATE
+ * for a bitstring outside the sparse state, with `out` holding 0 there). */
+int  tn_server_wait(tn_server_t* server, uint64_t ticket, tn_request_result* result);
+int  tn_server_get_stats(tn_server_t* server, tn_server_stats* out);
+void tn_server_free(tn_server_t* server);   /* drains the queue first */
 
 /* Squared norm N = sum |H|^2 (FP64) and, if group_norms != NULL, the L
  * per-group sums (host memory).  Synchronises `stream`. */

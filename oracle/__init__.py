@@ -21,4 +21,4 @@ from .statevector import (statevector, sliced_statevector, sparse_state_from_vec
 from .network import network_amplitudes
 from .metrics import (fidelity, f_estimate, companion_factor, linear_xeb, expected_group_sampler_xeb,
                       porter_thomas_ks, gpu_efficiency, normalised_probabilities)
-from .sampler import philox4x32_10, sample_groups
+from .sampler import philox4x32_10, sample_groups, sample_groups_mcmc

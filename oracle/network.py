@@ -38,7 +38,7 @@ class _Net:
         self.next_id += 1
 
 
-def _build(circ, cuts, open_qubits, tail):
+def _build(circ, cuts, open_qubits, tail, post_cuts=()):
     n = circ.n_qubits
     net = _Net()
     wire = []
@@ -49,6 +49,9 @@ def _build(circ, cuts, open_qubits, tail):
     by_gate = {}
     for (g, leg, v) in cuts:
         by_gate.setdefault(int(g), []).append((int(leg), int(v)))
+    after = {}
+    for (g, leg, v) in post_cuts:
+        after.setdefault(int(g), []).append((int(leg), int(v)))
     for gi, gate in enumerate(circ.gates):
         for (leg, v) in by_gate.get(gi, ()):
             # |v><v| on the wire written as its two factors: the wire ends in
@@ -68,6 +71,14 @@ def _build(circ, cuts, open_qubits, tail):
             e0, e1 = net.label(), net.label()
             net.add(gate.U.reshape(2, 2, 2, 2), [e0, e1, wire[gate.q0], wire[gate.q1]])
             wire[gate.q0], wire[gate.q1] = e0, e1
+        for (leg, v) in after.get(gi, ()):
+            q = gate.q0 if leg == 0 else gate.q1
+            vec = np.zeros(2)
+            vec[v] = 1.0
+            net.add(vec, [wire[q]])
+            e = net.label()
+            net.add(vec.copy(), [e])
+            wire[q] = e
     open_set = set(int(q) for q in open_qubits)
     for q in range(n):
         if q in open_set:
@@ -175,7 +186,9 @@ def network_amplitudes(circ, open_qubits, tails, sliced_edges=(), pins=(), slice
                        groups=None) -> np.ndarray:
     """H[g][mu] for the selected groups (all by default), mu bit j = open_qubits[j].
 
-    sliced_edges: [(gate, leg)] enumerated as slice id bits; pins: [(gate, leg, value)]."""
+    sliced_edges: [(gate, leg)] or [(gate, leg, companion)] enumerated as slice id
+    bits (a companion also fixes the partner output, as in sliced_statevector);
+    pins: [(gate, leg, value)]."""
     h = len(open_qubits)
     k = len(sliced_edges)
     if slice_range is None:
@@ -186,8 +199,14 @@ def network_amplitudes(circ, open_qubits, tails, sliced_edges=(), pins=(), slice
     H = np.zeros((len(groups), 1 << h), dtype=np.complex128)
     for gi, g in enumerate(groups):
         for s in range(*slice_range):
-            cuts = [(ge, leg, (s >> j) & 1) for j, (ge, leg) in enumerate(sliced_edges)] + list(pins)
-            net, out_labels = _build(circ, cuts, open_qubits, tails[g])
+            cuts, post = [], []
+            for j, e in enumerate(sliced_edges):
+                v = (s >> j) & 1
+                cuts.append((e[0], e[1], v))
+                if len(e) > 2 and e[2]:
+                    post.append((e[0], 1 - e[1], v))
+            cuts += list(pins)
+            net, out_labels = _build(circ, cuts, open_qubits, tails[g], post)
             arr, labs = _contract(net, out_labels)
             # order axes as (open[h-1], ..., open[0]) so C-order flattening gives mu
             perm = [labs.index(out_labels[j]) for j in range(h - 1, -1, -1)]

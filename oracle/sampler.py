@@ -89,3 +89,75 @@ def sample_groups(H, tails, open_qubits, n_qubits, n_samples, target_fidelity, f
             s |= ((mu >> j) & 1) << int(q)
         out[i] = s
     return out
+
+
+def _weights_rn(Hg):
+    # |h|^2 as re*re + im*im, each operation rounded to nearest
+    return Hg.real * Hg.real + Hg.imag * Hg.imag
+
+
+def _emit(tail, open_qubits, open_mask, mu):
+    s = int(tail) & ~open_mask
+    for j, q in enumerate(open_qubits):
+        s |= ((mu >> j) & 1) << int(q)
+    return s
+
+
+def sample_groups_mcmc(H, tails, open_qubits, n_qubits, n_samples, target_fidelity, f_head, seed,
+                       method, param):
+    """In-group Markov chain (method "metropolis", param = chain length T) or
+    frugal rejection (method "frugal", param = bound M), one sample per group
+    (Method; Supplement, bitstring choice and validation).  Random numbers from
+    Philox-4x32-10 with counter words (i_lo, i_hi, c2, t): c2 = 0 mixing and
+    pick, c2 = 1 uniform bitstring, c2 = 2 chain step t, c2 = 3 frugal round t.
+
+    Metropolis: start at member 0; propose mu' = low bits of word 0, accept when
+    u * w(mu) < w(mu') (u from words 2-3), which leaves the law w/Z stationary.
+    Frugal: candidate mu = low bits of word 0, accepted when
+    (u * M) * Z < w(mu) * l; after 64 M rounds the last candidate is kept."""
+    H = np.asarray(H)
+    L, l = H.shape
+    seed = int(seed)
+    key = (seed & _MASK, (seed >> 32) & _MASK)
+    mix = 0.0
+    if target_fidelity > 0.0 and f_head > 0.0 and target_fidelity < f_head:
+        mix = 1.0 - target_fidelity / f_head
+    full = (1 << n_qubits) - 1 if n_qubits < 64 else (1 << 64) - 1
+    open_mask = 0
+    for q in open_qubits:
+        open_mask |= 1 << int(q)
+    out = np.zeros(n_samples, dtype=np.uint64)
+    for i in range(n_samples):
+        g = i % L
+        lo, hi = i & _MASK, (i >> 32) & _MASK
+        r0, r1, _, _ = philox4x32_10((lo, hi, 0, 0), key)
+        if mix > 0.0 and _u53(r0, r1) * 2.0 ** -53 < mix:
+            b0, b1, _, _ = philox4x32_10((lo, hi, 1, 0), key)
+            out[i] = ((b1 << 32) | b0) & full
+            continue
+        w = _weights_rn(H[g])
+        if method == "metropolis":
+            cur, wc = 0, w[0]
+            for t in range(int(param)):
+                q0, _, q2, q3 = philox4x32_10((lo, hi, 2, t), key)
+                prop = q0 & (l - 1)
+                u = _u53(q2, q3) * 2.0 ** -53
+                if u * wc < w[prop]:
+                    cur, wc = prop, w[prop]
+            mu = cur
+        elif method == "frugal":
+            M = float(param)
+            Z = float(np.sum(w))
+            bound = M * Z
+            cand = 0
+            for t in range(64 * int(param)):
+                q0, _, q2, q3 = philox4x32_10((lo, hi, 3, t), key)
+                cand = q0 & (l - 1)
+                u = _u53(q2, q3) * 2.0 ** -53
+                if u * bound < w[cand] * l:
+                    break
+            mu = cand
+        else:
+            raise ValueError(method)
+        out[i] = _emit(tails[g], open_qubits, open_mask, mu)
+    return out

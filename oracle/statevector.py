@@ -48,14 +48,19 @@ def project(psi: np.ndarray, n: int, q: int, v: int) -> np.ndarray:
     return t.reshape(-1)
 
 
-def statevector(circ, cuts=()) -> np.ndarray:
+def statevector(circ, cuts=(), post_cuts=()) -> np.ndarray:
     """Final state of `circ` from |0...0> with every edge in `cuts` fixed.
 
-    cuts: iterable of (gate_index, leg, value)."""
+    cuts: iterable of (gate_index, leg, value), the wire entering the gate;
+    post_cuts: iterable of (gate_index, leg, value), the wire leaving the gate
+    on that leg's qubit (the companion edge of Method case (ii))."""
     n = circ.n_qubits
     by_gate = {}
     for (g, leg, v) in cuts:
         by_gate.setdefault(int(g), []).append((int(leg), int(v)))
+    after = {}
+    for (g, leg, v) in post_cuts:
+        after.setdefault(int(g), []).append((int(leg), int(v)))
     psi = np.zeros(1 << n, dtype=np.complex128)
     psi[0] = 1.0
     for gi, gate in enumerate(circ.gates):
@@ -66,20 +71,33 @@ def statevector(circ, cuts=()) -> np.ndarray:
             psi = apply_1q(psi, n, gate.q0, gate.U)
         else:
             psi = apply_2q(psi, n, gate.q0, gate.q1, gate.U)
+        for (leg, v) in after.get(gi, ()):
+            q = gate.q0 if leg == 0 else gate.q1
+            psi = project(psi, n, q, v)
     return psi
 
 
 def sliced_statevector(circ, sliced_edges, pins=(), slice_range=None) -> np.ndarray:
     """Sum over slices s in slice_range of the state with sliced edge j fixed to
-    (s >> j) & 1 and every pin fixed (Supplement, slicing figure)."""
+    (s >> j) & 1 and every pin fixed (Supplement, slicing figure).
+
+    A sliced edge (gate, leg, True) is a companion cut: in slice s the partner
+    qubit's output of that gate is fixed to the same value (Method case (ii):
+    the rank-one approximation keeps the partner output at the pinned value)."""
     k = len(sliced_edges)
     if slice_range is None:
         slice_range = (0, 1 << k)
     acc = np.zeros(1 << circ.n_qubits, dtype=np.complex128)
     for s in range(*slice_range):
-        cuts = [(g, leg, (s >> j) & 1) for j, (g, leg) in enumerate(sliced_edges)]
+        cuts, post = [], []
+        for j, e in enumerate(sliced_edges):
+            g, leg = e[0], e[1]
+            v = (s >> j) & 1
+            cuts.append((g, leg, v))
+            if len(e) > 2 and e[2]:
+                post.append((g, 1 - leg, v))
         cuts += [(g, leg, v) for (g, leg, v) in pins]
-        acc += statevector(circ, cuts)
+        acc += statevector(circ, cuts, post)
     return acc
 
 

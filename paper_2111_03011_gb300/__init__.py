@@ -20,6 +20,8 @@ from .buildlib import LIBPATH, build
 TN_OK, TN_ERR_INVALID, TN_ERR_OOM, TN_ERR_NOT_IN_STATE, TN_ERR_TIMEOUT, TN_ERR_CUDA, TN_ERR_UNSUPPORTED = range(7)
 TN_EDGE_SLICE, TN_EDGE_PIN, TN_EDGE_COMPANION = 0, 1, 2
 TN_C64, TN_C128 = 0, 1
+TN_SAMPLE_EXACT, TN_SAMPLE_METROPOLIS, TN_SAMPLE_FRUGAL = 0, 1, 2
+TN_REQ_AMPLITUDES, TN_REQ_SAMPLE = 0, 1
 TN_GEMM_AUTO, TN_GEMM_TC_3XTF32, TN_GEMM_SIMT_FP32, TN_GEMM_TC_BF16X3 = 0, 1, 2, 3
 
 
@@ -55,6 +57,30 @@ class tn_plan_opts(C.Structure):
     _fields_ = [("max_log2_elements", C.c_double), ("gemm", C.c_int), ("host_only", C.c_int),
                 ("order_trials", C.c_int), ("order_seed", C.c_uint64), ("max_host_absorb_log2", C.c_int),
                 ("small_max_bits", C.c_int)]
+
+
+class tn_server_opts(C.Structure):
+    _fields_ = [("n_slots", C.c_int), ("hbm_budget_bytes", C.c_int64)]
+
+
+class tn_request(C.Structure):
+    _fields_ = [("circuit", C.c_int), ("kind", C.c_int), ("bitstrings", C.c_void_p), ("n", C.c_int64),
+                ("out", C.c_void_p), ("dtype", C.c_int), ("target_fidelity", C.c_double), ("seed", C.c_uint64),
+                ("method", C.c_int), ("param", C.c_int64)]
+
+
+class tn_request_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("latency_us", C.c_double), ("queue_us", C.c_double)]
+
+
+class tn_server_stats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("in_flight", C.c_int64), ("queued", C.c_int64),
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("mean_us", C.c_double),
+                ("heads_cached", C.c_int64), ("head_bytes", C.c_int64), ("evictions", C.c_int64),
+                ("wall_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class tn_plan_stats(C.Structure):
@@ -96,6 +122,16 @@ def _load():
     lib.tn_amplitudes.argtypes = [vp, vp, i64, vp, C.c_int, vp]
     lib.tn_sample.argtypes = [vp, i64, C.c_double, C.c_uint64, vp, vp]
     lib.tn_head_norm.argtypes = [vp, C.POINTER(C.c_double), vp, vp]
+    lib.tn_contract_slices_graph.argtypes = [vp, tn_range, vp, vp]
+    lib.tn_contract_batch.argtypes = [C.POINTER(vp), C.POINTER(tn_range), C.POINTER(vp), C.c_int, vp]
+    lib.tn_server_create.argtypes = [C.POINTER(tn_server_opts), C.POINTER(vp)]
+    lib.tn_server_add_circuit.argtypes = [vp, vp, tn_range, C.POINTER(C.c_int)]
+    lib.tn_server_submit.argtypes = [vp, C.POINTER(tn_request), C.POINTER(C.c_uint64)]
+    lib.tn_server_wait.argtypes = [vp, C.c_uint64, C.POINTER(tn_request_result)]
+    lib.tn_server_get_stats.argtypes = [vp, C.POINTER(tn_server_stats)]
+    lib.tn_server_free.argtypes = [vp]
+    lib.tn_server_free.restype = None
+    lib.tn_sample_ex.argtypes = [vp, i64, C.c_double, C.c_uint64, C.c_int, i64, vp, vp]
     lib.tn_profile_slices.argtypes = [vp, tn_range, vp, vp, C.POINTER(C.c_double), i64]
     lib.tn_plan_step_info.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.tn_head_norm_noalloc.argtypes = [vp, i64, C.c_int, vp, vp]
@@ -103,7 +139,9 @@ def _load():
     lib.tn_version.restype = C.c_char_p
     for name in ("tn_plan", "tn_plan_get_stats", "tn_plan_order", "tn_head_create", "tn_head_fidelity",
                  "tn_head_set_fidelity", "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm",
-                 "tn_profile_slices", "tn_plan_step_info", "tn_head_reset", "tn_head_norm_noalloc"):
+                 "tn_profile_slices", "tn_plan_step_info", "tn_head_reset", "tn_head_norm_noalloc", "tn_sample_ex",
+                 "tn_contract_slices_graph", "tn_contract_batch", "tn_server_create", "tn_server_add_circuit",
+                 "tn_server_submit", "tn_server_wait", "tn_server_get_stats"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -113,8 +151,10 @@ lib = _lib
 
 EXPORTED = ["tn_plan", "tn_plan_free", "tn_plan_get_stats", "tn_plan_order", "tn_plan_describe",
             "tn_head_create", "tn_head_free", "tn_head_data", "tn_head_reset", "tn_head_fidelity", "tn_head_set_fidelity",
-            "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm", "tn_profile_slices",
-            "tn_plan_step_info", "tn_head_norm_noalloc", "tn_last_error", "tn_version"]
+            "tn_contract_slices", "tn_contract_slices_graph", "tn_contract_batch", "tn_amplitudes", "tn_sample", "tn_sample_ex", "tn_head_norm", "tn_profile_slices",
+            "tn_plan_step_info", "tn_head_norm_noalloc", "tn_server_create", "tn_server_add_circuit",
+            "tn_server_submit", "tn_server_wait", "tn_server_get_stats", "tn_server_free", "tn_last_error",
+            "tn_version"]
 
 
 def _check(rc):
@@ -261,6 +301,20 @@ def tn_contract_slices(plan: Plan, begin: int, end: int, head: Head, stream=None
     _check(_lib.tn_contract_slices(plan.handle, tn_range(int(begin), int(end)), head.handle, _stream(stream)))
 
 
+def tn_contract_slices_graph(plan: Plan, begin: int, end: int, head: Head, stream=None):
+    _check(_lib.tn_contract_slices_graph(plan.handle, tn_range(int(begin), int(end)), head.handle,
+                                         _stream(stream)))
+
+
+def tn_contract_batch(plans, ranges, heads, stream=None):
+    """plans, heads: lists of Plan / Head; ranges: list of (begin, end)."""
+    n = len(plans)
+    P = (C.c_void_p * max(1, n))(*[p.handle for p in plans])
+    R = (tn_range * max(1, n))(*[tn_range(int(b), int(e)) for (b, e) in ranges])
+    Hh = (C.c_void_p * max(1, n))(*[h.handle for h in heads])
+    _check(_lib.tn_contract_batch(P, R, Hh, n, _stream(stream)))
+
+
 def tn_amplitudes(head: Head, bitstrings, out=None, dtype=TN_C128, stream=None):
     """bitstrings: numpy uint64 (host) or torch uint64/int64 tensor (device).
     Returns `out` (allocated as numpy complex128/complex64 when None)."""
@@ -277,6 +331,15 @@ def tn_sample(head: Head, n: int, target_fidelity=0.0, seed=0, out=None, stream=
     if out is None:
         out = np.zeros(int(n), dtype=np.uint64)
     _check(_lib.tn_sample(head.handle, int(n), float(target_fidelity), int(seed), _ptr(out), _stream(stream)))
+    return out
+
+
+def tn_sample_ex(head: Head, n: int, target_fidelity=0.0, seed=0, method=TN_SAMPLE_EXACT, param=0, out=None,
+                 stream=None):
+    if out is None:
+        out = np.zeros(int(n), dtype=np.uint64)
+    _check(_lib.tn_sample_ex(head.handle, int(n), float(target_fidelity), int(seed), int(method), int(param),
+                             _ptr(out), _stream(stream)))
     return out
 
 
@@ -311,6 +374,73 @@ def tn_head_norm_noalloc(head_buffer, n_groups: int, n_open: int, norm_out, stre
     double `norm_out`, with no device allocation (asynchronous on `stream`)."""
     _check(_lib.tn_head_norm_noalloc(_ptr(head_buffer), int(n_groups), int(n_open), _ptr(norm_out),
                                      _stream(stream)))
+
+
+class Server:
+    """Owns a tn_server_t; keeps registered plans and in-flight buffers alive."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.plans = []
+        self.inflight = {}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tn_server_free(self.handle)
+            self.handle = None
+
+
+def tn_server_create(n_slots=0, hbm_budget_bytes=0) -> Server:
+    h = C.c_void_p()
+    _check(_lib.tn_server_create(C.byref(tn_server_opts(int(n_slots), int(hbm_budget_bytes))), C.byref(h)))
+    return Server(h)
+
+
+def tn_server_add_circuit(server: Server, plan: Plan, begin: int, end: int) -> int:
+    cid = C.c_int()
+    _check(_lib.tn_server_add_circuit(server.handle, plan.handle, tn_range(int(begin), int(end)), C.byref(cid)))
+    server.plans.append(plan)
+    return cid.value
+
+
+def tn_server_submit(server: Server, circuit: int, kind: int, n: int, bitstrings=None, out=None, dtype=TN_C128,
+                     target_fidelity=0.0, seed=0, method=TN_SAMPLE_EXACT, param=0) -> int:
+    """Queue a request; returns its ticket.  `out` (allocated when None) and the
+    bitstrings are kept alive until tn_server_wait."""
+    if kind == TN_REQ_AMPLITUDES:
+        bitstrings = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint64))
+        n = bitstrings.size
+        if out is None:
+            out = np.zeros(n, dtype=np.complex128 if dtype == TN_C128 else np.complex64)
+    elif out is None:
+        out = np.zeros(int(n), dtype=np.uint64)
+    req = tn_request(int(circuit), int(kind), bitstrings.ctypes.data if bitstrings is not None else None, int(n),
+                     out.ctypes.data, int(dtype), float(target_fidelity), int(seed), int(method), int(param))
+    t = C.c_uint64()
+    _check(_lib.tn_server_submit(server.handle, C.byref(req), C.byref(t)))
+    server.inflight[t.value] = (bitstrings, out)
+    return t.value
+
+
+def tn_server_wait(server: Server, ticket: int):
+    """Blocks for the request; returns (out, latency_us)."""
+    res = tn_request_result()
+    rc = _lib.tn_server_wait(server.handle, int(ticket), C.byref(res))
+    bufs = server.inflight.pop(int(ticket), (None, None))
+    _check(rc)
+    return bufs[1], res.latency_us
+
+
+def tn_server_get_stats(server: Server) -> dict:
+    st = tn_server_stats()
+    _check(_lib.tn_server_get_stats(server.handle, C.byref(st)))
+    return st.as_dict()
+
+
+def tn_server_free(server: Server):
+    if server.handle:
+        _lib.tn_server_free(server.handle)
+        server.handle = None
 
 
 def tn_last_error() -> str:

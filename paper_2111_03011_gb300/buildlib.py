@@ -20,7 +20,7 @@ LIBPATH = os.path.join(LIBDIR, "libtn_gb300.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["capi.cu", "kernels.cu", "gemm_tc.cu", "noalloc.cu"]
+CU_SOURCES = ["capi.cu", "kernels.cu", "gemm_tc.cu", "noalloc.cu", "server.cu"]
 CPP_SOURCES = ["planner.cpp"]
 
 

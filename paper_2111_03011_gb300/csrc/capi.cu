@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "handles.h"
 #include "kernels.h"
 #include "planner.h"
 #include "tn_gb300.h"
@@ -39,37 +40,6 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
-struct tn_plan {
-  tn::Plan P;
-  bool on_device = false;
-  int device = -1;
-  float2* d_leaves = nullptr;
-  uint32_t* d_meta = nullptr;
-  char* d_arena = nullptr;
-  uint64_t* d_keys = nullptr;      // sorted masked tails
-  uint32_t* d_key_groups = nullptr;
-  uint64_t* d_tails = nullptr;     // tails in group order
-  int* d_open = nullptr;
-  unsigned int* d_status = nullptr;
-  int64_t n_keys = 0;
-};
-
-struct tn_head {
-  tn_plan_t* plan = nullptr;
-  double2* H = nullptr;
-  bool owns = false;
-  std::map<int64_t, int64_t> done;   // begin -> end of accumulated slice ranges
-  int64_t slices_done = 0;
-  bool f_override = false;
-  double f_value = 0.0;
-  // scratch
-  double* d_Z = nullptr;
-  double* d_N = nullptr;
-  unsigned long long* d_status = nullptr;
-  void* d_stage = nullptr;
-  size_t stage_bytes = 0;
-};
-
 static const char* kVersion = "tn_gb300 0.1 (sm_103a)";
 
 namespace tn {
@@ -94,6 +64,8 @@ static void plan_release(tn_plan_t* p) {
     cudaFree(p->d_tails);
     cudaFree(p->d_open);
     cudaFree(p->d_status);
+    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (cur >= 0) cudaSetDevice(cur);
   }
   delete p;
@@ -104,6 +76,7 @@ extern "C" void tn_plan_free(tn_plan_t* plan) { plan_release(plan); }
 static int plan_upload(tn_plan_t* p) {
   tn::Plan& P = p->P;
   CUDA_TRY(cudaGetDevice(&p->device));
+  CUDA_TRY(tn::prepare_gemm_tc());
   std::vector<float2> leaves(P.leaf_arena.size());
   for (size_t i = 0; i < leaves.size(); ++i)
     leaves[i] = make_float2((float)P.leaf_arena[i].real(), (float)P.leaf_arena[i].imag());
@@ -273,6 +246,7 @@ extern "C" int tn_head_create(tn_plan_t* plan, void* dev_c128, tn_head_t** out) 
     h->owns = true;
   }
   cudaError_t e1 = cudaMemset(h->H, 0, (size_t)elems * sizeof(double2));
+  if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(0);   // zeroed before any stream, blocking or not, uses it
   cudaError_t e2 = cudaMalloc(&h->d_Z, (size_t)std::max<int64_t>(L, 1) * sizeof(double));
   cudaError_t e3 = cudaMalloc(&h->d_N, sizeof(double));
   cudaError_t e4 = cudaMalloc(&h->d_status, sizeof(unsigned long long));
@@ -311,7 +285,8 @@ extern "C" int tn_head_fidelity(const tn_head_t* h, double* f_est, int64_t* slic
   if (!h) return fail(TN_ERR_INVALID, "NULL head");
   const tn::Plan& P = h->plan->P;
   double f = h->f_override ? h->f_value
-                           : std::ldexp((double)h->slices_done, -P.n_sliced) * std::ldexp(1.0, -P.n_pinned);
+                           : std::ldexp((double)h->slices_done, -P.n_sliced) * std::ldexp(1.0, -P.n_pinned) *
+                                 P.companion_factor;
   if (f_est) *f_est = f;
   if (slices_done) *slices_done = h->slices_done;
   return TN_OK;
@@ -524,6 +499,112 @@ extern "C" int tn_contract_slices(tn_plan_t* plan, tn_range r, tn_head_t* head, 
   return TN_OK;
 }
 
+// ---------------------------------------------------------- CUDA graphs
+
+// Capture the launches of `slices` of every (plan, head) item, item i on branch
+// stream branch_of[i], into one graph (fork/join through events).
+static int capture_items(const std::vector<tn_plan_t*>& plans, const std::vector<tn_range>& ranges,
+                         const std::vector<tn_head_t*>& heads, const std::vector<int>& branch_of, int n_branches,
+                         cudaGraphExec_t* exec_out) {
+  static thread_local std::vector<cudaStream_t> streams;
+  while ((int)streams.size() < n_branches + 1) {
+    cudaStream_t st;
+    CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    streams.push_back(st);
+  }
+  cudaStream_t main = streams[0];
+  std::vector<cudaEvent_t> ev(n_branches + 1);
+  for (auto& e : ev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  CUDA_TRY(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
+  int rc = TN_OK;
+  cudaError_t ce = cudaEventRecord(ev[0], main);
+  for (int b = 0; b < n_branches && ce == cudaSuccess; ++b) ce = cudaStreamWaitEvent(streams[1 + b], ev[0], 0);
+  if (ce != cudaSuccess) rc = fail(TN_ERR_CUDA, std::string("graph fork: ") + cudaGetErrorString(ce));
+  for (size_t i = 0; i < plans.size() && rc == TN_OK; ++i)
+    for (int64_t s = ranges[i].begin; s < ranges[i].end && rc == TN_OK; ++s)
+      rc = run_slice(plans[i], s, heads[i]->H, streams[1 + branch_of[i]]);
+  for (int b = 0; b < n_branches && rc == TN_OK; ++b) {
+    ce = cudaEventRecord(ev[1 + b], streams[1 + b]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(main, ev[1 + b], 0);
+    if (ce != cudaSuccess) rc = fail(TN_ERR_CUDA, std::string("graph join: ") + cudaGetErrorString(ce));
+  }
+  cudaGraph_t graph = nullptr;
+  ce = cudaStreamEndCapture(main, &graph);
+  if (rc == TN_OK && ce != cudaSuccess) rc = fail(TN_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(ce));
+  if (rc == TN_OK) {
+    ce = cudaGraphInstantiate(exec_out, graph, 0);
+    if (ce != cudaSuccess) rc = fail(TN_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+  }
+  if (graph) cudaGraphDestroy(graph);
+  for (auto& e : ev) cudaEventDestroy(e);
+  cudaGetLastError();
+  return rc;
+}
+
+extern "C" int tn_contract_slices_graph(tn_plan_t* plan, tn_range r, tn_head_t* head, void* stream) {
+  int rc = check_range(plan, r, head);
+  if (rc) return rc;
+  if (r.begin == r.end) return TN_OK;
+  GraphEntry* hit = nullptr;
+  for (auto& g : plan->graphs)
+    if (g.begin == r.begin && g.end == r.end && g.H == (void*)head->H) hit = &g;
+  if (!hit) {
+    GraphEntry g;
+    g.begin = r.begin;
+    g.end = r.end;
+    g.H = head->H;
+    rc = capture_items({plan}, {r}, {head}, {0}, 1, &g.exec);
+    if (rc) return rc;
+    plan->graphs.push_back(g);
+    hit = &plan->graphs.back();
+  }
+  CUDA_TRY(cudaGraphLaunch(hit->exec, (cudaStream_t)stream));
+  mark_done(head, r);
+  return TN_OK;
+}
+
+extern "C" int tn_contract_batch(tn_plan_t* const* plans, const tn_range* ranges, tn_head_t* const* heads, int n,
+                                 void* stream) {
+  if (n < 0 || (n > 0 && (!plans || !ranges || !heads))) return fail(TN_ERR_INVALID, "bad batch arrays");
+  if (n == 0) return TN_OK;
+  std::vector<tn_plan_t*> P(plans, plans + n);
+  std::vector<tn_range> R(ranges, ranges + n);
+  std::vector<tn_head_t*> Hs(heads, heads + n);
+  std::vector<int> branch(n);
+  std::map<tn_plan_t*, int> branch_of_plan;   // items of one plan share its arena: same branch
+  std::map<tn_head_t*, int> head_seen;
+  for (int i = 0; i < n; ++i) {
+    int rc = check_range(P[i], R[i], Hs[i]);
+    if (rc) return rc;
+    if (head_seen.count(Hs[i])) return fail(TN_ERR_INVALID, "a head appears twice in one batch");
+    head_seen[Hs[i]] = i;
+    auto it = branch_of_plan.find(P[i]);
+    if (it == branch_of_plan.end()) it = branch_of_plan.emplace(P[i], (int)branch_of_plan.size()).first;
+    branch[i] = it->second;
+  }
+  const int n_branches = std::min<int>((int)branch_of_plan.size(), 32);
+  for (int i = 0; i < n; ++i) branch[i] %= n_branches;
+  // single-entry cache: the same batch again replays the same graph
+  static thread_local std::vector<tn_plan_t*> last_p;
+  static thread_local std::vector<int64_t> last_r;
+  static thread_local std::vector<tn_head_t*> last_h;
+  static thread_local cudaGraphExec_t last_exec = nullptr;
+  std::vector<int64_t> rr;
+  for (auto& x : R) { rr.push_back(x.begin); rr.push_back(x.end); }
+  if (!(last_exec && last_p == P && last_r == rr && last_h == Hs)) {
+    if (last_exec) cudaGraphExecDestroy(last_exec);
+    last_exec = nullptr;
+    int rc = capture_items(P, R, Hs, branch, n_branches, &last_exec);
+    if (rc) { last_exec = nullptr; return rc; }
+    last_p = P;
+    last_r = rr;
+    last_h = Hs;
+  }
+  CUDA_TRY(cudaGraphLaunch(last_exec, (cudaStream_t)stream));
+  for (int i = 0; i < n; ++i) mark_done(Hs[i], R[i]);
+  return TN_OK;
+}
+
 // ------------------------------------------------------ amplitudes, sampling
 
 static int ensure_stage(tn_head* h, size_t bytes) {
@@ -589,8 +670,28 @@ extern "C" int tn_head_norm(tn_head_t* h, double* norm, double* group_norms, voi
   return TN_OK;
 }
 
+static int sample_impl(tn_head_t* h, int64_t n, double target_fidelity, uint64_t seed, int method, int64_t param,
+                       uint64_t* out, void* stream);
+
 extern "C" int tn_sample(tn_head_t* h, int64_t n, double target_fidelity, uint64_t seed, uint64_t* out, void* stream) {
+  return sample_impl(h, n, target_fidelity, seed, TN_SAMPLE_EXACT, 0, out, stream);
+}
+
+extern "C" int tn_sample_ex(tn_head_t* h, int64_t n, double target_fidelity, uint64_t seed, int method,
+                            int64_t param, uint64_t* out, void* stream) {
+  return sample_impl(h, n, target_fidelity, seed, method, param, out, stream);
+}
+
+static int sample_impl(tn_head_t* h, int64_t n, double target_fidelity, uint64_t seed, int method, int64_t param,
+                       uint64_t* out, void* stream) {
   if (!h || (n > 0 && !out)) return fail(TN_ERR_INVALID, "NULL argument");
+  if (method < TN_SAMPLE_EXACT || method > TN_SAMPLE_FRUGAL) return fail(TN_ERR_INVALID, "unknown sampling method");
+  const int64_t l = 1LL << h->plan->P.open_qubits.size();
+  if (method == TN_SAMPLE_METROPOLIS && param == 0) param = l;
+  if (method == TN_SAMPLE_FRUGAL && param == 0) param = 10;
+  if (param < 0 || (method == TN_SAMPLE_METROPOLIS && param > (1LL << 32)) ||
+      (method == TN_SAMPLE_FRUGAL && param > (1LL << 20)))
+    return fail(TN_ERR_INVALID, "sampling parameter out of range");
   if (n < 0) return fail(TN_ERR_INVALID, "n < 0");
   if (n == 0) return TN_OK;
   tn_plan_t* p = h->plan;
@@ -620,8 +721,22 @@ extern "C" int tn_sample(tn_head_t* h, int64_t n, double target_fidelity, uint64
   sp.mix = mix;
   sp.seed = seed;
   sp.out = d_out;
+  sp.method = method;
+  sp.param = param;
   CUDA_TRY(tn::launch_sample(sp, st));
   if (!dev_out) CUDA_TRY(cudaMemcpyAsync(out, d_out, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   return TN_OK;
 }
+
+namespace tn {
+int enqueue_slices(tn_plan_t* plan, tn_range r, double2* H, cudaStream_t stream) {
+  for (int64_t s = r.begin; s < r.end; ++s) {
+    int rc = run_slice(plan, s, H, stream);
+    if (rc) return rc;
+  }
+  return TN_OK;
+}
+int check_slice_range(tn_plan_t* plan, tn_range r, tn_head_t* head) { return check_range(plan, r, head); }
+void mark_slices_done(tn_head_t* head, tn_range r) { mark_done(head, r); }
+}  // namespace tn

@@ -380,15 +380,14 @@ static bool encode3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1,
 }
 
 template <int BN, int STAGES, bool BF16>
+static cudaError_t set_attr() {
+  using Lay = Layout<BN, STAGES>;
+  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL);
+}
+
+template <int BN, int STAGES, bool BF16>
 static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   using Lay = Layout<BN, STAGES>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   const int64_t K2 = 2 * p.K, N2 = 2 * p.N;
   const uint32_t BKE = BF16 ? 64 : 32;
   const int64_t es = BF16 ? 2 : 4;
@@ -421,6 +420,18 @@ static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStrea
 }
 
 }  // namespace tc
+
+cudaError_t prepare_gemm_tc() {
+  // the opt-in shared-memory size, set once per device before any launch (and
+  // so before any stream capture)
+  cudaError_t e = cudaSuccess;
+  const cudaError_t r[8] = {tc::set_attr<16, 6, false>(), tc::set_attr<32, 5, false>(), tc::set_attr<64, 4, false>(),
+                            tc::set_attr<128, 3, false>(), tc::set_attr<16, 6, true>(), tc::set_attr<32, 5, true>(),
+                            tc::set_attr<64, 4, true>(), tc::set_attr<128, 3, true>()};
+  for (cudaError_t x : r)
+    if (x != cudaSuccess) e = x;
+  return e;
+}
 
 cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   // row pitch of A (2K elements) must be a multiple of 16 bytes

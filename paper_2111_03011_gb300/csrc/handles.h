@@ -1,0 +1,62 @@
+// Internal handle layouts shared by the C ABI (capi.cu) and the request
+// server (server.cu).  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "planner.h"
+#include "tn_gb300.h"
+
+struct GraphEntry {
+  int64_t begin = 0, end = 0;
+  void* H = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct tn_plan {
+  tn::Plan P;
+  std::vector<GraphEntry> graphs;     // captured slice ranges (tn_contract_slices_graph)
+  cudaStream_t cap_stream = nullptr;
+  bool on_device = false;
+  int device = -1;
+  float2* d_leaves = nullptr;
+  uint32_t* d_meta = nullptr;
+  char* d_arena = nullptr;
+  uint64_t* d_keys = nullptr;      // sorted masked tails
+  uint32_t* d_key_groups = nullptr;
+  uint64_t* d_tails = nullptr;     // tails in group order
+  int* d_open = nullptr;
+  unsigned int* d_status = nullptr;
+  int64_t n_keys = 0;
+};
+
+struct tn_head {
+  tn_plan_t* plan = nullptr;
+  double2* H = nullptr;
+  bool owns = false;
+  std::map<int64_t, int64_t> done;   // begin -> end of accumulated slice ranges
+  int64_t slices_done = 0;
+  bool f_override = false;
+  double f_value = 0.0;
+  // scratch
+  double* d_Z = nullptr;
+  double* d_N = nullptr;
+  unsigned long long* d_status = nullptr;
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+
+namespace tn {
+void set_last_error(const std::string& msg);
+// Enqueue the slices of `r` of `plan` into H on `stream` (no range checks).
+int enqueue_slices(tn_plan_t* plan, tn_range r, double2* H, cudaStream_t stream);
+// Range checks and bookkeeping of tn_contract_slices.
+int check_slice_range(tn_plan_t* plan, tn_range r, tn_head_t* head);
+void mark_slices_done(tn_head_t* head, tn_range r);
+}  // namespace tn

@@ -478,8 +478,20 @@ __device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
   return (double)(x >> 11) * 0x1.0p-53;
 }
 
-// One warp per sample: group i mod L, draw by inverse CDF over the chunked
-// warp-scan prefix sums of |H[g][mu]|^2 (same order as k_group_norms).
+// |h|^2 with each operation rounded to nearest (no fused multiply-add), so
+// that weights and the comparisons built on them are reproducible bit by bit.
+__device__ __forceinline__ double weight_rn(double2 v) { return __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)); }
+
+// One warp per sample, group i mod L.
+//   method 0: exact draw by inverse CDF over the chunked warp-scan prefix sums
+//             of |H[g][mu]|^2 (same order as k_group_norms);
+//   method 1: Metropolis chain with uniform proposals (the paper's in-group
+//             MCMC, Method and Supplement): start at member 0; for t < T,
+//             propose mu' = bits of Philox(i, 2, t), accept when
+//             u * w(mu) < w(mu');
+//   method 2: frugal rejection sampling (Supplement, bitstring choice): for
+//             t < 64 M rounds, draw mu = bits of Philox(i, 3, t) and accept
+//             when (u * M) * Z < w(mu) * l; after the last round keep mu.
 __global__ void k_sample(SampleParams p) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -488,38 +500,66 @@ __global__ void k_sample(SampleParams p) {
   const uint64_t full = p.n_qubits >= 64 ? ~0ULL : ((1ULL << p.n_qubits) - 1);
   for (int64_t i = warp; i < p.n; i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t g = i % p.L;
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, 0u), key);
+    const uint32_t ilo = (uint32_t)i, ihi = (uint32_t)((uint64_t)i >> 32);
+    const uint4 r = philox4x32_10(make_uint4(ilo, ihi, 0u, 0u), key);
     const double u_mix = u53(r.x, r.y), u_pick = u53(r.z, r.w);
     if (p.mix > 0.0 && u_mix < p.mix) {
-      const uint4 q = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 1u, 0u), key);
+      const uint4 q = philox4x32_10(make_uint4(ilo, ihi, 1u, 0u), key);
       if (lane == 0) p.out[i] = ((((uint64_t)q.y) << 32) | q.x) & full;
       continue;
     }
     const double2* __restrict__ Hg = p.H + (g << p.h);
-    // pass 1: total in chunk order
-    double Z = 0.0;
-    for (int64_t c = 0; c < l; c += 32) {
-      double w = 0.0;
-      if (c + lane < l) { const double2 v = Hg[c + lane]; w = v.x * v.x + v.y * v.y; }
-      const double s = warp_inclusive_scan(w);
-      Z += __shfl_sync(0xffffffffu, s, 31);
-    }
     int64_t mu = l - 1;
-    if (Z > 0.0) {
-      const double t = u_pick * Z;
-      double carry = 0.0;
-      for (int64_t c = 0; c < l; c += 32) {
-        double w = 0.0;
-        if (c + lane < l) { const double2 v = Hg[c + lane]; w = v.x * v.x + v.y * v.y; }
-        const double s = warp_inclusive_scan(w);
-        const bool hit = (c + lane < l) && (carry + s > t);
-        const unsigned ball = __ballot_sync(0xffffffffu, hit);
-        if (ball) { mu = c + __ffs(ball) - 1; break; }
-        carry += __shfl_sync(0xffffffffu, s, 31);
+    if (p.method == 1) {
+      // lane 0 runs the chain (it is sequential); the other lanes idle
+      if (lane == 0) {
+        int64_t cur = 0;
+        double wc = weight_rn(Hg[0]);
+        for (int64_t t = 0; t < p.param; ++t) {
+          const uint4 q = philox4x32_10(make_uint4(ilo, ihi, 2u, (uint32_t)t), key);
+          const int64_t prop = (int64_t)(q.x & (uint32_t)(l - 1));
+          const double wp = weight_rn(Hg[prop]);
+          const double u = u53(q.z, q.w);
+          if (__dmul_rn(u, wc) < wp) { cur = prop; wc = wp; }
+        }
+        mu = cur;
       }
     } else {
-      mu = (int64_t)(u_pick * (double)l);
-      if (mu >= l) mu = l - 1;
+      // chunked warp-scan total (exact draw and frugal bound)
+      double Z = 0.0;
+      for (int64_t c = 0; c < l; c += 32) {
+        const double w = (c + lane < l) ? weight_rn(Hg[c + lane]) : 0.0;
+        const double s = warp_inclusive_scan(w);
+        Z += __shfl_sync(0xffffffffu, s, 31);
+      }
+      if (p.method == 2) {
+        if (lane == 0) {
+          const double M = (double)p.param;
+          const double bound = __dmul_rn(M, Z);
+          int64_t cand = 0;
+          for (int64_t t = 0; t < 64 * p.param; ++t) {
+            const uint4 q = philox4x32_10(make_uint4(ilo, ihi, 3u, (uint32_t)t), key);
+            cand = (int64_t)(q.x & (uint32_t)(l - 1));
+            const double u = u53(q.z, q.w);
+            if (__dmul_rn(u, bound) < __dmul_rn(weight_rn(Hg[cand]), (double)l)) break;
+          }
+          mu = cand;
+        }
+      } else if (Z > 0.0) {
+        const double t = u_pick * Z;
+        double carry = 0.0;
+        for (int64_t c = 0; c < l; c += 32) {
+          const double w = (c + lane < l) ? weight_rn(Hg[c + lane]) : 0.0;
+          const double s = warp_inclusive_scan(w);
+          const bool hit = (c + lane < l) && (carry + s > t);
+          const unsigned ball = __ballot_sync(0xffffffffu, hit);
+          if (ball) { mu = c + __ffs(ball) - 1; break; }
+          carry += __shfl_sync(0xffffffffu, s, 31);
+        }
+      } else {
+        mu = (int64_t)(u_pick * (double)l);
+        if (mu >= l) mu = l - 1;
+      }
     }
     if (lane == 0) {
       uint64_t s = p.tails[g] & ~p.open_mask;

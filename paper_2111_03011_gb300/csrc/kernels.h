@@ -67,6 +67,7 @@ cudaError_t launch_accum(const AccumParams& p, cudaStream_t s);
 // B = real-embedded hi then lo planes [PB][2N][2K].
 // `status` receives a nonzero code if a bounded wait gave up.
 cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s);
+cudaError_t prepare_gemm_tc();   // kernel attributes; call before launching or capturing
 
 // amplitude lookup: out[i] = H[g][mu] (c128 or c64); status <- min missing index
 cudaError_t launch_amplitudes(const double2* H, int h, const uint64_t* keys, const uint32_t* groups, int64_t n_keys,
@@ -84,6 +85,8 @@ struct SampleParams {
   double mix;                 // probability of a uniform draw
   uint64_t seed;
   uint64_t* out;
+  int method;                 // 0 exact inverse CDF, 1 Metropolis chain, 2 frugal rejection
+  int64_t param;              // chain length (1) or the bound M (2)
 };
 cudaError_t launch_sample(const SampleParams& p, cudaStream_t s);
 

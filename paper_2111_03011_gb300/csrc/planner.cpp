@@ -135,7 +135,12 @@ static int build_network(const PlanInput& in, Plan& plan, Builder& b, std::strin
   int slice_bit = 0;
   std::vector<int> edge_slice_bit(in.edges.size(), -1);
   for (size_t e = 0; e < in.edges.size(); ++e)
-    if (in.edges[e].kind == TN_EDGE_SLICE) edge_slice_bit[e] = slice_bit++;
+    if (in.edges[e].kind == TN_EDGE_SLICE || in.edges[e].kind == TN_EDGE_COMPANION) edge_slice_bit[e] = slice_bit++;
+  // companion cuts: gate -> (partner output leg position 0/1 of the outputs, slice bit)
+  std::map<int, std::vector<std::pair<int, int>>> companions;
+  for (size_t e = 0; e < in.edges.size(); ++e)
+    if (in.edges[e].kind == TN_EDGE_COMPANION)
+      companions[in.edges[e].gate].push_back({1 - in.edges[e].leg, edge_slice_bit[e]});
 
   for (int gi = 0; gi < in.n_gates; ++gi) {
     const int ar = in.arity[gi];
@@ -148,7 +153,7 @@ static int build_network(const PlanInput& in, Plan& plan, Builder& b, std::strin
         int old = wire[q];
         int nw = b.new_leg(LEG_HALF);
         plan.legs[old].kind = LEG_HALF;
-        if (E.kind == TN_EDGE_SLICE) {
+        if (E.kind == TN_EDGE_SLICE || E.kind == TN_EDGE_COMPANION) {
           plan.legs[old].slice_bit = edge_slice_bit[c.second];
           plan.legs[nw].slice_bit = edge_slice_bit[c.second];
         } else {
@@ -178,6 +183,20 @@ static int build_network(const PlanInput& in, Plan& plan, Builder& b, std::strin
               t.data[i0 + 2 * i1 + 4 * a0 + 8 * a1] = U[(2 * a0 + a1) * 4 + (2 * i0 + i1)];
       wire[q0] = o0;
       wire[q1] = o1;
+      // rank-one companion cut (Method case (ii)): with input leg a fixed to v
+      // by the slice, the partner output is fixed to the same v, so that wire
+      // becomes a pair of half legs carrying the same slice bit
+      auto ic = companions.find(gi);
+      if (ic != companions.end())
+        for (auto& pc : ic->second) {
+          const int q = pc.first == 0 ? q0 : q1;
+          int old = wire[q];
+          int nw = b.new_leg(LEG_HALF);
+          plan.legs[old].kind = LEG_HALF;
+          plan.legs[old].slice_bit = pc.second;
+          plan.legs[nw].slice_bit = pc.second;
+          wire[q] = nw;
+        }
     }
     b.T.push_back(t);
   }
@@ -743,7 +762,8 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
 
   // edges
   std::set<std::pair<int, int>> seen;
-  int k = 0, pins = 0;
+  int k = 0, pins = 0, companions = 0;
+  double comp_factor = 1.0;
   for (auto& e : in.edges) {
     if (e.gate < 0 || e.gate >= in.n_gates) { err = "edge: gate out of range"; return TN_ERR_INVALID; }
     if (e.leg < 0 || e.leg >= in.arity[e.gate]) { err = "edge: leg out of range"; return TN_ERR_INVALID; }
@@ -753,13 +773,34 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
       if (e.value != 0 && e.value != 1) { err = "pin value must be 0 or 1"; return TN_ERR_INVALID; }
       ++pins;
     } else if (e.kind == TN_EDGE_COMPANION) {
-      err = "companion edges are not implemented";
-      return TN_ERR_UNSUPPORTED;
+      if (in.arity[e.gate] != 2) { err = "companion edge on a single-qubit gate"; return TN_ERR_INVALID; }
+      ++k;
+      ++companions;
+      // kept norm fraction of the rank-one cut, averaged over the two values of
+      // the pinned input: |F[partner out = v]|^2 / |F|^2 with F = gate[:, in_a = v]
+      const cd* U = in.mats + (size_t)e.gate * 16;
+      double frac = 0.0;
+      for (int v = 0; v < 2; ++v) {
+        double kept = 0.0, tot = 0.0;
+        for (int o0 = 0; o0 < 2; ++o0)
+          for (int o1 = 0; o1 < 2; ++o1)
+            for (int other = 0; other < 2; ++other) {
+              const int i0 = e.leg == 0 ? v : other, i1 = e.leg == 0 ? other : v;
+              const double w = std::norm(U[(2 * o0 + o1) * 4 + (2 * i0 + i1)]);
+              tot += w;
+              const int partner_out = e.leg == 0 ? o1 : o0;
+              if (partner_out == v) kept += w;
+            }
+        frac += 0.5 * (tot > 0 ? kept / tot : 1.0);
+      }
+      comp_factor *= frac;
     } else { err = "edge: unknown kind"; return TN_ERR_INVALID; }
   }
   if (k > 40) { err = "at most 40 sliced edges"; return TN_ERR_INVALID; }
   plan.n_sliced = k;
   plan.n_pinned = pins;
+  plan.n_companion = companions;
+  plan.companion_factor = comp_factor;
 
   Builder b(plan);
   int rc = build_network(in, plan, b, err);

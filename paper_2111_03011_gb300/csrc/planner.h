@@ -122,7 +122,8 @@ struct Plan {
   std::vector<int> open_qubits;
   std::vector<uint64_t> tails_raw;
   uint64_t open_mask = 0, tail_mask = 0;
-  int n_sliced = 0, n_pinned = 0;
+  int n_sliced = 0, n_pinned = 0, n_companion = 0;
+  double companion_factor = 1.0;   // product of the companion cuts' kept norm fractions
   double cap_log2 = 28;
   int gemm_engine = 0;
   int small_max_bits = 4;

@@ -1,0 +1,469 @@
+// Request server: continuous admission of amplitude and sampling requests on
+// several circuits, with head tensors cached in HBM.
+//
+// A dispatcher thread owns `n_slots` slots, each a CUDA stream with pinned and
+// device staging buffers.  Queued requests are admitted into free slots as
+// soon as a slot and the HBM budget allow; admitted requests run concurrently
+// on their slots' streams, so work that arrives while other requests are on
+// the GPU overlaps with it.  The first request on a circuit contracts its kept
+// slices into a new head (the circuit is BUILDING); later requests on that
+// circuit wait on the head's ready event on the device, not on the host.
+// Heads are freed least-recently-used first when a new head does not fit the
+// budget.  Completion is detected by polling per-slot events; latency is
+// measured from submit to the moment the result is in the caller's buffer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "handles.h"
+#include "kernels.h"
+#include "tn_gb300.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+int fail(int code, const std::string& msg) {
+  tn::set_last_error(msg);
+  return code;
+}
+
+struct Request {
+  uint64_t ticket = 0;
+  tn_request r{};
+  Clock::time_point t_submit, t_start, t_done;
+  int status = TN_OK;
+  std::string err;
+  bool done = false;
+};
+
+enum { C_EMPTY = 0, C_BUILDING = 1, C_READY = 2 };
+
+struct Circuit {
+  tn_plan_t* plan = nullptr;
+  tn_range kept{0, 0};
+  tn_head_t* head = nullptr;
+  int state = C_EMPTY;
+  cudaEvent_t ready = nullptr;
+  int builder_slot = -1;
+  int users = 0;           // admitted requests not yet retired
+  uint64_t last_use = 0;
+  int64_t bytes = 0;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  Request* req = nullptr;
+  int circuit = -1;
+  bool building = false;
+  void* d_buf = nullptr;     // device: bitstrings then results
+  size_t d_cap = 0;
+  void* h_buf = nullptr;     // pinned host staging
+  size_t h_cap = 0;
+  unsigned long long* d_status = nullptr;
+  unsigned long long* h_status = nullptr;
+};
+
+}  // namespace
+
+struct tn_server {
+  tn_server_opts opts{};
+  std::vector<Circuit> circuits;
+  std::vector<Slot> slots;
+  std::deque<Request*> queue;
+  std::map<uint64_t, Request*> reqs;
+  std::vector<double> latencies_us;
+  int64_t failed = 0, evictions = 0, head_bytes = 0;
+  uint64_t next_ticket = 1, tick = 0;
+  Clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  std::thread worker;
+};
+
+namespace {
+
+int ensure_slot_buffers(Slot& s, size_t dev_bytes, size_t host_bytes) {
+  if (s.d_cap < dev_bytes) {
+    cudaFree(s.d_buf);
+    s.d_buf = nullptr;
+    s.d_cap = 0;
+    if (cudaMalloc(&s.d_buf, dev_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return TN_ERR_OOM;
+    }
+    s.d_cap = dev_bytes;
+  }
+  if (s.h_cap < host_bytes) {
+    cudaFreeHost(s.h_buf);
+    s.h_buf = nullptr;
+    s.h_cap = 0;
+    if (cudaMallocHost(&s.h_buf, host_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return TN_ERR_OOM;
+    }
+    s.h_cap = host_bytes;
+  }
+  return TN_OK;
+}
+
+int64_t head_bytes_of(tn_plan_t* p) {
+  return (int64_t)p->P.tails_raw.size() * ((int64_t)16 << p->P.open_qubits.size());
+}
+
+// Enqueue one request's device work on its slot (the head is, or will be, ready).
+int enqueue_op(tn_server* sv, Slot& s, Request* q, Circuit& c) {
+  const tn_request& r = q->r;
+  tn_plan_t* p = c.plan;
+  const int h = (int)p->P.open_qubits.size();
+  const size_t esz = r.kind == TN_REQ_AMPLITUDES ? (r.dtype == TN_C128 ? 16 : 8) : 8;
+  const size_t n = (size_t)r.n;
+  const size_t in_bytes = r.kind == TN_REQ_AMPLITUDES ? n * 8 : 0;
+  const size_t out_off = (in_bytes + 255) / 256 * 256;
+  int rc = ensure_slot_buffers(s, std::max<size_t>(out_off + n * esz, 256), std::max<size_t>(out_off + n * esz, 256));
+  if (rc) return fail(rc, "server: slot staging allocation failed");
+  cudaStream_t st = s.stream;
+  if (c.state == C_BUILDING && !s.building) cudaStreamWaitEvent(st, c.ready, 0);
+  char* d = (char*)s.d_buf;
+  char* hs = (char*)s.h_buf;
+  if (r.kind == TN_REQ_AMPLITUDES) {
+    std::memcpy(hs, r.bitstrings, in_bytes);
+    if (cudaMemcpyAsync(d, hs, in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return fail(TN_ERR_CUDA, "server: H2D copy");
+    *s.h_status = ~0ULL;
+    cudaMemcpyAsync(s.d_status, s.h_status, sizeof(unsigned long long), cudaMemcpyHostToDevice, st);
+    cudaError_t e = tn::launch_amplitudes(c.head->H, h, p->d_keys, p->d_key_groups, p->n_keys, p->P.tail_mask,
+                                          p->d_open, (const uint64_t*)d, (int64_t)n, d + out_off,
+                                          r.dtype == TN_C128 ? 1 : 0, s.d_status, st);
+    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("server: amplitudes: ") + cudaGetErrorString(e));
+    cudaMemcpyAsync(s.h_status, s.d_status, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+  } else {
+    double f_head = 0.0;
+    tn_head_fidelity(c.head, &f_head, nullptr);
+    double mix = 0.0;
+    if (r.target_fidelity > 0.0 && f_head > 0.0 && r.target_fidelity < f_head) mix = 1.0 - r.target_fidelity / f_head;
+    tn::SampleParams sp;
+    sp.H = c.head->H;
+    sp.L = (int64_t)p->P.tails_raw.size();
+    sp.h = h;
+    sp.tails = p->d_tails;
+    sp.open_mask = p->P.open_mask;
+    sp.open_q = p->d_open;
+    sp.n_qubits = p->P.n_qubits;
+    sp.n = (int64_t)n;
+    sp.mix = mix;
+    sp.seed = r.seed;
+    sp.out = (uint64_t*)(d + out_off);
+    sp.method = r.method;
+    sp.param = r.param != 0 ? r.param
+                            : (r.method == TN_SAMPLE_METROPOLIS ? ((int64_t)1 << h) : (r.method == TN_SAMPLE_FRUGAL ? 10 : 0));
+    cudaError_t e = tn::launch_sample(sp, st);
+    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("server: sample: ") + cudaGetErrorString(e));
+  }
+  if (cudaMemcpyAsync(hs + out_off, d + out_off, n * esz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return fail(TN_ERR_CUDA, "server: D2H copy");
+  return TN_OK;
+}
+
+void retire(tn_server* sv, int si) {
+  Slot& s = sv->slots[si];
+  Request* q = s.req;
+  Circuit& c = sv->circuits[s.circuit];
+  if (s.building) {
+    c.state = C_READY;
+    c.builder_slot = -1;
+    s.building = false;
+  }
+  const tn_request& r = q->r;
+  if (q->status == TN_OK) {
+    const size_t esz = r.kind == TN_REQ_AMPLITUDES ? (r.dtype == TN_C128 ? 16 : 8) : 8;
+    const size_t in_bytes = r.kind == TN_REQ_AMPLITUDES ? (size_t)r.n * 8 : 0;
+    const size_t out_off = (in_bytes + 255) / 256 * 256;
+    std::memcpy(r.out, (char*)s.h_buf + out_off, (size_t)r.n * esz);
+    if (r.kind == TN_REQ_AMPLITUDES && *s.h_status != ~0ULL) {
+      q->status = TN_ERR_NOT_IN_STATE;
+      q->err = "bitstring " + std::to_string(*s.h_status) + " has a tail that is not a group";
+    }
+  }
+  q->t_done = Clock::now();
+  q->done = true;
+  if (q->status == TN_OK)
+    sv->latencies_us.push_back(std::chrono::duration<double, std::micro>(q->t_done - q->t_submit).count());
+  else
+    ++sv->failed;
+  --c.users;
+  s.req = nullptr;
+  s.circuit = -1;
+}
+
+// Free least-recently-used idle heads until `need` more bytes fit.
+bool make_room(tn_server* sv, int64_t need) {
+  while (sv->head_bytes + need > sv->opts.hbm_budget_bytes) {
+    int victim = -1;
+    for (size_t i = 0; i < sv->circuits.size(); ++i) {
+      Circuit& c = sv->circuits[i];
+      if (c.state == C_READY && c.users == 0 && (victim < 0 || c.last_use < sv->circuits[victim].last_use))
+        victim = (int)i;
+    }
+    if (victim < 0) return false;
+    Circuit& c = sv->circuits[victim];
+    tn_head_free(c.head);
+    c.head = nullptr;
+    c.state = C_EMPTY;
+    sv->head_bytes -= c.bytes;
+    ++sv->evictions;
+  }
+  return true;
+}
+
+bool plan_building(tn_server* sv, tn_plan_t* p) {
+  for (auto& c : sv->circuits)
+    if (c.plan == p && c.state == C_BUILDING) return true;
+  return false;
+}
+
+void dispatcher(tn_server* sv) {
+  cudaSetDevice(sv->circuits.empty() ? 0 : sv->circuits[0].plan->device);
+  std::unique_lock<std::mutex> lock(sv->mu);
+  while (true) {
+    // retire finished slots
+    bool progressed = false;
+    for (size_t si = 0; si < sv->slots.size(); ++si) {
+      Slot& s = sv->slots[si];
+      if (!s.req) continue;
+      cudaError_t e = cudaEventQuery(s.done);
+      if (e == cudaErrorNotReady) continue;
+      if (e != cudaSuccess) {
+        s.req->status = TN_ERR_CUDA;
+        s.req->err = std::string("server: ") + cudaGetErrorString(e);
+      }
+      retire(sv, (int)si);
+      progressed = true;
+    }
+    if (progressed) sv->cv_done.notify_all();
+    if (sv->stop && sv->queue.empty()) {
+      bool busy = false;
+      for (auto& s : sv->slots) busy |= s.req != nullptr;
+      if (!busy) break;
+    }
+    // admit queued requests into free slots (requests that need no new
+    // memory may pass one that waits for room)
+    for (auto it = sv->queue.begin(); it != sv->queue.end();) {
+      int free_slot = -1;
+      for (size_t si = 0; si < sv->slots.size(); ++si)
+        if (!sv->slots[si].req) { free_slot = (int)si; break; }
+      if (free_slot < 0) break;
+      Request* q = *it;
+      Circuit& c = sv->circuits[q->r.circuit];
+      Slot& s = sv->slots[free_slot];
+      bool build = false;
+      if (c.state == C_EMPTY) {
+        if (plan_building(sv, c.plan)) { ++it; continue; }   // the plan's workspace is in use
+        if (!make_room(sv, c.bytes)) { ++it; continue; }
+        tn_head_t* hd = nullptr;
+        if (tn_head_create(c.plan, nullptr, &hd) != TN_OK) {
+          q->status = TN_ERR_OOM;
+          q->err = "server: head allocation failed";
+          q->done = true;
+          ++sv->failed;
+          it = sv->queue.erase(it);
+          sv->cv_done.notify_all();
+          continue;
+        }
+        c.head = hd;
+        sv->head_bytes += c.bytes;
+        c.state = C_BUILDING;
+        c.builder_slot = free_slot;
+        build = true;
+      }
+      q->t_start = Clock::now();
+      s.req = q;
+      s.circuit = q->r.circuit;
+      s.building = build;
+      ++c.users;
+      c.last_use = ++sv->tick;
+      int rc = TN_OK;
+      if (build) {
+        rc = tn::enqueue_slices(c.plan, c.kept, c.head->H, s.stream);
+        if (rc == TN_OK) {
+          tn::mark_slices_done(c.head, c.kept);
+          cudaEventRecord(c.ready, s.stream);
+        }
+      }
+      if (rc == TN_OK) rc = enqueue_op(sv, s, q, c);
+      if (rc != TN_OK) {
+        q->status = rc;
+        q->err = "server: enqueue failed";
+        if (build) {   // leave the circuit unbuilt: the next request starts over
+          cudaStreamSynchronize(s.stream);
+          tn_head_free(c.head);
+          c.head = nullptr;
+          sv->head_bytes -= c.bytes;
+          c.state = C_EMPTY;
+          c.builder_slot = -1;
+          s.building = false;
+        }
+      }
+      cudaEventRecord(s.done, s.stream);
+      it = sv->queue.erase(it);
+    }
+    // wait for new work or poll the device again shortly
+    sv->cv_work.wait_for(lock, std::chrono::microseconds(50));
+  }
+}
+
+}  // namespace
+
+extern "C" int tn_server_create(const tn_server_opts* opts, tn_server_t** out) {
+  if (!out) return fail(TN_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  tn_server* sv = new tn_server();
+  sv->opts.n_slots = opts && opts->n_slots > 0 ? opts->n_slots : 8;
+  sv->opts.hbm_budget_bytes = opts && opts->hbm_budget_bytes > 0 ? opts->hbm_budget_bytes : ((int64_t)64 << 30);
+  if (sv->opts.n_slots > 64) {
+    delete sv;
+    return fail(TN_ERR_INVALID, "at most 64 slots");
+  }
+  sv->slots.resize(sv->opts.n_slots);
+  for (auto& s : sv->slots) {
+    if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&s.d_status, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&s.h_status, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      tn_server_free(sv);
+      return fail(TN_ERR_CUDA, "server: slot set-up failed");
+    }
+  }
+  sv->t0 = Clock::now();
+  *out = sv;
+  return TN_OK;
+}
+
+extern "C" int tn_server_add_circuit(tn_server_t* sv, tn_plan_t* plan, tn_range kept, int* circuit_id) {
+  if (!sv || !plan || !circuit_id) return fail(TN_ERR_INVALID, "NULL argument");
+  if (!plan->on_device) return fail(TN_ERR_INVALID, "plan was made host_only");
+  const int64_t ns = 1LL << plan->P.n_sliced;
+  if (kept.begin < 0 || kept.end > ns || kept.begin >= kept.end) return fail(TN_ERR_INVALID, "bad kept slice range");
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (sv->worker.joinable()) return fail(TN_ERR_INVALID, "add circuits before the first submit");
+  Circuit c;
+  c.plan = plan;
+  c.kept = kept;
+  c.bytes = head_bytes_of(plan);
+  if (cudaEventCreateWithFlags(&c.ready, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TN_ERR_CUDA, "server: event");
+  }
+  sv->circuits.push_back(c);
+  *circuit_id = (int)sv->circuits.size() - 1;
+  return TN_OK;
+}
+
+extern "C" int tn_server_submit(tn_server_t* sv, const tn_request* r, uint64_t* ticket) {
+  if (!sv || !r || !ticket) return fail(TN_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (sv->stop) return fail(TN_ERR_INVALID, "server is stopping");
+  if (r->circuit < 0 || r->circuit >= (int)sv->circuits.size()) return fail(TN_ERR_INVALID, "unknown circuit");
+  if (r->kind != TN_REQ_AMPLITUDES && r->kind != TN_REQ_SAMPLE) return fail(TN_ERR_INVALID, "unknown request kind");
+  if (r->n < 1 || !r->out || (r->kind == TN_REQ_AMPLITUDES && !r->bitstrings))
+    return fail(TN_ERR_INVALID, "request needs n >= 1 and its buffers");
+  if (r->kind == TN_REQ_AMPLITUDES && r->dtype != TN_C64 && r->dtype != TN_C128)
+    return fail(TN_ERR_INVALID, "dtype must be TN_C64 or TN_C128");
+  if (r->kind == TN_REQ_SAMPLE && (r->method < TN_SAMPLE_EXACT || r->method > TN_SAMPLE_FRUGAL))
+    return fail(TN_ERR_INVALID, "unknown sampling method");
+  if (sv->circuits[r->circuit].bytes > sv->opts.hbm_budget_bytes)
+    return fail(TN_ERR_OOM, "the circuit's head is larger than the server's HBM budget");
+  Request* q = new Request();
+  q->ticket = sv->next_ticket++;
+  q->r = *r;
+  q->t_submit = Clock::now();
+  sv->reqs[q->ticket] = q;
+  sv->queue.push_back(q);
+  if (!sv->worker.joinable()) sv->worker = std::thread(dispatcher, sv);
+  *ticket = q->ticket;
+  sv->cv_work.notify_one();
+  return TN_OK;
+}
+
+extern "C" int tn_server_wait(tn_server_t* sv, uint64_t ticket, tn_request_result* res) {
+  if (!sv) return fail(TN_ERR_INVALID, "NULL server");
+  std::unique_lock<std::mutex> lock(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return fail(TN_ERR_INVALID, "unknown ticket");
+  Request* q = it->second;
+  sv->cv_done.wait(lock, [&] { return q->done; });
+  if (res) {
+    res->status = q->status;
+    res->latency_us = std::chrono::duration<double, std::micro>(q->t_done - q->t_submit).count();
+    res->queue_us = q->t_start.time_since_epoch().count() == 0
+                        ? 0.0
+                        : std::chrono::duration<double, std::micro>(q->t_start - q->t_submit).count();
+  }
+  const int st = q->status;
+  const std::string err = q->err;
+  sv->reqs.erase(it);
+  delete q;
+  if (st != TN_OK) return fail(st, err);
+  return TN_OK;
+}
+
+extern "C" int tn_server_get_stats(tn_server_t* sv, tn_server_stats* out) {
+  if (!sv || !out) return fail(TN_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lock(sv->mu);
+  std::memset(out, 0, sizeof(*out));
+  std::vector<double> v = sv->latencies_us;
+  std::sort(v.begin(), v.end());
+  out->completed = (int64_t)v.size();
+  out->failed = sv->failed;
+  out->queued = (int64_t)sv->queue.size();
+  for (auto& s : sv->slots) out->in_flight += s.req != nullptr;
+  if (!v.empty()) {
+    out->p50_us = v[(v.size() - 1) / 2];
+    out->p99_us = v[std::min(v.size() - 1, (size_t)((v.size() - 1) * 0.99 + 0.5))];
+    double sum = 0;
+    for (double x : v) sum += x;
+    out->mean_us = sum / (double)v.size();
+  }
+  for (auto& c : sv->circuits) out->heads_cached += c.state != C_EMPTY;
+  out->head_bytes = sv->head_bytes;
+  out->evictions = sv->evictions;
+  out->wall_s = std::chrono::duration<double>(Clock::now() - sv->t0).count();
+  return TN_OK;
+}
+
+extern "C" void tn_server_free(tn_server_t* sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->stop = true;
+    sv->cv_work.notify_all();
+  }
+  if (sv->worker.joinable()) sv->worker.join();
+  for (auto& s : sv->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    cudaStreamDestroy(s.stream);
+    cudaEventDestroy(s.done);
+    cudaFree(s.d_buf);
+    cudaFreeHost(s.h_buf);
+    cudaFree(s.d_status);
+    cudaFreeHost(s.h_status);
+  }
+  for (auto& c : sv->circuits) {
+    if (c.head) tn_head_free(c.head);
+    if (c.ready) cudaEventDestroy(c.ready);
+  }
+  for (auto& kv : sv->reqs) delete kv.second;
+  delete sv;
+}

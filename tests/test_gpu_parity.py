@@ -298,3 +298,196 @@ def test_profile_and_reset(tn):
     assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg))
     kinds = [tn.tn_plan_step_info(plan, i)[0] for i in range(st["n_launches"])]
     assert kinds[-1] == -1 and set(kinds[:-1]) <= {0, 1, 2, 3, 4, 5}
+
+
+@pytest.mark.parametrize("gemm", [0, 3], ids=["tc", "bf16"])
+def test_companion_cuts_parity_and_f_est(tn, gemm):
+    """Companion cuts on the GPU path vs the oracle with the partner outputs
+    fixed; F_est = prod (1 + sin^2 theta)/2 over the companions."""
+    import math
+    c = ci.make_grid_circuit(4, 4, 10, seed=17)
+    cut = ci.mid_circuit_cut_edges(c, 3)
+    g0, g1, g2 = cut[0][0], cut[2][0], cut[4][0]
+    edges = [(g0, 0, tn.TN_EDGE_COMPANION, 0), (g1, 1, tn.TN_EDGE_COMPANION, 0), (g2, 0, tn.TN_EDGE_SLICE, 0)]
+    oq = list(range(10, 16))
+    tails = ci.draw_tails(16, oq, 12, seed=5)
+    cfg = dict(circuit=c, open_qubits=oq, tails=tails, edges=edges)
+    plan, head = contract_all(tn, cfg, gemm=gemm)
+    H = read_head(tn, plan, head, cfg)
+    se = [(g0, 0, True), (g1, 1, True), (g2, 0)]
+    ref = O.sparse_state_from_vector(O.sliced_statevector(c, se), oq, tails)
+    assert_close(H, ref, REL_L2_BF16 if gemm == 3 else REL_L2)
+    f, done = tn.tn_head_fidelity(head)
+    expect = O.companion_factor(c.gates[g0].theta) * O.companion_factor(c.gates[g1].theta)
+    assert done == 8 and abs(f - expect) < 1e-12
+
+
+@pytest.mark.parametrize("L,h,n,T", [(64, 6, 256, 64), (16, 10, 64, 300), (1, 8, 500, 40)])
+def test_metropolis_sampler_matches_oracle_bit_exact(tn, L, h, n, T):
+    """In-group Metropolis chain: both sides draw the same Philox stream and
+    compare round-to-nearest FP64 weights, so every sample must agree."""
+    plan, head, buf, H, tails, oq = _synthetic_head(tn, L, h, seed=L + 3 * h)
+    seed = 0xABCDEF12345
+    s = tn.tn_sample_ex(head, n, 0.0, seed, tn.TN_SAMPLE_METROPOLIS, T)
+    ref = O.sample_groups_mcmc(H, tails, oq, 30, n, 0.0, 1.0, seed, "metropolis", T)
+    assert np.array_equal(s, ref)
+
+
+@pytest.mark.parametrize("L,h,n,M", [(64, 6, 256, 10), (32, 10, 64, 4)])
+def test_frugal_sampler_matches_oracle(tn, L, h, n, M):
+    """Frugal rejection: same stream on both sides; the group sum Z is summed
+    in a different order, so a draw may differ only when it sits within 1e-12
+    (relative) of its acceptance threshold."""
+    plan, head, buf, H, tails, oq = _synthetic_head(tn, L, h, seed=L + h + 1)
+    seed = 4242
+    s = tn.tn_sample_ex(head, n, 0.0, seed, tn.TN_SAMPLE_FRUGAL, M)
+    ref = O.sample_groups_mcmc(H, tails, oq, 30, n, 0.0, 1.0, seed, "frugal", M)
+    bad = np.nonzero(s != ref)[0]
+    assert len(bad) <= 1
+    for i in bad:
+        lo_ref = O.sample_groups_mcmc(H * (1 + 1e-12), tails, oq, 30, i + 1, 0.0, 1.0, seed, "frugal", M)[i]
+        hi_ref = O.sample_groups_mcmc(H * (1 - 1e-12), tails, oq, 30, i + 1, 0.0, 1.0, seed, "frugal", M)[i]
+        assert s[i] in (lo_ref, hi_ref)
+
+
+def test_sampler_methods_mixing_and_errors(tn):
+    plan, head, buf, H, tails, oq = _synthetic_head(tn, 64, 6, seed=2)
+    tn.tn_head_set_fidelity(head, 0.5)
+    s = tn.tn_sample_ex(head, 300, 0.1, 9, tn.TN_SAMPLE_METROPOLIS, 32)
+    ref = O.sample_groups_mcmc(H, tails, oq, 30, 300, 0.1, 0.5, 9, "metropolis", 32)
+    assert np.array_equal(s, ref)
+    with pytest.raises(tn.TNError):
+        tn.tn_sample_ex(head, 10, 0.0, 1, 7, 0)
+
+
+def _heads_array(tn, plan, head, cfg):
+    return read_head(tn, plan, head, cfg)
+
+
+def test_graph_replay_equals_plain_launches(tn):
+    """Batched form: the slice range captured as a CUDA graph and replayed
+    gives bit-identical heads to the plain launches (same kernels, order)."""
+    cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    h1 = tn.tn_head_create(plan)
+    h2 = tn.tn_head_create(plan)
+    tn.tn_contract_slices(plan, 0, 16, h1)
+    tn.tn_contract_slices_graph(plan, 0, 16, h2)
+    A, B = read_head(tn, plan, h1, cfg), read_head(tn, plan, h2, cfg)
+    assert np.array_equal(A, B)
+    assert_close(B, oracle_head(cfg))
+    tn.tn_head_reset(h2)
+    tn.tn_contract_slices_graph(plan, 0, 16, h2)        # replay of the cached graph
+    assert np.array_equal(read_head(tn, plan, h2, cfg), A)
+    with pytest.raises(tn.TNError):
+        tn.tn_contract_slices_graph(plan, 0, 4, h2)      # already accumulated
+
+
+def test_batch_of_mixed_circuits_in_one_graph(tn):
+    """Many small circuits of uneven step shapes as parallel branches of one
+    graph: each head equals its own plain contraction and the oracle."""
+    shapes = [(3, 3, 6, 3, 4, 0), (3, 4, 8, 4, 6, 1), (4, 4, 6, 6, 8, 1), (2, 5, 8, 5, 4, 0),
+              (4, 5, 8, 6, 16, 2), (3, 5, 10, 5, 8, 1)]
+    cfgs, plans, heads, refs, plain = [], [], [], [], []
+    for i, (r, c, m, h, L, cut) in enumerate(shapes):
+        cfg = ci.config_small(r, c, m, seed=40 + i, n_open=h, L=L, n_cut_gates=cut)
+        p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+        cfgs.append(cfg)
+        plans.append(p)
+        heads.append(tn.tn_head_create(p))
+        hp = tn.tn_head_create(p)
+        k = tn.tn_plan_get_stats(p)["n_sliced"]
+        tn.tn_contract_slices(p, 0, 1 << k, hp)
+        plain.append(read_head(tn, p, hp, cfg))
+    ranges = [(0, 1 << tn.tn_plan_get_stats(p)["n_sliced"]) for p in plans]
+    tn.tn_contract_batch(plans, ranges, heads)
+    for cfg, p, hd, pl in zip(cfgs, plans, heads, plain):
+        H = read_head(tn, p, hd, cfg)
+        assert np.array_equal(H, pl)
+        assert_close(H, oracle_head(cfg))
+    for hd in heads:
+        tn.tn_head_reset(hd)
+    tn.tn_contract_batch(plans, ranges, heads)             # cached graph replay
+    for cfg, p, hd, pl in zip(cfgs, plans, heads, plain):
+        assert np.array_equal(read_head(tn, p, hd, cfg), pl)
+    with pytest.raises(tn.TNError):
+        tn.tn_contract_batch(plans[:2], ranges[:2], [heads[0], heads[0]])
+
+
+def _server_cases(tn):
+    shapes = [(3, 4, 8, 4, 16, 1), (4, 4, 8, 6, 32, 2), (3, 5, 10, 5, 64, 1)]
+    out = []
+    for i, (r, c, m, h, L, cut) in enumerate(shapes):
+        cfg = ci.config_small(r, c, m, seed=60 + i, n_open=h, L=L, n_cut_gates=cut)
+        plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+        k = tn.tn_plan_get_stats(plan)["n_sliced"]
+        kept = (0, max(1, (1 << k) // 2))                  # kept fraction 1/2 (1 when k = 0)
+        out.append((cfg, plan, kept))
+    return out
+
+
+def _requests(cases, rng):
+    reqs = []
+    for j in range(24):
+        ci_ = j % len(cases)
+        cfg = cases[ci_][0]
+        if j % 3 == 2:
+            reqs.append(dict(circuit=ci_, kind=1, n=int(rng.integers(10, 200)), seed=int(rng.integers(1 << 40)),
+                             method=int(j % 9 // 3)))
+        else:
+            oq, tails = cfg["open_qubits"], cfg["tails"]
+            g = rng.integers(0, len(tails), 300)
+            mu = rng.integers(0, 1 << len(oq), 300)
+            bits = np.array([O.bitstring_index(int(tails[a]), oq, int(b)) for a, b in zip(g, mu)], np.uint64)
+            reqs.append(dict(circuit=ci_, kind=0, bits=bits))
+    return reqs
+
+
+def _submit(tn, sv, q):
+    if q["kind"] == 0:
+        return tn.tn_server_submit(sv, q["circuit"], tn.TN_REQ_AMPLITUDES, 0, bitstrings=q["bits"])
+    return tn.tn_server_submit(sv, q["circuit"], tn.TN_REQ_SAMPLE, q["n"], seed=q["seed"], method=q["method"],
+                               param=16 if q["method"] == 1 else 0)
+
+
+def test_server_results_same_alone_and_in_the_mix(tn):
+    """Serving: every request's result equals the plain API on a directly
+    contracted head, whether it ran alone or admitted into a busy server
+    (continuous admission, overlapping slots, LRU head eviction)."""
+    cases = _server_cases(tn)
+    rng = np.random.default_rng(7)
+    reqs = _requests(cases, rng)
+    # expected: plain calls on heads built directly
+    expect = []
+    heads = []
+    for cfg, plan, kept in cases:
+        hd = tn.tn_head_create(plan)
+        tn.tn_contract_slices(plan, kept[0], kept[1], hd)
+        heads.append(hd)
+    for q in reqs:
+        hd = heads[q["circuit"]]
+        if q["kind"] == 0:
+            expect.append(tn.tn_amplitudes(hd, q["bits"]))
+        else:
+            expect.append(tn.tn_sample_ex(hd, q["n"], 0.0, q["seed"], q["method"], 16 if q["method"] == 1 else 0))
+    del heads
+    for mode in ("alone", "mix"):
+        # heads of 4, 32 and 32 KiB: a 40 kB budget holds two at a time, forcing evictions
+        sv = tn.tn_server_create(n_slots=4, hbm_budget_bytes=(64 << 30) if mode == "alone" else 40_000)
+        for cfg, plan, kept in cases:
+            tn.tn_server_add_circuit(sv, plan, kept[0], kept[1])
+        got = []
+        if mode == "alone":
+            for q in reqs:
+                got.append(tn.tn_server_wait(sv, _submit(tn, sv, q))[0])
+        else:
+            tickets = [_submit(tn, sv, q) for q in reqs]
+            got = [tn.tn_server_wait(sv, t)[0] for t in tickets]
+        st = tn.tn_server_get_stats(sv)
+        assert st["completed"] == len(reqs) and st["failed"] == 0
+        assert 0 < st["p50_us"] <= st["p99_us"]
+        if mode == "mix":
+            assert st["evictions"] > 0
+        for q, a, b in zip(reqs, got, expect):
+            assert np.array_equal(a, b), (mode, q["kind"])
+        tn.tn_server_free(sv)

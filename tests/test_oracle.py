@@ -274,3 +274,86 @@ def test_paper_sparse_state_example_amplitudes():
     assert np.abs(H - H2).max() < 1e-14
     for g, t in enumerate(tails):
         assert H[g, 0] == psi[int(t)]
+
+
+# ---------------- companion cuts (Method case (ii)) ----------------
+
+def _with_theta(c, gi, theta):
+    g = c.gates[gi]
+    c2 = ci.Circuit(c.n_qubits, list(c.gates), c.rows, c.cols, c.cycles, c.seed, c.cycle_first_gate)
+    c2.gates[gi] = ci.Gate(2, g.q0, g.q1, ci.fsim(theta, g.phi), kind="fsim", theta=theta, phi=g.phi)
+    return c2
+
+
+def test_companion_cut_exact_at_theta_half_pi():
+    """cos(theta) = 0 makes the dropped singular value zero: slicing an input of
+    fSim(pi/2, phi) with its companion and summing all slices is exact."""
+    c = ci.make_grid_circuit(3, 3, 6, seed=14)
+    gi = ci.mid_circuit_cut_edges(c, 1)[0][0]
+    c = _with_theta(c, gi, math.pi / 2)
+    exact = O.statevector(c)
+    for leg in (0, 1):
+        hat = O.sliced_statevector(c, [(gi, leg, True)])
+        assert np.abs(hat - exact).max() < 1e-14
+
+
+def test_companion_matches_between_oracle_routes():
+    c = ci.make_grid_circuit(3, 4, 6, seed=15)
+    cut = ci.mid_circuit_cut_edges(c, 2)
+    se = [(cut[0][0], 0, True), (cut[2][0], 1, True), (cut[3][0], 0)]
+    oq = [8, 9, 10, 11]
+    tails = ci.draw_tails(12, oq, 5, seed=2)
+    H1 = O.sparse_state_from_vector(O.sliced_statevector(c, se), oq, tails)
+    H2 = O.network_amplitudes(c, oq, tails, se)
+    assert np.abs(H1 - H2).max() < 1e-14
+
+
+def test_companion_fidelity_tracks_estimate():
+    """One companion cut at theta = pi/2 - 0.3 keeps fidelity ~ (1+sin^2)/2."""
+    c = ci.make_grid_circuit(4, 4, 12, seed=16)
+    gi = ci.mid_circuit_cut_edges(c, 1)[0][0]
+    th = math.pi / 2 - 0.3
+    c = _with_theta(c, gi, th)
+    psi = O.statevector(c)
+    hat = O.sliced_statevector(c, [(gi, 0, True)])
+    F = O.fidelity(psi, hat)
+    assert abs(F - O.companion_factor(th)) < 0.03, (F, O.companion_factor(th))
+
+
+# ---------------- in-group Markov chain and frugal sampling ----------------
+
+def test_metropolis_chain_converges_to_group_law():
+    """The Metropolis chain with uniform proposals has the categorical law
+    w/Z as its stationary law (Method, last paragraph)."""
+    H = ci.synthetic_head(1, 3, seed=8)
+    w = np.abs(H[0]) ** 2
+    w /= w.sum()
+    n = 6000
+    s = O.sample_groups_mcmc(H, np.zeros(1, np.uint64), [0, 1, 2], 3, n, 0.0, 1.0, 5, "metropolis", 64)
+    cnt = np.bincount(s.astype(np.int64), minlength=8)
+    chi2 = ((cnt - n * w) ** 2 / (n * w)).sum()
+    assert chi2 < 24.3                                  # chi2(7) 99.9%
+
+
+def test_frugal_sampling_exact_when_bound_holds_and_xeb():
+    """Frugal rejection is exact when M bounds l*w/Z; under Porter-Thomas
+    with l = 64 and M = 10 its XEB matches the Dirichlet closed form
+    (l-1)/(l+1) (Supplement: frugal sampling is near-perfect at l = 64)."""
+    H = ci.synthetic_head(1, 3, seed=9)
+    w = np.abs(H[0]) ** 2
+    M = 8.0 * w.max() / w.mean()                        # bound holds
+    n = 6000
+    s = O.sample_groups_mcmc(H, np.zeros(1, np.uint64), [0, 1, 2], 3, n, 0.0, 1.0, 6, "frugal", int(np.ceil(M)))
+    cnt = np.bincount(s.astype(np.int64), minlength=8)
+    p = w / w.sum()
+    assert ((cnt - n * p) ** 2 / (n * p)).sum() < 24.3
+    L, h = 3000, 6
+    l = 1 << h
+    H = ci.synthetic_head(L, h, seed=10)
+    n_q = 30
+    P = np.abs(H) ** 2 / 2 ** n_q
+    s = O.sample_groups_mcmc(H, np.arange(L, dtype=np.uint64) << np.uint64(h), list(range(h)), n_q, L, 0.0, 1.0,
+                             7, "frugal", 10)
+    mu = (s & np.uint64(l - 1)).astype(np.int64)
+    x = 2 ** n_q * P[np.arange(L), mu]
+    assert abs(x.mean() - 1 - (l - 1) / (l + 1)) < 3 * x.std() / math.sqrt(L) + 0.01
