@@ -113,6 +113,8 @@ typedef struct {
   double  max_log2_elements;  /* largest intermediate */
   int64_t workspace_bytes;    /* device arena of one slice */
   int     n_gemm_tc, n_gemm_simt, n_small, n_permute;  /* step counts by kernel kind */
+  double  measured_slice_ms;  /* tn_plan_autotune: measured time of one slice (0 otherwise) */
+  int     autotune_candidates;/* tn_plan_autotune: distinct orders timed */
 } tn_plan_stats;
 
 /* Plan the contraction (host).  `order`: n_pairs pairs (i, j) of leaf ids, the
@@ -127,6 +129,14 @@ int tn_plan(const tn_circuit* circuit, const tn_open_spec* open_spec,
             const int32_t* order, int64_t n_pairs,
             const tn_plan_opts* opts, tn_plan_t** out);
 void tn_plan_free(tn_plan_t* plan);
+/* Autotuner: builds up to n_candidates plans whose orders come from greedy
+ * searches with seeds opts->order_seed + c (each with opts->order_trials
+ * restarts), times one slice of each distinct order on the current device
+ * (CUDA events on `stream`, after one untimed slice), and returns the fastest
+ * in *out (the others are freed).  Same arguments and errors as tn_plan. */
+int tn_plan_autotune(const tn_circuit* circuit, const tn_open_spec* open_spec,
+                     const tn_edge* sliced_edges, int n_edges, const tn_plan_opts* opts,
+                     int n_candidates, void* stream, tn_plan_t** out);
 int  tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* out);
 /* Copies up to `cap` pairs of the order used into pairs[2*i], pairs[2*i+1];
  * *n_pairs receives the full count. */

@@ -88,7 +88,8 @@ class tn_plan_stats(C.Structure):
                 ("n_sliced", C.c_int), ("n_pinned", C.c_int), ("n_leaves", C.c_int), ("n_contractions", C.c_int),
                 ("n_launches", C.c_int), ("tc_macs", C.c_double), ("alg_bytes", C.c_double),
                 ("max_log2_elements", C.c_double), ("workspace_bytes", C.c_int64),
-                ("n_gemm_tc", C.c_int), ("n_gemm_simt", C.c_int), ("n_small", C.c_int), ("n_permute", C.c_int)]
+                ("n_gemm_tc", C.c_int), ("n_gemm_simt", C.c_int), ("n_small", C.c_int), ("n_permute", C.c_int),
+                ("measured_slice_ms", C.c_double), ("autotune_candidates", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -104,6 +105,8 @@ def _load():
     vp, i64, i32p = C.c_void_p, C.c_int64, C.POINTER(C.c_int32)
     lib.tn_plan.argtypes = [C.POINTER(tn_circuit), C.POINTER(tn_open_spec), C.POINTER(tn_edge), C.c_int, i32p, i64,
                             C.POINTER(tn_plan_opts), C.POINTER(vp)]
+    lib.tn_plan_autotune.argtypes = [C.POINTER(tn_circuit), C.POINTER(tn_open_spec), C.POINTER(tn_edge), C.c_int,
+                                     C.POINTER(tn_plan_opts), C.c_int, vp, C.POINTER(vp)]
     lib.tn_plan_free.argtypes = [vp]
     lib.tn_plan_free.restype = None
     lib.tn_plan_get_stats.argtypes = [vp, C.POINTER(tn_plan_stats)]
@@ -137,7 +140,7 @@ def _load():
     lib.tn_head_norm_noalloc.argtypes = [vp, i64, C.c_int, vp, vp]
     lib.tn_last_error.restype = C.c_char_p
     lib.tn_version.restype = C.c_char_p
-    for name in ("tn_plan", "tn_plan_get_stats", "tn_plan_order", "tn_head_create", "tn_head_fidelity",
+    for name in ("tn_plan", "tn_plan_autotune", "tn_plan_get_stats", "tn_plan_order", "tn_head_create", "tn_head_fidelity",
                  "tn_head_set_fidelity", "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm",
                  "tn_profile_slices", "tn_plan_step_info", "tn_head_reset", "tn_head_norm_noalloc", "tn_sample_ex",
                  "tn_contract_slices_graph", "tn_contract_batch", "tn_server_create", "tn_server_add_circuit",
@@ -149,7 +152,7 @@ def _load():
 _lib = _load()
 lib = _lib
 
-EXPORTED = ["tn_plan", "tn_plan_free", "tn_plan_get_stats", "tn_plan_order", "tn_plan_describe",
+EXPORTED = ["tn_plan", "tn_plan_autotune", "tn_plan_free", "tn_plan_get_stats", "tn_plan_order", "tn_plan_describe",
             "tn_head_create", "tn_head_free", "tn_head_data", "tn_head_reset", "tn_head_fidelity", "tn_head_set_fidelity",
             "tn_contract_slices", "tn_contract_slices_graph", "tn_contract_batch", "tn_amplitudes", "tn_sample", "tn_sample_ex", "tn_head_norm", "tn_profile_slices",
             "tn_plan_step_info", "tn_head_norm_noalloc", "tn_server_create", "tn_server_add_circuit",
@@ -245,6 +248,26 @@ def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements
                             o.size // 2, C.byref(opts), C.byref(h)))
     else:
         _check(_lib.tn_plan(C.byref(circ), C.byref(spec), ed, len(edges), None, 0, C.byref(opts), C.byref(h)))
+    return Plan(h, (gates, oq, t, ed))
+
+
+def tn_plan_autotune(circuit, open_qubits, tails, edges=(), n_candidates=4, max_log2_elements=0.0,
+                     gemm=TN_GEMM_AUTO, order_trials=0, order_seed=0, max_host_absorb_log2=0, small_max_bits=0,
+                     stream=None) -> Plan:
+    gates = gates_to_c(circuit)
+    circ = tn_circuit(int(circuit.n_qubits), len(circuit.gates), gates)
+    oq = (C.c_int * max(1, len(open_qubits)))(*[int(q) for q in open_qubits])
+    t = np.ascontiguousarray(np.asarray(tails, dtype=np.uint64))
+    spec = tn_open_spec(oq, len(open_qubits), t.ctypes.data_as(C.POINTER(C.c_uint64)), int(t.size))
+    ed = (tn_edge * max(1, len(edges)))()
+    for i, e in enumerate(edges):
+        g, leg, kind, val = (list(e) + [TN_EDGE_SLICE, 0])[:4] if len(e) < 4 else e
+        ed[i] = tn_edge(int(g), int(leg), int(kind), int(val))
+    opts = tn_plan_opts(float(max_log2_elements), int(gemm), 0, int(order_trials), int(order_seed),
+                        int(max_host_absorb_log2), int(small_max_bits))
+    h = C.c_void_p()
+    _check(_lib.tn_plan_autotune(C.byref(circ), C.byref(spec), ed, len(edges), C.byref(opts), int(n_candidates),
+                                 _stream(stream), C.byref(h)))
     return Plan(h, (gates, oq, t, ed))
 
 

@@ -69,12 +69,12 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         jobs.append(cmd)
     for s in CPP_SOURCES:
         o = os.path.join(OBJDIR, os.path.splitext(s)[0] + ".o")
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-I", INCLUDE,
+        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-pthread", "-I", INCLUDE,
                      "-I", os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include"),
                      "-c", os.path.join(CSRC, s), "-o", o])
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
-    link = [nvcc, "-shared", *ARCH, "-cudart", "static", "-o", LIBPATH, *_objs()]
+    link = [nvcc, "-shared", *ARCH, "-cudart", "static", "-Xcompiler", "-pthread", "-o", LIBPATH, *_objs()]
     logs.append(_run(link))
     if verbose:
         for l in logs:

@@ -198,6 +198,8 @@ extern "C" int tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* s) {
   s->alg_bytes = P.alg_bytes;
   s->max_log2_elements = P.max_log2;
   s->workspace_bytes = P.workspace_bytes;
+  s->measured_slice_ms = plan->measured_slice_ms;
+  s->autotune_candidates = plan->autotune_candidates;
   for (auto& st : P.steps) {
     if (st.kind == tn::ST_GEMM_TC) ++s->n_gemm_tc;
     if (st.kind == tn::ST_GEMM_SIMT) ++s->n_gemm_simt;
@@ -740,3 +742,78 @@ int enqueue_slices(tn_plan_t* plan, tn_range r, double2* H, cudaStream_t stream)
 int check_slice_range(tn_plan_t* plan, tn_range r, tn_head_t* head) { return check_range(plan, r, head); }
 void mark_slices_done(tn_head_t* head, tn_range r) { mark_done(head, r); }
 }  // namespace tn
+
+extern "C" int tn_plan_autotune(const tn_circuit* circuit, const tn_open_spec* open_spec, const tn_edge* sliced_edges,
+                                int n_edges, const tn_plan_opts* opts, int n_candidates, void* stream,
+                                tn_plan_t** out) {
+  if (!out) return fail(TN_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_candidates < 1 || n_candidates > 64) return fail(TN_ERR_INVALID, "n_candidates must be in [1, 64]");
+  tn_plan_opts o{};
+  if (opts) o = *opts;
+  if (o.host_only) return fail(TN_ERR_INVALID, "autotuning needs the device");
+  const uint64_t seed0 = o.order_seed ? o.order_seed : 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  tn_plan_t* best = nullptr;
+  double best_ms = 1e300;
+  int distinct = 0;
+  std::vector<std::vector<std::pair<int, int>>> seen;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  int last_rc = TN_OK;
+  for (int c = 0; c < n_candidates; ++c) {
+    o.order_seed = seed0 + (uint64_t)c;
+    tn_plan_opts ho = o;
+    ho.host_only = 1;
+    tn_plan_t* hp = nullptr;
+    int rc = tn_plan(circuit, open_spec, sliced_edges, n_edges, nullptr, 0, &ho, &hp);
+    if (rc) { last_rc = rc; continue; }
+    bool dup = false;
+    for (auto& s_ : seen) dup |= s_ == hp->P.order;
+    if (dup) { tn_plan_free(hp); continue; }
+    seen.push_back(hp->P.order);
+    // upload this candidate (same order, now on the device)
+    std::vector<int32_t> pairs;
+    for (auto& pr : hp->P.order) { pairs.push_back(pr.first); pairs.push_back(pr.second); }
+    tn_plan_free(hp);
+    tn_plan_opts dopt = o;
+    dopt.host_only = 0;
+    tn_plan_t* p = nullptr;
+    rc = tn_plan(circuit, open_spec, sliced_edges, n_edges, pairs.data(), (int64_t)pairs.size() / 2, &dopt, &p);
+    if (rc) { last_rc = rc; continue; }
+    ++distinct;
+    tn_head_t* h = nullptr;
+    rc = tn_head_create(p, nullptr, &h);
+    double ms = 1e300;
+    if (rc == TN_OK) {
+      rc = run_slice(p, 0, h->H, st);   // untimed
+      if (rc == TN_OK) {
+        cudaEventRecord(e0, st);
+        rc = run_slice(p, 0, h->H, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) == cudaSuccess) {
+          float f = 0.f;
+          cudaEventElapsedTime(&f, e0, e1);
+          ms = f;
+        }
+      }
+      tn_head_free(h);
+    }
+    if (rc == TN_OK && ms < best_ms) {
+      if (best) tn_plan_free(best);
+      best = p;
+      best_ms = ms;
+    } else {
+      tn_plan_free(p);
+    }
+    if (rc) last_rc = rc;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!best) return last_rc ? last_rc : fail(TN_ERR_OOM, "no candidate plan could be built");
+  best->measured_slice_ms = best_ms;
+  best->autotune_candidates = distinct;
+  *out = best;
+  return TN_OK;
+}

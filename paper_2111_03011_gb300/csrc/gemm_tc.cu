@@ -18,12 +18,12 @@
 // accuracy from Tensor Cores while surpassing the FP32 theoretical peak
 // performance", 2022).  The K loop is therefore cut into chunks of one k-block
 // (32 reduction terms): each accumulates in a fresh TMEM buffer (two,
-// ping-pong) and four drain warps fold it into a TMEM running sum with
+// ping-pong) and eight drain warps fold it into a TMEM running sum with
 // ordinary FP32 adds.
 //
-// Roles (192 threads): warps 0-3 drain chunk accumulators into the running sum
-// and write the tile out, warp 4 issues TMA loads, warp 5 owns TMEM and issues
-// the MMAs.  One CTA computes a 128 x BN tile of C_r.  Every mbarrier wait is
+// Roles (320 threads): warps 0-7 drain chunk accumulators into the running sum
+// and write the tile out (two warps per TMEM lane quarter, half the columns
+// each), warp 8 issues TMA loads, warp 9 owns TMEM and issues the MMAs.  One CTA computes a 128 x BN tile of C_r.  Every mbarrier wait is
 // bounded; on timeout the CTA records a status code and leaves its loops
 // instead of hanging.
 #include <cuda.h>
@@ -40,7 +40,7 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK_BYTES = 128;           // one 128-byte swizzle row of K per k-block
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -219,12 +219,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 128);
+      mbar_init(&acce[b], 256);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 5) {
+  if (warp == 9) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32((const void*)tmem_slot)),
                  "r"(Lay::TMEM_COLS));
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
+  if (warp == 8) {
     if (lane == 0) {
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES, r = kb / STAGES;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_load_3d(st + 2 * Lay::A_BYTES + Lay::B_BYTES, &tmBlo, &full[s], kb * BKE, (int)(tn_ * BN), (int)pb);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     if (lane == 0) {
       const uint32_t idesc = idesc_mma<BN, BF16>();
       for (int kb = 0; kb < nkb; ++kb) {
@@ -279,8 +279,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // drain warps 0-3: TMEM lane quarter = warp
-    const int q = warp & 3;
+    // drain warps 0-7: TMEM lane quarter = warp % 4, column half = warp / 4.
+    // Each warp issues all of its TMEM loads before one wait.
+    constexpr int MAXC = BN >= 32 ? BN / 32 : 1;   // 16-column pieces per warp
+    const int q = warp & 3, half = warp >> 2;
+    const int nc = BN >= 32 ? MAXC : (half == 0 ? 1 : 0);
+    const int col0 = BN >= 32 ? half * (BN / 2) : 0;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const uint32_t sum_col = 2u * BN;
     bool ok = true;
@@ -289,48 +293,51 @@ __global__ void __launch_bounds__(kThreads, 1)
       ok = mbar_wait(&accf[b], (uint32_t)((c >> 1) & 1), abort_flag);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      if (nkb > 1) {
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          uint32_t v[16], w[16];
-          tmem_ld16(tmem + lane_base + (uint32_t)(b * BN + c0), v);
-          if (c > 0) {
-            tmem_ld16(tmem + lane_base + sum_col + (uint32_t)c0, w);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (nkb > 1 && nc > 0) {
+        uint32_t v[MAXC][16], w[MAXC][16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
-          } else {
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int j = 0; j < MAXC; ++j) {
+          tmem_ld16(tmem + lane_base + (uint32_t)(b * BN + col0 + 16 * j), v[j]);
+          if (c > 0) tmem_ld16(tmem + lane_base + sum_col + (uint32_t)(col0 + 16 * j), w[j]);
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < MAXC; ++j) {
+          if (c > 0) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              v[j][e] = __float_as_uint(__uint_as_float(v[j][e]) + __uint_as_float(w[j][e]));
           }
-          tmem_st16(tmem + lane_base + sum_col + (uint32_t)c0, v);
+          tmem_st16(tmem + lane_base + sum_col + (uint32_t)(col0 + 16 * j), v[j]);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       mbar_arrive(&acce[b]);
     }
-    if (ok) {
-      // write the tile: from the running sum, or straight from buffer 0 for one chunk
+    if (ok && nc > 0) {
+      // write this warp's columns: from the running sum, or straight from buffer 0 for one chunk
       const uint32_t src = nkb > 1 ? sum_col : 0u;
       const int64_t row = tm * BM + q * 32 + lane;
       float* crow = C + (pc * M + row) * N2;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16(tmem + lane_base + src + (uint32_t)c0, v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int64_t col = tn_ * BN + c0;
-        if (row < M) {
+      uint32_t v[MAXC][16];
+#pragma unroll
+      for (int j = 0; j < MAXC; ++j) tmem_ld16(tmem + lane_base + src + (uint32_t)(col0 + 16 * j), v[j]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < MAXC; ++j) {
+          const int64_t col = tn_ * BN + col0 + 16 * j;
           if (col + 16 <= N2) {
             float4* dst = (float4*)(crow + col);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                   __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+            for (int e = 0; e < 4; ++e)
+              dst[e] = make_float4(__uint_as_float(v[j][4 * e]), __uint_as_float(v[j][4 * e + 1]),
+                                   __uint_as_float(v[j][4 * e + 2]), __uint_as_float(v[j][4 * e + 3]));
           } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (col + j < N2) crow[col + j] = __uint_as_float(v[j]);
+            for (int e = 0; e < 16; ++e)
+              if (col + e < N2) crow[col + e] = __uint_as_float(v[j][e]);
           }
         }
       }
@@ -339,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) atomicOr(status, 1u);
-  if (warp == 5) {
+  if (warp == 9) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lay::TMEM_COLS));
   }

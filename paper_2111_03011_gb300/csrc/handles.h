@@ -20,6 +20,8 @@ struct GraphEntry {
 
 struct tn_plan {
   tn::Plan P;
+  double measured_slice_ms = 0.0;
+  int autotune_candidates = 0;
   std::vector<GraphEntry> graphs;     // captured slice ranges (tn_contract_slices_graph)
   cudaStream_t cap_stream = nullptr;
   bool on_device = false;

@@ -9,6 +9,7 @@
 #include <random>
 #include <set>
 #include <sstream>
+#include <thread>
 
 #include "tn_gb300.h"
 
@@ -325,17 +326,117 @@ static int shared_count(const std::vector<int>& a, const std::vector<int>& b) {
   return s;
 }
 
-// Rough execution-time model of a pairwise contraction (seconds), used only to
-// pick among greedy restarts.
+// Execution-time model of a pairwise contraction (seconds), calibrated on the
+// GB300 kernels (streaming steps ~5 TB/s; tensor-core GEMM ~200 TFLOP/s
+// algorithmic; split permute 24 B/element at ~4 TB/s; B prep 40 B/element;
+// ~4 us per launch).  Used only to pick among greedy restarts.
 static double step_time_model(double lA, double lB, double lC, int nk, int nn_small, bool tc) {
-  const double bw = 6.5e12;
   double A = std::exp2(lA), B = std::exp2(lB), C = std::exp2(lC);
-  double macs = C * std::exp2(nk);
-  double bytes = 8.0 * (A + B + C);
-  bool small = nk <= 4 && nn_small <= 4;
-  double peak = small ? 40e12 : (tc ? 250e12 : 40e12);
-  if (!small) bytes += 16.0 * std::max(A, B);  // permute of the big operand
-  return std::max(bytes / bw, 8.0 * macs / peak) + 3e-6;
+  const double big = std::max(A, B), sml = std::min(A, B);
+  const double macs = C * std::exp2(nk);
+  const bool small = nk <= 4 && nn_small <= 4;
+  if (small) return 8.0 * (A + B + C) / 5.0e12 + 4e-6;
+  const double peak = tc ? 200e12 : 40e12;
+  double t = std::max(8.0 * macs / peak, (16.0 * big + 8.0 * C) / 5.5e12);   // GEMM
+  t += 24.0 * big / 4.0e12;                                                     // permute (split)
+  t += 40.0 * sml / 3.0e12;                                                     // B prep
+  return t + 12e-6;
+}
+
+struct TrialResult {
+  bool fits = false;
+  double cost = 1e300, mx = 1e300;
+  std::vector<std::pair<int, int>> order;
+};
+
+// One randomised greedy trial; trial 0 is the plain greedy (alpha 1, no noise).
+static TrialResult greedy_trial(const Plan& plan, PatternBook& book, const std::vector<GNode>& init, double cap,
+                                uint64_t seed, int trial) {
+  std::mt19937_64 rng(seed * 0x9E3779B97F4A7C15ULL + (uint64_t)trial * 0xD1B54A32D192ED03ULL + 1);
+  std::uniform_real_distribution<double> ud(1e-12, 1.0);
+  const double alpha = trial == 0 ? 1.0 : 0.3 + 1.2 * ud(rng);
+  const double tau = trial == 0 ? 0.0 : 0.05 + 0.6 * ud(rng);
+  std::vector<GNode> g = init;
+  TrialResult res;
+  double cost = 0, mx = 0;
+  int alive = 0;
+  for (auto& x : g) {
+    alive += x.alive;
+    mx = std::max(mx, x.lsz);
+  }
+  std::unordered_map<int, std::vector<int>> owners;
+  for (size_t i = 0; i < g.size(); ++i)
+    if (g[i].alive)
+      for (int l : g[i].legs)
+        if (plan.legs[l].kind == LEG_BOND) owners[l].push_back((int)i);
+  while (alive > 1) {
+    std::set<std::pair<int, int>> cand;
+    for (auto& kv : owners)
+      if (kv.second.size() == 2) {
+        int a = std::min(kv.second[0], kv.second[1]), b = std::max(kv.second[0], kv.second[1]);
+        cand.insert({a, b});
+      }
+    int bi = -1, bj = -1;
+    double bs = 1e300;
+    for (auto& pr : cand) {
+      const GNode &A = g[pr.first], &B = g[pr.second];
+      std::vector<int> cl = sym_diff_bond(A.legs, B.legs);
+      double lc = std::log2((double)book.count(A.tq | B.tq)) + (double)cl.size();
+      double score = std::exp2(lc) - alpha * (std::exp2(A.lsz) + std::exp2(B.lsz));
+      // log-domain key keeps the noise scale-free; pairs over the cap go last
+      double key = (score >= 0 ? std::log2(1.0 + score) : -std::log2(1.0 - score));
+      if (tau > 0) key -= tau * std::log(-std::log(ud(rng)));
+      if (lc > cap + 1e-9) key += 1e6 + lc;
+      if (key < bs) { bs = key; bi = pr.first; bj = pr.second; }
+    }
+    if (bi < 0) {
+      // disconnected: outer product of the two smallest
+      std::vector<int> al;
+      for (size_t i = 0; i < g.size(); ++i)
+        if (g[i].alive) al.push_back((int)i);
+      std::sort(al.begin(), al.end(), [&](int a, int b) { return g[a].lsz < g[b].lsz; });
+      bi = std::min(al[0], al[1]);
+      bj = std::max(al[0], al[1]);
+    }
+    GNode &A = g[bi], &B = g[bj];
+    int nk = shared_count(A.legs, B.legs);
+    std::vector<int> cl = sym_diff_bond(A.legs, B.legs);
+    GNode C;
+    C.legs = cl;
+    C.tq = A.tq | B.tq;
+    C.lsz = std::log2((double)book.count(C.tq)) + (double)cl.size();
+    mx = std::max(mx, C.lsz);
+    int nn_small = (int)((A.lsz <= B.lsz ? A.legs.size() : B.legs.size())) - nk;
+    cost += step_time_model(A.lsz, B.lsz, C.lsz, nk, nn_small, plan.gemm_engine != TN_GEMM_SIMT_FP32);
+    for (int l : A.legs)
+      if (plan.legs[l].kind == LEG_BOND) {
+        auto& v = owners[l];
+        v.erase(std::remove(v.begin(), v.end(), bi), v.end());
+        if (v.empty()) owners.erase(l);
+      }
+    for (int l : B.legs)
+      if (plan.legs[l].kind == LEG_BOND) {
+        auto& v = owners[l];
+        v.erase(std::remove(v.begin(), v.end(), bj), v.end());
+        if (v.empty()) owners.erase(l);
+      }
+    for (int l : C.legs)
+      if (plan.legs[l].kind == LEG_BOND) owners[l].push_back(bi);
+    res.order.push_back({bi, bj});
+    g[bi] = C;
+    g[bj].alive = false;
+    --alive;
+  }
+  res.fits = mx <= cap + 1e-9;
+  res.cost = cost;
+  res.mx = mx;
+  return res;
+}
+
+static bool better(const TrialResult& a, const TrialResult& b) {   // is a better than b
+  if (a.fits != b.fits) return a.fits;
+  if (a.fits) return a.cost < b.cost;
+  return a.mx < b.mx || (a.mx == b.mx && a.cost < b.cost);
 }
 
 // Randomised greedy search (restarts).  Each trial repeatedly contracts the
@@ -343,106 +444,44 @@ static double step_time_model(double lA, double lB, double lC, int nk, int nn_sm
 // drawn per trial and Gumbel noise of temperature tau on log-scores after the
 // first trial.  A trial never stops at the cap: it records its largest
 // intermediate, and the best trial is the one under the cap with the lowest
-// modelled time (or, if none fits, the one with the smallest maximum).
+// modelled time (or, if none fits, the one with the smallest maximum).  Trials
+// are seeded independently and spread over the host's cores; the result does
+// not depend on the number of threads (ties go to the lower trial index).
 static int greedy_order(Plan& plan, const std::vector<GNode>& init, double cap, int trials, uint64_t seed,
                         std::vector<std::pair<int, int>>& best_order, std::string& err) {
-  double best_cost = 1e300, best_max = 1e300;
-  bool best_fits = false;
-  std::mt19937_64 rng(seed);
-  std::uniform_real_distribution<double> ud(1e-12, 1.0);
-  for (int trial = 0; trial < std::max(1, trials); ++trial) {
-    const double alpha = trial == 0 ? 1.0 : 0.3 + 1.2 * ud(rng);
-    const double tau = trial == 0 ? 0.0 : 0.05 + 0.6 * ud(rng);
-    std::vector<GNode> g = init;
-    std::vector<std::pair<int, int>> order;
-    double cost = 0, mx = 0;
-    int alive = 0;
-    for (auto& x : g) {
-      alive += x.alive;
-      mx = std::max(mx, x.lsz);
-    }
-    std::unordered_map<int, std::vector<int>> owners;
-    for (size_t i = 0; i < g.size(); ++i)
-      if (g[i].alive)
-        for (int l : g[i].legs)
-          if (plan.legs[l].kind == LEG_BOND) owners[l].push_back((int)i);
-    while (alive > 1) {
-      std::set<std::pair<int, int>> cand;
-      for (auto& kv : owners)
-        if (kv.second.size() == 2) {
-          int a = std::min(kv.second[0], kv.second[1]), b = std::max(kv.second[0], kv.second[1]);
-          cand.insert({a, b});
+  trials = std::max(1, trials);
+  const int nthreads = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), std::min(trials, 32)));
+  // pattern counts of every tail-qubit subset a trial may meet, warmed serially
+  // per thread (PatternBook is not thread-safe): each thread gets its own copy
+  std::vector<TrialResult> best(nthreads);
+  std::vector<int> best_idx(nthreads, -1);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t)
+    pool.emplace_back([&, t] {
+      PatternBook book;
+      book.tails = plan.book.tails;
+      for (int trial = t; trial < trials; trial += nthreads) {
+        TrialResult r = greedy_trial(plan, book, init, cap, seed, trial);
+        if (best_idx[t] < 0 || better(r, best[t])) {
+          best[t] = std::move(r);
+          best_idx[t] = trial;
         }
-      int bi = -1, bj = -1;
-      double bs = 1e300;
-      for (auto& pr : cand) {
-        const GNode &A = g[pr.first], &B = g[pr.second];
-        std::vector<int> cl = sym_diff_bond(A.legs, B.legs);
-        double lc = std::log2((double)plan.book.count(A.tq | B.tq)) + (double)cl.size();
-        // prefer pairs under the cap; among those the greedy score
-        double score = std::exp2(lc) - alpha * (std::exp2(A.lsz) + std::exp2(B.lsz));
-        // log-domain key keeps the noise scale-free
-        double key = (score >= 0 ? std::log2(1.0 + score) : -std::log2(1.0 - score));
-        if (tau > 0) key -= tau * std::log(-std::log(ud(rng)));
-        if (lc > cap + 1e-9) key += 1e6 + lc;
-        if (key < bs) { bs = key; bi = pr.first; bj = pr.second; }
       }
-      if (bi < 0) {
-        // disconnected: outer product of the two smallest
-        std::vector<int> al;
-        for (size_t i = 0; i < g.size(); ++i)
-          if (g[i].alive) al.push_back((int)i);
-        std::sort(al.begin(), al.end(), [&](int a, int b) { return g[a].lsz < g[b].lsz; });
-        bi = std::min(al[0], al[1]);
-        bj = std::max(al[0], al[1]);
-      }
-      GNode &A = g[bi], &B = g[bj];
-      int nk = shared_count(A.legs, B.legs);
-      std::vector<int> cl = sym_diff_bond(A.legs, B.legs);
-      GNode C;
-      C.legs = cl;
-      C.tq = A.tq | B.tq;
-      C.lsz = std::log2((double)plan.book.count(C.tq)) + (double)cl.size();
-      mx = std::max(mx, C.lsz);
-      int nn_small = (int)((A.lsz <= B.lsz ? A.legs.size() : B.legs.size())) - nk;
-      cost += step_time_model(A.lsz, B.lsz, C.lsz, nk, nn_small, plan.gemm_engine != TN_GEMM_SIMT_FP32);
-      // update owners: legs of B move to slot bi, shared legs vanish
-      for (int l : A.legs)
-        if (plan.legs[l].kind == LEG_BOND) {
-          auto& v = owners[l];
-          v.erase(std::remove(v.begin(), v.end(), bi), v.end());
-          if (v.empty()) owners.erase(l);
-        }
-      for (int l : B.legs)
-        if (plan.legs[l].kind == LEG_BOND) {
-          auto& v = owners[l];
-          v.erase(std::remove(v.begin(), v.end(), bj), v.end());
-          if (v.empty()) owners.erase(l);
-        }
-      for (int l : C.legs)
-        if (plan.legs[l].kind == LEG_BOND) owners[l].push_back(bi);
-      order.push_back({bi, bj});
-      g[bi] = C;
-      g[bj].alive = false;
-      --alive;
-    }
-    const bool fits = mx <= cap + 1e-9;
-    bool better;
-    if (fits != best_fits) better = fits;
-    else if (fits) better = cost < best_cost;
-    else better = mx < best_max || (mx == best_max && cost < best_cost);
-    if (better || best_order.empty()) {
-      best_fits = fits;
-      best_cost = cost;
-      best_max = mx;
-      best_order = order;
-    }
+    });
+  for (auto& th : pool) th.join();
+  int bt = -1;
+  for (int t = 0; t < nthreads; ++t) {
+    if (best_idx[t] < 0) continue;
+    if (bt < 0 || better(best[t], best[bt]) ||
+        (!better(best[bt], best[t]) && best_idx[t] < best_idx[bt]))
+      bt = t;
   }
-  if (!best_fits) {
+  if (bt < 0 || !best[bt].fits) {
     err = "no contraction order found keeps every intermediate under the size cap (best 2^" +
-          std::to_string(best_max) + " elements); slice more edges or raise the cap";
+          std::to_string(bt < 0 ? 0.0 : best[bt].mx) + " elements); slice more edges or raise the cap";
     return TN_ERR_OOM;
   }
+  best_order = best[bt].order;
   return TN_OK;
 }
 

@@ -245,7 +245,8 @@ def test_sliced30_full_size_properties(tn):
     2^-n), the partial sums track the kept fraction, and amplitudes are
     consistent between the tensor-core and CUDA-core engines."""
     cfg = ci.config_sliced30()
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], order_trials=512)
+    plan = tn.tn_plan_autotune(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], n_candidates=4,
+                               order_trials=2048)
     head = tn.tn_head_create(plan)
     tn.tn_contract_slices(plan, 0, 16, head)
     N16 = tn.tn_head_norm(head)
@@ -269,7 +270,10 @@ def test_sliced30_full_size_sampled_groups_vs_oracle(tn, gemm):
     kernels): one slice contracted for all 64 groups; two sampled groups
     checked element by element against the O2 network oracle."""
     cfg = ci.config_sliced30()
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], order_trials=512, gemm=gemm)
+    # the plan bench.py times: the autotuner over 4 candidates of 2048 restarts
+    plan = tn.tn_plan_autotune(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], n_candidates=4,
+                               order_trials=2048, gemm=gemm)
+    assert tn.tn_plan_get_stats(plan)["autotune_candidates"] >= 1
     head = tn.tn_head_create(plan)
     s = 5
     tn.tn_contract_slices(plan, s, s + 1, head)
@@ -491,3 +495,16 @@ def test_server_results_same_alone_and_in_the_mix(tn):
         for q, a, b in zip(reqs, got, expect):
             assert np.array_equal(a, b), (mode, q["kind"])
         tn.tn_server_free(sv)
+
+
+def test_autotuned_plan_parity(tn):
+    """The autotuner times distinct candidate orders and keeps the fastest;
+    whatever it keeps computes the same amplitudes."""
+    cfg = ci.config_small(4, 5, 10, seed=13, n_open=8, L=24, n_cut_gates=2)
+    plan = tn.tn_plan_autotune(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], n_candidates=3,
+                               order_trials=16)
+    st = tn.tn_plan_get_stats(plan)
+    assert 1 <= st["autotune_candidates"] <= 3 and st["measured_slice_ms"] > 0
+    head = tn.tn_head_create(plan)
+    tn.tn_contract_slices(plan, 0, 1 << st["n_sliced"], head)
+    assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg))
