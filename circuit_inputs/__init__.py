@@ -134,6 +134,53 @@ def make_grid_circuit(rows: int, cols: int, cycles: int, seed: int,
     return Circuit(n, gates, rows, cols, cycles, seed, first)
 
 
+def sycamore_couplers(rows: int = 9, cols: int = 6, removed=((8, 5),)):
+    """Couplers of a Sycamore-like staggered diagonal lattice: sites (r, c),
+    minus `removed`; site (r, c) couples down-right to (r+1, c + (r % 2)) and
+    down-left to (r+1, c - 1 + (r % 2)).  Pattern A = down-right from even
+    rows, B = down-right from odd rows, C = down-left from even rows,
+    D = down-left from odd rows (each pattern is a matching).  Returns
+    (number of qubits, qubit index of each site, {pattern: [(a, b), ...]})."""
+    sites = [(r, c) for r in range(rows) for c in range(cols) if (r, c) not in set(removed)]
+    index = {rc: i for i, rc in enumerate(sites)}
+    pats = {"A": [], "B": [], "C": [], "D": []}
+    for (r, c) in sites:
+        for kind, dc in (("R", r % 2), ("L", -1 + r % 2)):
+            nb = (r + 1, c + dc)
+            if nb in index:
+                key = {("R", 0): "A", ("R", 1): "B", ("L", 0): "C", ("L", 1): "D"}[(kind, r % 2)]
+                pats[key].append((index[(r, c)], index[nb]))
+    return len(sites), index, pats
+
+
+def make_sycamore_circuit(cycles: int, seed: int, sequence: str = PATTERN_ABCD) -> Circuit:
+    """Seeded 53-qubit Sycamore-topology circuit: the grid circuit's gate
+    distribution on the staggered lattice of `sycamore_couplers`."""
+    rng = np.random.default_rng(seed)
+    n, _, pats = sycamore_couplers()
+    params = {}
+    for p in pats.values():
+        for cp in p:
+            params[cp] = (math.pi / 2 + rng.uniform(-0.11, 0.11), math.pi / 6 + rng.uniform(-0.05, 0.05))
+    gates, prev, names, first = [], [None] * n, ["sx", "sy", "sw"], []
+
+    def single_layer():
+        for q in range(n):
+            choices = [k for k in names if k != prev[q]]
+            k = choices[rng.integers(len(choices))]
+            prev[q] = k
+            gates.append(Gate(1, q, -1, SQRT_GATES[k].copy(), kind=k))
+
+    for t in range(cycles):
+        single_layer()
+        first.append(len(gates))
+        for (a, b) in pats[sequence[t % len(sequence)]]:
+            th, ph = params[(a, b)]
+            gates.append(Gate(2, a, b, fsim(th, ph), kind="fsim", theta=th, phi=ph))
+    single_layer()
+    return Circuit(n, gates, 9, 6, cycles, seed, first)
+
+
 def make_random_2q_circuit(n: int, depth: int, seed: int) -> Circuit:
     """Circuit of random (Haar-ish) 1q and generic 2q unitaries on random qubit
     pairs, both orientations; exercises conventions the symmetric fSim cannot."""
