@@ -16,10 +16,10 @@
 // nearest, so a long K loop accumulated in place drifts (the error grows
 // linearly with K; see Ootomo and Yokota, "Recovering single precision
 // accuracy from Tensor Cores while surpassing the FP32 theoretical peak
-// performance", 2022).  The K loop is therefore cut into chunks of one k-block
-// (32 reduction terms): each accumulates in a fresh TMEM buffer (two,
-// ping-pong) and eight drain warps fold it into a TMEM running sum with
-// ordinary FP32 adds.
+// performance", 2022).  The K loop is therefore cut into chunks -- one k-block
+// (two ping-pong TMEM buffers) for BN <= 128, two k-blocks (one buffer) for
+// BN = 256 -- each accumulated from zero in TMEM and folded by eight drain
+// warps into a TMEM running sum with ordinary FP32 adds.
 //
 // Roles (320 threads): warps 0-7 drain chunk accumulators into the running sum
 // and write the tile out (two warps per TMEM lane quarter, half the columns
@@ -158,7 +158,12 @@ struct Layout {
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // A hi, A lo, B hi, B lo
   static constexpr int DATA = STAGES * STAGE;
   static constexpr int TOTAL = DATA + 1024 /*align*/ + 256 /*barriers*/;
-  static constexpr uint32_t TMEM_COLS = 512;           // two chunk buffers + the running sum (BN <= 128)
+  static constexpr uint32_t TMEM_COLS = 512;
+  // BN <= 128: two chunk buffers (ping-pong) + the running sum; BN = 256: one
+  // chunk buffer + the running sum, chunks of two k-blocks
+  static constexpr bool PINGPONG = BN <= 128;
+  static constexpr int CH = PINGPONG ? 1 : 2;
+  static constexpr uint32_t SUM_COL = PINGPONG ? 2 * BN : BN;
 };
 
 // Tile order: groups of GROUP_M m-tiles; inside a group n-tiles and (when A is
@@ -252,9 +257,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       const uint32_t idesc = idesc_mma<BN, BF16>();
       for (int kb = 0; kb < nkb; ++kb) {
-        // one k-block per TMEM chunk: buffer b alternates
-        const int s = kb % STAGES, r = kb / STAGES, b = kb & 1;
-        if (!mbar_wait(&acce[b], (uint32_t)(((kb >> 1) & 1) ^ 1), abort_flag)) break;
+        // chunk c (CH k-blocks) accumulates in TMEM buffer b from zero
+        const int s = kb % STAGES, r = kb / STAGES;
+        const int c = kb / Lay::CH;
+        const int b = Lay::PINGPONG ? (c & 1) : 0;
+        const int u = Lay::PINGPONG ? (c >> 1) : c;   // use index of buffer b
+        const bool first = (kb % Lay::CH) == 0;
+        const bool last = (kb % Lay::CH) == Lay::CH - 1 || kb == nkb - 1;
+        if (first && !mbar_wait(&acce[b], (uint32_t)((u & 1) ^ 1), abort_flag)) break;
         if (!mbar_wait(&full[s], (uint32_t)(r & 1), abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t d = tmem + (uint32_t)(b * BN);
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const uint32_t o = kk * 32;  // one MMA's K = 32 bytes of each operand row
-          mma<BF16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, kk > 0 ? 1u : 0u);
+          mma<BF16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
           mma<BF16>(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
         }
 #pragma unroll
@@ -275,69 +285,80 @@ __global__ void __launch_bounds__(kThreads, 1)
           mma<BF16>(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
         }
         mma_commit(&empty[s]);
-        mma_commit(&accf[b]);
+        if (last) mma_commit(&accf[b]);
       }
     }
   } else {
     // drain warps 0-7: TMEM lane quarter = warp % 4, column half = warp / 4.
-    // Each warp issues all of its TMEM loads before one wait.
-    constexpr int MAXC = BN >= 32 ? BN / 32 : 1;   // 16-column pieces per warp
+    // Each warp handles its columns in rounds of up to 4 pieces of 16 columns,
+    // issuing a round's TMEM loads before one wait.
+    constexpr int NPIECE = BN >= 32 ? BN / 32 : 1;   // 16-column pieces per warp
+    constexpr int RP = NPIECE < 4 ? NPIECE : 4;        // pieces per round
     const int q = warp & 3, half = warp >> 2;
-    const int nc = BN >= 32 ? MAXC : (half == 0 ? 1 : 0);
+    const bool active = BN >= 32 || half == 0;
     const int col0 = BN >= 32 ? half * (BN / 2) : 0;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    const uint32_t sum_col = 2u * BN;
+    const uint32_t sum_col = Lay::SUM_COL;
+    const int nch = (nkb + Lay::CH - 1) / Lay::CH;
     bool ok = true;
-    for (int c = 0; c < nkb && ok; ++c) {
-      const int b = c & 1;
-      ok = mbar_wait(&accf[b], (uint32_t)((c >> 1) & 1), abort_flag);
+    for (int c = 0; c < nch && ok; ++c) {
+      const int b = Lay::PINGPONG ? (c & 1) : 0;
+      const int u = Lay::PINGPONG ? (c >> 1) : c;
+      ok = mbar_wait(&accf[b], (uint32_t)(u & 1), abort_flag);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      if (nkb > 1 && nc > 0) {
-        uint32_t v[MAXC][16], w[MAXC][16];
+      if (nch > 1 && active) {
+#pragma unroll 1
+        for (int p0 = 0; p0 < NPIECE; p0 += RP) {
+          uint32_t v[RP][16], w[RP][16];
 #pragma unroll
-        for (int j = 0; j < MAXC; ++j) {
-          tmem_ld16(tmem + lane_base + (uint32_t)(b * BN + col0 + 16 * j), v[j]);
-          if (c > 0) tmem_ld16(tmem + lane_base + sum_col + (uint32_t)(col0 + 16 * j), w[j]);
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < MAXC; ++j) {
-          if (c > 0) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e)
-              v[j][e] = __float_as_uint(__uint_as_float(v[j][e]) + __uint_as_float(w[j][e]));
+          for (int j = 0; j < RP; ++j) {
+            const uint32_t col = (uint32_t)(col0 + 16 * (p0 + j));
+            tmem_ld16(tmem + lane_base + (uint32_t)(b * BN) + col, v[j]);
+            if (c > 0) tmem_ld16(tmem + lane_base + sum_col + col, w[j]);
           }
-          tmem_st16(tmem + lane_base + sum_col + (uint32_t)(col0 + 16 * j), v[j]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < RP; ++j) {
+            if (c > 0) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                v[j][e] = __float_as_uint(__uint_as_float(v[j][e]) + __uint_as_float(w[j][e]));
+            }
+            tmem_st16(tmem + lane_base + sum_col + (uint32_t)(col0 + 16 * (p0 + j)), v[j]);
+          }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       mbar_arrive(&acce[b]);
     }
-    if (ok && nc > 0) {
+    if (ok && active) {
       // write this warp's columns: from the running sum, or straight from buffer 0 for one chunk
-      const uint32_t src = nkb > 1 ? sum_col : 0u;
+      const uint32_t src = nch > 1 ? sum_col : 0u;
       const int64_t row = tm * BM + q * 32 + lane;
       float* crow = C + (pc * M + row) * N2;
-      uint32_t v[MAXC][16];
+#pragma unroll 1
+      for (int p0 = 0; p0 < NPIECE; p0 += RP) {
+        uint32_t v[RP][16];
 #pragma unroll
-      for (int j = 0; j < MAXC; ++j) tmem_ld16(tmem + lane_base + src + (uint32_t)(col0 + 16 * j), v[j]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < M) {
+        for (int j = 0; j < RP; ++j) tmem_ld16(tmem + lane_base + src + (uint32_t)(col0 + 16 * (p0 + j)), v[j]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < M) {
 #pragma unroll
-        for (int j = 0; j < MAXC; ++j) {
-          const int64_t col = tn_ * BN + col0 + 16 * j;
-          if (col + 16 <= N2) {
-            float4* dst = (float4*)(crow + col);
+          for (int j = 0; j < RP; ++j) {
+            const int64_t col = tn_ * BN + col0 + 16 * (p0 + j);
+            if (col + 16 <= N2) {
+              float4* dst = (float4*)(crow + col);
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              dst[e] = make_float4(__uint_as_float(v[j][4 * e]), __uint_as_float(v[j][4 * e + 1]),
-                                   __uint_as_float(v[j][4 * e + 2]), __uint_as_float(v[j][4 * e + 3]));
-          } else {
+              for (int e = 0; e < 4; ++e)
+                dst[e] = make_float4(__uint_as_float(v[j][4 * e]), __uint_as_float(v[j][4 * e + 1]),
+                                     __uint_as_float(v[j][4 * e + 2]), __uint_as_float(v[j][4 * e + 3]));
+            } else {
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (col + e < N2) crow[col + e] = __uint_as_float(v[j][e]);
+              for (int e = 0; e < 16; ++e)
+                if (col + e < N2) crow[col + e] = __uint_as_float(v[j][e]);
+            }
           }
         }
       }
@@ -423,7 +444,8 @@ static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStrea
   if (N2 <= 16) return run<16, 6, BF16>(p, status, s);
   if (N2 <= 32) return run<32, 5, BF16>(p, status, s);
   if (N2 <= 64) return run<64, 4, BF16>(p, status, s);
-  return run<128, 3, BF16>(p, status, s);
+  if (N2 <= 128) return run<128, 3, BF16>(p, status, s);
+  return run<256, 2, BF16>(p, status, s);
 }
 
 }  // namespace tc
@@ -432,9 +454,11 @@ cudaError_t prepare_gemm_tc() {
   // the opt-in shared-memory size, set once per device before any launch (and
   // so before any stream capture)
   cudaError_t e = cudaSuccess;
-  const cudaError_t r[8] = {tc::set_attr<16, 6, false>(), tc::set_attr<32, 5, false>(), tc::set_attr<64, 4, false>(),
-                            tc::set_attr<128, 3, false>(), tc::set_attr<16, 6, true>(), tc::set_attr<32, 5, true>(),
-                            tc::set_attr<64, 4, true>(), tc::set_attr<128, 3, true>()};
+  const cudaError_t r[10] = {tc::set_attr<16, 6, false>(), tc::set_attr<32, 5, false>(),
+                             tc::set_attr<64, 4, false>(),  tc::set_attr<128, 3, false>(),
+                             tc::set_attr<256, 2, false>(), tc::set_attr<16, 6, true>(),
+                             tc::set_attr<32, 5, true>(),   tc::set_attr<64, 4, true>(),
+                             tc::set_attr<128, 3, true>(),  tc::set_attr<256, 2, true>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
   return e;
