@@ -172,7 +172,8 @@ def run_ours(args):
     smp_host = torch.empty(n_samples, dtype=torch.int64).pin_memory()
     head = tn.tn_head_create(plan)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    n_launch = int(st["n_launches"])
+    n_pass = 1 << int(st["n_internal_sliced"])     # passes of the launch list per slice
+    n_launch = int(st["n_launches"]) // n_pass     # launches of one pass
     step_ms_acc = np.zeros(n_launch)
 
     def step(host_io, profile):
@@ -220,7 +221,7 @@ def run_ours(args):
     e2e = ws * flops_step / (ms_e2e * 1e-3) / 1e12
     peaks, peak_src = _peaks()
     # dominant launch over the timed steps
-    per_launch = step_ms_acc / args.steps / n_slices      # ms per launch (per slice)
+    per_launch = step_ms_acc / args.steps / (n_slices * n_pass)   # ms per launch
     i_dom = int(np.argmax(per_launch))
     kind, macs, abytes = tn.tn_plan_step_info(plan, i_dom)
     t_dom = per_launch[i_dom] * 1e-3
@@ -289,7 +290,7 @@ def run_ours(args):
         "alg_bytes_per_slice": st["alg_bytes"],
         "e2e": {"value": round(e2e, 3), "unit": "TFLOP/s", "ms_per_step": round(ms_e2e, 3),
                 "h2d_bytes_per_step": int(n_amp * 8), "d2h_bytes_per_step": int(n_amp * 16 + n_samples * 8 + 8)},
-        "gpu_launches": int(args.steps * (n_slices * n_launch + 4)),
+        "gpu_launches": int(args.steps * (n_slices * n_pass * n_launch + 4)),
         "roofline": roof,
         "clocks": clocks,
     }

@@ -93,6 +93,13 @@ typedef struct {
   int    max_host_absorb_log2;/* size cap of host-side absorption of order<=2 tensors (0: 12)*/
   int    small_max_bits;      /* contractions with <= this many contracted and new legs use the
                                  streaming small-operand kernel (0: 4; -1: none, all GEMM steps) */
+  int    auto_slice;          /* 0: off.  Otherwise, when no order fits the cap, slice up to this
+                                 many more wires (at most 24), chosen on the best over-cap order:
+                                 each is the bond carried by the most over-cap intermediates
+                                 (Supplement, slicing: sliced edges are those that cut the largest
+                                 intermediates).  These internal edges take slice bits k, k+1, ...
+                                 and are summed inside every user slice, so slice ids, F_est and
+                                 the head are those of the k user edges, exactly. */
 } tn_plan_opts;
 
 typedef struct tn_plan tn_plan_t;
@@ -115,6 +122,8 @@ typedef struct {
   int     n_gemm_tc, n_gemm_simt, n_small, n_permute;  /* step counts by kernel kind */
   double  measured_slice_ms;  /* tn_plan_autotune: measured time of one slice (0 otherwise) */
   int     autotune_candidates;/* tn_plan_autotune: distinct orders timed */
+  int     n_internal_sliced;  /* edges added by auto_slice; n_launches, tc_macs and alg_bytes count
+                                 all 2^n_internal_sliced passes of one user slice */
 } tn_plan_stats;
 
 /* Plan the contraction (host).  `order`: n_pairs pairs (i, j) of leaf ids, the
@@ -258,15 +267,17 @@ void tn_server_free(tn_server_t* server);   /* drains the queue first */
 int  tn_head_norm(tn_head_t* head, double* norm, double* group_norms, void* stream);
 
 /* Tracing: like tn_contract_slices, but times every launch with CUDA events
- * on `stream` (synchronising after each slice) and returns in step_ms[i] the
- * summed milliseconds of launch i over the range (i < n_launches of
+ * on `stream` (synchronising after each pass) and returns in step_ms[i] the
+ * summed milliseconds of launch i of the per-pass launch list over the range
+ * and every internal pass (i < n_launches >> n_internal_sliced of
  * tn_plan_stats; the last entry is the slice accumulation).  Accumulates
  * into the head like tn_contract_slices. */
 int  tn_profile_slices(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, void* stream,
                        double* step_ms, int64_t n_entries);
 /* Kind (tn step kind: 0 small-operand, 1 permute, 2 B prep (tensor core),
  * 3 tensor-core GEMM, 4 B prep (SIMT), 5 SIMT GEMM, -1 accumulation) and the
- * algorithmic complex multiply-adds and HBM bytes of launch i of one slice. */
+ * algorithmic complex multiply-adds and HBM bytes of launch i of one pass
+ * (a slice runs 2^n_internal_sliced passes). */
 int  tn_plan_step_info(const tn_plan_t* plan, int64_t i, int* kind, double* macs, double* bytes);
 
 /* Largest group count tn_head_norm_noalloc accepts (its fixed scratch: 1 MiB). */

@@ -56,7 +56,7 @@ class tn_range(C.Structure):
 class tn_plan_opts(C.Structure):
     _fields_ = [("max_log2_elements", C.c_double), ("gemm", C.c_int), ("host_only", C.c_int),
                 ("order_trials", C.c_int), ("order_seed", C.c_uint64), ("max_host_absorb_log2", C.c_int),
-                ("small_max_bits", C.c_int)]
+                ("small_max_bits", C.c_int), ("auto_slice", C.c_int)]
 
 
 class tn_server_opts(C.Structure):
@@ -89,7 +89,8 @@ class tn_plan_stats(C.Structure):
                 ("n_launches", C.c_int), ("tc_macs", C.c_double), ("alg_bytes", C.c_double),
                 ("max_log2_elements", C.c_double), ("workspace_bytes", C.c_int64),
                 ("n_gemm_tc", C.c_int), ("n_gemm_simt", C.c_int), ("n_small", C.c_int), ("n_permute", C.c_int),
-                ("measured_slice_ms", C.c_double), ("autotune_candidates", C.c_int)]
+                ("measured_slice_ms", C.c_double), ("autotune_candidates", C.c_int),
+                ("n_internal_sliced", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -229,7 +230,8 @@ class Head:
 
 
 def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements=0.0, gemm=TN_GEMM_AUTO,
-            host_only=False, order_trials=0, order_seed=0, max_host_absorb_log2=0, small_max_bits=0) -> Plan:
+            host_only=False, order_trials=0, order_seed=0, max_host_absorb_log2=0, small_max_bits=0,
+            auto_slice=0) -> Plan:
     gates = gates_to_c(circuit)
     circ = tn_circuit(int(circuit.n_qubits), len(circuit.gates), gates)
     oq = (C.c_int * max(1, len(open_qubits)))(*[int(q) for q in open_qubits])
@@ -240,7 +242,7 @@ def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements
         g, leg, kind, val = (list(e) + [TN_EDGE_SLICE, 0])[:4] if len(e) < 4 else e
         ed[i] = tn_edge(int(g), int(leg), int(kind), int(val))
     opts = tn_plan_opts(float(max_log2_elements), int(gemm), int(bool(host_only)), int(order_trials),
-                        int(order_seed), int(max_host_absorb_log2), int(small_max_bits))
+                        int(order_seed), int(max_host_absorb_log2), int(small_max_bits), int(auto_slice))
     h = C.c_void_p()
     if order is not None:
         o = np.ascontiguousarray(np.asarray(order, dtype=np.int32).reshape(-1))
@@ -253,7 +255,7 @@ def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements
 
 def tn_plan_autotune(circuit, open_qubits, tails, edges=(), n_candidates=4, max_log2_elements=0.0,
                      gemm=TN_GEMM_AUTO, order_trials=0, order_seed=0, max_host_absorb_log2=0, small_max_bits=0,
-                     stream=None) -> Plan:
+                     stream=None, auto_slice=0) -> Plan:
     gates = gates_to_c(circuit)
     circ = tn_circuit(int(circuit.n_qubits), len(circuit.gates), gates)
     oq = (C.c_int * max(1, len(open_qubits)))(*[int(q) for q in open_qubits])
@@ -264,7 +266,7 @@ def tn_plan_autotune(circuit, open_qubits, tails, edges=(), n_candidates=4, max_
         g, leg, kind, val = (list(e) + [TN_EDGE_SLICE, 0])[:4] if len(e) < 4 else e
         ed[i] = tn_edge(int(g), int(leg), int(kind), int(val))
     opts = tn_plan_opts(float(max_log2_elements), int(gemm), 0, int(order_trials), int(order_seed),
-                        int(max_host_absorb_log2), int(small_max_bits))
+                        int(max_host_absorb_log2), int(small_max_bits), int(auto_slice))
     h = C.c_void_p()
     _check(_lib.tn_plan_autotune(C.byref(circ), C.byref(spec), ed, len(edges), C.byref(opts), int(n_candidates),
                                  _stream(stream), C.byref(h)))
@@ -375,8 +377,10 @@ def tn_head_norm(head: Head, with_groups=False, stream=None):
 
 
 def tn_profile_slices(plan: Plan, begin: int, end: int, head: Head, stream=None) -> np.ndarray:
-    """Contract [begin, end) into head, returning summed ms per launch."""
-    n = int(tn_plan_get_stats(plan)["n_launches"])
+    """Contract [begin, end) into head, returning summed ms per launch of one
+    pass (summed over every pass: 2^n_internal_sliced per slice)."""
+    st = tn_plan_get_stats(plan)
+    n = int(st["n_launches"]) >> int(st["n_internal_sliced"])
     ms = np.zeros(n, dtype=np.float64)
     _check(_lib.tn_profile_slices(plan.handle, tn_range(int(begin), int(end)), head.handle, _stream(stream),
                                   ms.ctypes.data_as(C.POINTER(C.c_double)), n))

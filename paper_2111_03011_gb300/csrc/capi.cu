@@ -160,6 +160,8 @@ extern "C" int tn_plan(const tn_circuit* circuit, const tn_open_spec* open_spec,
     if (opts->order_seed) in.order_seed = opts->order_seed;
     if (opts->max_host_absorb_log2 > 0) in.absorb_log2 = opts->max_host_absorb_log2;
     if (opts->small_max_bits != 0) in.small_max_bits = opts->small_max_bits < 0 ? -1 : std::min(4, opts->small_max_bits);
+    if (opts->auto_slice < 0 || opts->auto_slice > 24) return fail(TN_ERR_INVALID, "auto_slice must be in [0, 24]");
+    in.auto_slice = opts->auto_slice;
   }
   if (in.gemm_engine < 0 || in.gemm_engine > 3) return fail(TN_ERR_INVALID, "unknown gemm engine");
   if (in.cap_log2 > 34) return fail(TN_ERR_INVALID, "size cap above 2^34 elements");
@@ -193,9 +195,11 @@ extern "C" int tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* s) {
   s->n_pinned = P.n_pinned;
   s->n_leaves = (int)P.leaves.size();
   s->n_contractions = P.n_contractions;
-  s->n_launches = (int)P.steps.size() + 1;
-  s->tc_macs = P.tc_macs;
-  s->alg_bytes = P.alg_bytes;
+  const double ni = std::ldexp(1.0, P.n_internal);
+  s->n_launches = (int)(((int64_t)P.steps.size() + 1) << P.n_internal);
+  s->tc_macs = P.tc_macs * ni;
+  s->alg_bytes = P.alg_bytes * ni;
+  s->n_internal_sliced = P.n_internal;
   s->max_log2_elements = P.max_log2;
   s->workspace_bytes = P.workspace_bytes;
   s->measured_slice_ms = plan->measured_slice_ms;
@@ -317,7 +321,9 @@ static inline float2* buf_ptr(const tn_plan_t* p, const tn::Ref& r) {
   return (float2*)(p->d_arena + p->P.bufs[r.id].off);
 }
 
-static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEvent_t* ev = nullptr) {
+// One pass of the launch list for the full slice id s (user bits, then the
+// bits of automatically sliced edges).
+static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEvent_t* ev) {
   const tn::Plan& P = p->P;
   int si = 0;
   for (const tn::Step& x : P.steps) {
@@ -419,6 +425,17 @@ static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaE
   return TN_OK;
 }
 
+// User slice s: every value t of the automatically sliced edges, slice id
+// s | t << k, each pass accumulating into H.
+static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st) {
+  const int64_t ni = 1LL << p->P.n_internal;
+  for (int64_t t = 0; t < ni; ++t) {
+    int rc = run_pass(p, s | (t << p->P.n_sliced), H, st, nullptr);
+    if (rc) return rc;
+  }
+  return TN_OK;
+}
+
 static int check_range(tn_plan_t* plan, tn_range r, tn_head_t* head) {
   if (!plan || !head) return fail(TN_ERR_INVALID, "NULL argument");
   if (head->plan != plan) return fail(TN_ERR_INVALID, "head belongs to another plan");
@@ -453,8 +470,10 @@ extern "C" int tn_profile_slices(tn_plan_t* plan, tn_range r, tn_head_t* head, v
   std::vector<cudaEvent_t> ev(2 * ns);
   for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
   int status = TN_OK;
-  for (int64_t s = r.begin; s < r.end && status == TN_OK; ++s) {
-    status = run_slice(plan, s, head->H, st, ev.data());
+  const int64_t ni = 1LL << plan->P.n_internal;
+  for (int64_t q = r.begin * ni; q < r.end * ni && status == TN_OK; ++q) {
+    const int64_t s = (q / ni) | ((q % ni) << plan->P.n_sliced);
+    status = run_pass(plan, s, head->H, st, ev.data());
     if (status) break;
     cudaError_t e = cudaEventSynchronize(ev[2 * ns - 1]);
     if (e != cudaSuccess) { status = fail(TN_ERR_CUDA, cudaGetErrorString(e)); break; }
@@ -773,15 +792,10 @@ extern "C" int tn_plan_autotune(const tn_circuit* circuit, const tn_open_spec* o
     for (auto& s_ : seen) dup |= s_ == hp->P.order;
     if (dup) { tn_plan_free(hp); continue; }
     seen.push_back(hp->P.order);
-    // upload this candidate (same order, now on the device)
-    std::vector<int32_t> pairs;
-    for (auto& pr : hp->P.order) { pairs.push_back(pr.first); pairs.push_back(pr.second); }
-    tn_plan_free(hp);
-    tn_plan_opts dopt = o;
-    dopt.host_only = 0;
-    tn_plan_t* p = nullptr;
-    rc = tn_plan(circuit, open_spec, sliced_edges, n_edges, pairs.data(), (int64_t)pairs.size() / 2, &dopt, &p);
-    if (rc) { last_rc = rc; continue; }
+    // upload this candidate (its edges include any automatically sliced ones)
+    tn_plan_t* p = hp;
+    rc = plan_upload(p);
+    if (rc) { plan_release(p); last_rc = rc; continue; }
     ++distinct;
     tn_head_t* h = nullptr;
     rc = tn_head_create(p, nullptr, &h);

@@ -107,6 +107,8 @@ struct Builder {
   Plan& plan;
   std::vector<HostTensor> T;
   std::vector<int> pin_of_leg;   // -1 or pinned value
+  struct Use { int leg, gate, pos; };
+  std::vector<Use> consumed;     // input wires of gates
 
   explicit Builder(Plan& p) : plan(p) {}
 
@@ -165,6 +167,9 @@ static int build_network(const PlanInput& in, Plan& plan, Builder& b, std::strin
       }
     }
     const cd* U = in.mats + (size_t)gi * 16;
+    // the wire this gate consumes on each input leg (for automatic slicing)
+    b.consumed.push_back({wire[q0], gi, 0});
+    if (ar == 2) b.consumed.push_back({wire[q1], gi, 1});
     HostTensor t;
     if (ar == 1) {
       int out = b.new_leg(LEG_BOND);
@@ -449,6 +454,7 @@ static bool better(const TrialResult& a, const TrialResult& b) {   // is a bette
 // not depend on the number of threads (ties go to the lower trial index).
 static int greedy_order(Plan& plan, const std::vector<GNode>& init, double cap, int trials, uint64_t seed,
                         std::vector<std::pair<int, int>>& best_order, std::string& err) {
+  // on failure best_order still receives the best over-cap order (for slicing)
   trials = std::max(1, trials);
   const int nthreads = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), std::min(trials, 32)));
   // pattern counts of every tail-qubit subset a trial may meet, warmed serially
@@ -479,10 +485,72 @@ static int greedy_order(Plan& plan, const std::vector<GNode>& init, double cap, 
   if (bt < 0 || !best[bt].fits) {
     err = "no contraction order found keeps every intermediate under the size cap (best 2^" +
           std::to_string(bt < 0 ? 0.0 : best[bt].mx) + " elements); slice more edges or raise the cap";
+    if (bt >= 0) best_order = best[bt].order;
     return TN_ERR_OOM;
   }
   best_order = best[bt].order;
   return TN_OK;
+}
+
+// Automatic slicing: replay `order`, then pick bond legs one at a time -- the
+// leg carried by the most over-cap intermediates (ties: the larger summed
+// excess) -- until every intermediate fits the cap.  Only legs that are the
+// input wire of a gate (so that they can be written as a cut edge) qualify.
+static bool choose_slice_legs(const Plan& plan, PatternBook& book, const std::vector<GNode>& init,
+                              const std::vector<std::pair<int, int>>& order, double cap, int max_extra,
+                              std::vector<int>& legs_out, std::string& why) {
+  std::vector<GNode> g = init;
+  std::vector<GNode> inter;
+  for (auto& x : g) inter.push_back(x);
+  for (auto& pr : order) {
+    GNode C;
+    C.legs = sym_diff_bond(g[pr.first].legs, g[pr.second].legs);
+    C.tq = g[pr.first].tq | g[pr.second].tq;
+    C.lsz = std::log2((double)book.count(C.tq)) + (double)C.legs.size();
+    g[pr.first] = C;
+    g[pr.second].alive = false;
+    inter.push_back(C);
+  }
+  std::set<int> sliced;
+  while (true) {
+    std::map<int, std::pair<int, double>> score;   // leg -> (count, excess)
+    bool over = false;
+    for (auto& T : inter) {
+      int removed = 0;
+      for (int l : T.legs) removed += sliced.count(l) ? 1 : 0;
+      const double ex = T.lsz - removed - cap;
+      if (ex <= 1e-9) continue;
+      over = true;
+      int avail = 0;
+      for (int l : T.legs) {
+        if (sliced.count(l) || plan.legs[l].kind != LEG_BOND) continue;
+        if (l >= (int)plan.leg_edge.size() || plan.leg_edge[l].first < 0) continue;
+        auto& sc = score[l];
+        sc.first += 1;
+        sc.second += ex;
+        ++avail;
+      }
+      if (ex > avail + 1e-9) {
+        why = "open legs and tail patterns alone exceed the cap";
+        return false;
+      }
+    }
+    if (!over) break;
+    if ((int)sliced.size() >= max_extra || score.empty()) {
+      why = "more than " + std::to_string(max_extra) + " extra edges needed";
+      return false;
+    }
+    int best = -1;
+    std::pair<int, double> bs{-1, -1.0};
+    for (auto& kv : score)
+      if (kv.second.first > bs.first || (kv.second.first == bs.first && kv.second.second > bs.second)) {
+        bs = kv.second;
+        best = kv.first;
+      }
+    sliced.insert(best);
+  }
+  legs_out.assign(sliced.begin(), sliced.end());
+  return true;
 }
 
 // ---------------------------------------------------------------- step layout
@@ -836,7 +904,11 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
     } else { err = "edge: unknown kind"; return TN_ERR_INVALID; }
   }
   if (k > 40) { err = "at most 40 sliced edges"; return TN_ERR_INVALID; }
-  plan.n_sliced = k;
+  plan.n_sliced = k - in.n_internal;
+  plan.n_internal = in.n_internal;
+  plan.internal_edges.clear();
+  for (size_t e = in.edges.size() - in.n_internal; e < in.edges.size(); ++e)
+    plan.internal_edges.push_back({in.edges[e].gate, in.edges[e].leg});
   plan.n_pinned = pins;
   plan.n_companion = companions;
   plan.companion_factor = comp_factor;
@@ -844,6 +916,9 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
   Builder b(plan);
   int rc = build_network(in, plan, b, err);
   if (rc) return rc;
+  plan.leg_edge.assign(plan.legs.size(), {-1, -1});
+  for (auto& u : b.consumed)
+    if (plan.legs[u.leg].kind == LEG_BOND) plan.leg_edge[u.leg] = {u.gate, u.pos};
   simplify(plan, b.T, in.absorb_log2);
 
   // leaves
@@ -909,6 +984,29 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
       init[i].lsz = std::log2((double)plan.vts[i].P) + (double)plan.vts[i].legs.size();
     }
     rc = greedy_order(plan, init, plan.cap_log2, in.order_trials, in.order_seed, slot_order, err);
+    if (rc == TN_ERR_OOM && in.auto_slice > 0 && !slot_order.empty()) {
+      // slice the wires chosen on the best over-cap order: they become
+      // trailing SLICE edges whose slice bits are summed inside every slice
+      std::vector<int> legs;
+      std::string why;
+      if (!choose_slice_legs(plan, plan.book, init, slot_order, plan.cap_log2, in.auto_slice, legs, why)) {
+        err += " (automatic slicing: " + why + ")";
+        return TN_ERR_OOM;
+      }
+      // Cutting a wire can let host simplification absorb more tensors, so the
+      // order is searched again on the sliced network; what still does not fit
+      // is sliced further from the remaining budget.
+      PlanInput in2 = in;
+      for (int l : legs) in2.edges.push_back({plan.leg_edge[l].first, plan.leg_edge[l].second, TN_EDGE_SLICE, 0});
+      in2.auto_slice = in.auto_slice - (int)legs.size();
+      in2.n_internal = in.n_internal + (int)legs.size();
+      Plan fresh;
+      err.clear();
+      rc = build_plan(in2, fresh, err);
+      if (rc) return rc;
+      plan = std::move(fresh);
+      return TN_OK;
+    }
     if (rc) return rc;
   }
   // translate slot pairs to virtual-tensor pairs
@@ -961,6 +1059,10 @@ std::string describe_plan(const Plan& plan, bool with_data) {
   std::ostringstream o;
   o.precision(17);
   o << "{\"n_qubits\":" << plan.n_qubits << ",\"n_sliced\":" << plan.n_sliced << ",\"n_pinned\":" << plan.n_pinned;
+  o << ",\"n_internal\":" << plan.n_internal << ",\"internal_edges\":[";
+  for (size_t e = 0; e < plan.internal_edges.size(); ++e)
+    o << (e ? "," : "") << "[" << plan.internal_edges[e].first << "," << plan.internal_edges[e].second << "]";
+  o << "]";
   o << ",\"tail_mask\":" << plan.tail_mask << ",\"open_mask\":" << plan.open_mask;
   o << ",\"legs\":[";
   for (size_t l = 0; l < plan.legs.size(); ++l) {

@@ -123,6 +123,9 @@ struct Plan {
   std::vector<uint64_t> tails_raw;
   uint64_t open_mask = 0, tail_mask = 0;
   int n_sliced = 0, n_pinned = 0, n_companion = 0;
+  int n_internal = 0;              // slice bits added by automatic slicing (summed inside every slice)
+  std::vector<std::pair<int, int>> leg_edge;   // bond leg -> (gate, input leg) that consumes it
+  std::vector<std::pair<int, int>> internal_edges;   // (gate, leg) of the SLICE edges automatic slicing added
   double companion_factor = 1.0;   // product of the companion cuts' kept norm fractions
   double cap_log2 = 28;
   int gemm_engine = 0;
@@ -169,6 +172,8 @@ struct PlanInput {
   uint64_t order_seed = 1;
   int absorb_log2 = 12;
   int small_max_bits = 4;
+  int auto_slice = 0;       // at most this many extra sliced edges when no order fits the cap
+  int n_internal = 0;       // trailing SLICE edges that automatic slicing added
 };
 
 int build_plan(const PlanInput& in, Plan& plan, std::string& err);

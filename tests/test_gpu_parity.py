@@ -508,3 +508,28 @@ def test_autotuned_plan_parity(tn):
     head = tn.tn_head_create(plan)
     tn.tn_contract_slices(plan, 0, 1 << st["n_sliced"], head)
     assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg))
+
+
+@pytest.mark.parametrize("gemm", [0, 3], ids=["tc", "bf16"])
+def test_automatic_slicing_parity_f_est_profile_and_graph(tn, gemm):
+    """A cap that no order meets: the planner slices extra wires, runs every
+    internal value inside each user slice, and the head, F_est, the profile
+    and the graph replay are those of the user's slicing."""
+    cfg = ci.config_small(4, 5, 10, seed=13, n_open=8, L=24, n_cut_gates=1)
+    tol = REL_L2_BF16 if gemm == 3 else REL_L2
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=gemm,
+                      max_log2_elements=15, auto_slice=16)
+    st = tn.tn_plan_get_stats(plan)
+    assert st["n_sliced"] == 2 and st["n_internal_sliced"] >= 1 and st["max_log2_elements"] <= 15 + 1e-9
+    head = tn.tn_head_create(plan)
+    tn.tn_contract_slices(plan, 1, 3, head)
+    assert tn.tn_head_fidelity(head) == (0.5, 2)
+    assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg, slice_range=(1, 3)), tol)
+    tn.tn_contract_slices(plan, 0, 1, head)
+    tn.tn_contract_slices_graph(plan, 3, 4, head)
+    assert tn.tn_head_fidelity(head) == (1.0, 4)
+    assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg), tol)
+    h2 = tn.tn_head_create(plan)
+    ms = tn.tn_profile_slices(plan, 0, 4, h2)
+    assert ms.shape == (st["n_launches"] >> st["n_internal_sliced"],) and (ms > 0).all()
+    assert_close(read_head(tn, plan, h2, cfg), oracle_head(cfg), tol)

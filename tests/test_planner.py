@@ -179,3 +179,68 @@ def test_companion_cuts_replay_and_fidelity_estimate(tn):
     # checked on the GPU; here the formula itself
     f = O.companion_factor(c.gates[g0].theta) * O.companion_factor(c.gates[g1].theta)
     assert 0.9 < f <= 1.0
+
+
+def _auto_cfg():
+    return ci.config_small(4, 5, 10, seed=13, n_open=8, L=24, n_cut_gates=1)
+
+
+def test_automatic_slicing_is_exact_per_user_slice(tn):
+    """With a cap no order meets, the planner slices extra wires (Supplement,
+    slicing and contraction order: the sliced edges are those that cut the
+    largest intermediates) and sums them inside every user slice, so user
+    slice s replays to the oracle's slice s."""
+    cfg = _auto_cfg()
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True,
+                   max_log2_elements=13)
+    assert e.value.code == tn.TN_ERR_OOM
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True,
+                      max_log2_elements=13, auto_slice=16)
+    st = tn.tn_plan_get_stats(plan)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    k, ni = st["n_sliced"], st["n_internal_sliced"]
+    assert k == 2 and ni >= 1 and d["n_internal"] == ni and len(d["internal_edges"]) == ni
+    assert st["max_log2_elements"] <= 13 + 1e-9
+    # the extra edges are wires of the circuit: (gate, input leg)
+    for g, leg in d["internal_edges"]:
+        assert 0 <= g < len(cfg["circuit"].gates) and leg in (0, 1)
+        assert leg < cfg["circuit"].gates[g].arity
+    for s in (1, 2):
+        H = emulate(d, cfg["tails"], cfg["open_qubits"], [s | (t << k) for t in range(1 << ni)])
+        ref = _oracle_H(cfg, slice_range=(s, s + 1))
+        assert np.abs(H - ref).max() < 1e-12
+    # the internal slices alone are the oracle with those wires cut as well
+    se = [(g, l) for (g, l, kk, v) in cfg["edges"]] + [tuple(x) for x in d["internal_edges"]]
+    sub = 5 << k
+    H = emulate(d, cfg["tails"], cfg["open_qubits"], [sub])
+    ref = O.sparse_state_from_vector(O.sliced_statevector(cfg["circuit"], se, slice_range=(sub, sub + 1)),
+                                     cfg["open_qubits"], cfg["tails"])
+    assert np.abs(H - ref).max() < 1e-12
+
+
+def test_automatic_slicing_counts_and_limits(tn):
+    cfg = _auto_cfg()
+    base = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True,
+                      max_log2_elements=13, auto_slice=16)
+    st = tn.tn_plan_get_stats(base)
+    ni = st["n_internal_sliced"]
+    # per-user-slice figures count every internal pass
+    assert st["n_launches"] % (1 << ni) == 0
+    # a budget below what the cap needs is an error, not a silent over-cap plan
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True,
+                   max_log2_elements=13, auto_slice=1 if ni > 1 else 0)
+    assert e.value.code == tn.TN_ERR_OOM
+    # open legs cannot be sliced: 16 open qubits never fit 2^10
+    big = ci.config_small(4, 4, 8, seed=11, n_open=16, L=1, n_cut_gates=0)
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(big["circuit"], big["open_qubits"], big["tails"], host_only=True, max_log2_elements=10,
+                   auto_slice=20)
+    assert e.value.code == tn.TN_ERR_OOM
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True, auto_slice=25)
+    assert e.value.code == tn.TN_ERR_INVALID
+    # without need, automatic slicing adds nothing
+    p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True, auto_slice=8)
+    assert tn.tn_plan_get_stats(p)["n_internal_sliced"] == 0
