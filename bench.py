@@ -136,7 +136,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     cfg = _workload(args.workload)
-    gemm = {"tc": tn.TN_GEMM_TC_3XTF32, "simt": tn.TN_GEMM_SIMT_FP32, "bf16": tn.TN_GEMM_TC_BF16X3}[args.engine]
+    gemm = {"tc": tn.TN_GEMM_TC_3XTF32, "simt": tn.TN_GEMM_SIMT_FP32, "bf16": tn.TN_GEMM_TC_BF16X3,
+            "fp16": tn.TN_GEMM_TC_FP16X3}[args.engine]
     t0 = time.time()
     if args.autotune > 0:
         plan = tn.tn_plan_autotune(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"],
@@ -229,17 +230,18 @@ def run_ours(args):
     for i in range(n_launch):
         kk, _, _ = tn.tn_plan_step_info(plan, i)
         name = KIND_NAMES[kk]
-        if args.engine == "bf16":
-            name = name.replace("gemm_tc_3xtf32", "gemm_tc_bf16x3")
+        if args.engine in ("bf16", "fp16"):
+            name = name.replace("gemm_tc_3xtf32", f"gemm_tc_{args.engine}x3")
         kind_totals[name] = kind_totals.get(name, 0.0) + per_launch[i]
     tot = sum(kind_totals.values())
-    if kind in (3,) and args.engine == "bf16":
+    if kind in (3,) and args.engine in ("bf16", "fp16"):
         peak = peaks["bf16_tflops_sustained"] / 3.0
         achieved = 8.0 * macs / t_dom / 1e12
         roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "gemm_tc_bf16x3",
-                "peak_note": f"{peak_src} sustained bf16 / 3 (BF16x3 issues 3 MMAs per product)"}
+                "kernel": f"gemm_tc_{args.engine}x3",
+                "peak_note": f"{peak_src} sustained bf16 / 3 (kind::f16 runs bf16 and fp16 at one rate; "
+                             f"the split issues 3 MMAs per product)"}
     elif kind in (3,):
         tf32 = peaks["bf16_tflops_sustained"] * (1.1 / 2.25)
         peak = tf32 / 3.0
@@ -274,7 +276,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c64" if args.engine != "bf16" else "c64 (bf16x3 GEMM steps)",
+        "dtype": {"bf16": "c64 (bf16x3 GEMM steps)", "fp16": "c64 (fp16x3 GEMM steps)"}.get(args.engine, "c64"),
         "data": "synthetic (seeded Sycamore-like circuit; paper's circuit files not used)",
         "config": {"workload": cfg["name"], "qubits": st["n_qubits"], "cycles": cfg["circuit"].cycles,
                    "open_qubits": h, "groups": L, "amplitudes": n_amp, "sliced_edges": k, "slices": n_slices,
@@ -436,7 +438,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sliced30", choices=["sliced30", "tiny", "grid25", "serve"])
-    ap.add_argument("--engine", default="tc", choices=["tc", "simt", "bf16"])
+    ap.add_argument("--engine", default="tc", choices=["tc", "simt", "bf16", "fp16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", type=int, default=4,
                     help="plan candidates timed on the GPU by tn_plan_autotune (0: plain tn_plan)")

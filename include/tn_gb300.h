@@ -56,7 +56,7 @@ enum { TN_C64 = 0, TN_C128 = 1 };
  * FP32 (the plain complex64 reference engine).  TC_BF16X3: tcgen05 kind::f16,
  * bf16 hi/lo split with FP32 accumulation, relative L2 <= 1e-4 (a precision
  * form with twice the tensor rate). */
-enum { TN_GEMM_AUTO = 0, TN_GEMM_TC_3XTF32 = 1, TN_GEMM_SIMT_FP32 = 2, TN_GEMM_TC_BF16X3 = 3 };
+enum { TN_GEMM_AUTO = 0, TN_GEMM_TC_3XTF32 = 1, TN_GEMM_SIMT_FP32 = 2, TN_GEMM_TC_BF16X3 = 3, TN_GEMM_TC_FP16X3 = 4 };
 
 /* One gate, in time order.  arity 1: re/im[0..3] hold the 2x2 matrix
  * (row-major, row = output); arity 2: re/im[0..15] hold the 4x4 matrix. */

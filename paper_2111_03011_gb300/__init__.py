@@ -22,7 +22,7 @@ TN_EDGE_SLICE, TN_EDGE_PIN, TN_EDGE_COMPANION = 0, 1, 2
 TN_C64, TN_C128 = 0, 1
 TN_SAMPLE_EXACT, TN_SAMPLE_METROPOLIS, TN_SAMPLE_FRUGAL = 0, 1, 2
 TN_REQ_AMPLITUDES, TN_REQ_SAMPLE = 0, 1
-TN_GEMM_AUTO, TN_GEMM_TC_3XTF32, TN_GEMM_SIMT_FP32, TN_GEMM_TC_BF16X3 = 0, 1, 2, 3
+TN_GEMM_AUTO, TN_GEMM_TC_3XTF32, TN_GEMM_SIMT_FP32, TN_GEMM_TC_BF16X3, TN_GEMM_TC_FP16X3 = 0, 1, 2, 3, 4
 
 
 class TNError(RuntimeError):

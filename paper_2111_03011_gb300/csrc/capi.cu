@@ -163,7 +163,7 @@ extern "C" int tn_plan(const tn_circuit* circuit, const tn_open_spec* open_spec,
     if (opts->auto_slice < 0 || opts->auto_slice > 24) return fail(TN_ERR_INVALID, "auto_slice must be in [0, 24]");
     in.auto_slice = opts->auto_slice;
   }
-  if (in.gemm_engine < 0 || in.gemm_engine > 3) return fail(TN_ERR_INVALID, "unknown gemm engine");
+  if (in.gemm_engine < 0 || in.gemm_engine > 4) return fail(TN_ERR_INVALID, "unknown gemm engine");
   if (in.cap_log2 > 34) return fail(TN_ERR_INVALID, "size cap above 2^34 elements");
   tn_plan_t* p = new tn_plan_t();
   std::string err;
@@ -379,7 +379,7 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         bp.nn = x.nn;
         bp.bk = p->d_meta + x.bk_off;
         bp.bn = p->d_meta + x.bn_off;
-        bp.bf16 = x.bf16;
+        bp.h16 = x.h16;
         e = x.kind == tn::ST_BPREP_C ? tn::launch_bprep_c(bp, st) : tn::launch_bprep_tc(bp, st);
         break;
       }
@@ -399,7 +399,7 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         gp.mapB = p->d_meta + x.mapB_off;
         gp.mapA_mode = x.mapA_mode;
         gp.mapB_mode = x.mapB_mode;
-        gp.bf16 = x.bf16;
+        gp.h16 = x.h16;
         e = x.kind == tn::ST_GEMM_SIMT ? tn::launch_gemm_simt(gp, st) : tn::launch_gemm_tc(gp, p->d_status, st);
         break;
       }

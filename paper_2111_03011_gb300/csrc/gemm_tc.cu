@@ -6,9 +6,12 @@
 //     Bt = the real embedding of B, [2N][2K] K-major (built by k_bprep_tc).
 // FP32 accuracy from TF32 tensor cores by the 3xTF32 split
 //     A_r Bt ~ A_hi B_hi + A_hi B_lo + A_lo B_hi,
-// hi = round-to-tf32, lo = x - hi (or, in the BF16 engine, the same three
-// products of bf16 hi/lo parts on kind::f16: ~2^-16 relative per product, at
-// twice the tensor rate).  Both operands arrive pre-split in global
+// hi = round-to-tf32, lo = x - hi.  The BF16 engine takes the same three
+// products of bf16 hi/lo parts on kind::f16 (~2^-16 relative per product, at
+// twice the tensor rate); the FP16 engine takes them of fp16 hi/lo parts of
+// the operands scaled by 2^15 (fp16 and tf32 both carry 11 significant bits,
+// so it keeps the 3xTF32 accuracy at the kind::f16 rate; the scale, exact,
+// is undone in the epilogue).  Both operands arrive pre-split in global
 // memory (A by the split-mode permute, B by k_bprep_tc), so the kernel is a
 // plain TMA -> MMA pipeline.
 //
@@ -100,18 +103,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor: D f32, A/B tf32 (format 2) or bf16 (format 1), both
-// K-major, M = 128, N = BN.
-template <int BN, bool BF16>
+// Instruction descriptor: D f32, A/B tf32 (format 2), bf16 (format 1) or fp16
+// (format 0), both K-major, M = 128, N = BN.  FMT: 0 tf32, 1 bf16, 2 fp16.
+template <int BN, int FMT>
 __device__ __forceinline__ uint32_t idesc_mma() {
-  const uint32_t f = BF16 ? 1u : 2u;
+  const uint32_t f = FMT == 0 ? 2u : (FMT == 1 ? 1u : 0u);
   return (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-// One MMA: K = 8 (tf32) or 16 (bf16), i.e. 32 bytes of each operand row.
-template <bool BF16>
+// One MMA: K = 8 (tf32) or 16 (bf16, fp16), i.e. 32 bytes of each operand row.
+template <bool H16>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (BF16)
+  if (H16)
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -191,7 +194,7 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t tilesM, int64_t t
   pc = a_shared ? pin : outer;
 }
 
-template <int BN, int STAGES, bool BF16>
+template <int BN, int STAGES, int FMT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
               const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
@@ -214,7 +217,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   tile_coords(blockIdx.x, tilesM, tilesN, PC, mapA_mode == 1 && PC > 1, pc, tm, tn_);
   const int64_t pa = mapA_mode == 0 ? pc : (mapA_mode == 1 ? 0 : (int64_t)mapA[pc]);
   const int64_t pb = mapB_mode == 0 ? pc : (mapB_mode == 1 ? 0 : (int64_t)mapB[pc]);
-  constexpr int BKE = BF16 ? 64 : 32;     // K elements per k-block
+  constexpr bool H16 = FMT != 0;
+  constexpr int BKE = H16 ? 64 : 32;      // K elements per k-block
   const int nkb = (int)((K2 + BKE - 1) / BKE);
 
   if (threadIdx.x == 0) {
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 9) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_mma<BN, BF16>();
+      const uint32_t idesc = idesc_mma<BN, FMT>();
       for (int kb = 0; kb < nkb; ++kb) {
         // chunk c (CH k-blocks) accumulates in TMEM buffer b from zero
         const int s = kb % STAGES, r = kb / STAGES;
@@ -276,13 +280,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const uint32_t o = kk * 32;  // one MMA's K = 32 bytes of each operand row
-          mma<BF16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
-          mma<BF16>(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
+          mma<H16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
+          mma<H16>(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
         }
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const uint32_t o = kk * 32;
-          mma<BF16>(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
+          mma<H16>(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
         }
         mma_commit(&empty[s]);
         if (last) mma_commit(&accf[b]);
@@ -344,6 +348,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < RP; ++j) tmem_ld16(tmem + lane_base + src + (uint32_t)(col0 + 16 * (p0 + j)), v[j]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (FMT == 2) {
+#pragma unroll
+          for (int j = 0; j < RP; ++j)
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[j][e] = __float_as_uint(__uint_as_float(v[j][e]) * kFp16Unscale);
+        }
         if (row < M) {
 #pragma unroll
           for (int j = 0; j < RP; ++j) {
@@ -393,59 +403,71 @@ static EncodeTiledFn get_encode() {
 }
 
 static bool encode3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
-                     uint32_t b1, bool bf16) {
+                     uint32_t b1, int fmt) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[3] = {d0, d1, d2};
-  const uint64_t es_bytes = bf16 ? 2 : 4;
+  const uint64_t es_bytes = fmt ? 2 : 4;
+  const CUtensorMapDataType dt = fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   cuuint64_t strides[2] = {d0 * es_bytes, d0 * d1 * es_bytes};
   cuuint32_t box[3] = {b0, b1, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+  CUresult r = enc(m, dt, 3, const_cast<void*>(base), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES, bool BF16>
+template <int BN, int STAGES, int FMT>
 static cudaError_t set_attr() {
   using Lay = Layout<BN, STAGES>;
-  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL);
+  return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL);
 }
 
-template <int BN, int STAGES, bool BF16>
+template <int BN, int STAGES, int FMT>
 static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   using Lay = Layout<BN, STAGES>;
   const int64_t K2 = 2 * p.K, N2 = 2 * p.N;
-  const uint32_t BKE = BF16 ? 64 : 32;
-  const int64_t es = BF16 ? 2 : 4;
+  const uint32_t BKE = FMT ? 64 : 32;
+  const int64_t es = FMT ? 2 : 4;
   // A: hi plane then lo plane, each [PA][M][2K]; B: hi plane then lo plane, each [PB][2N][2K]
   const char* ahi = (const char*)p.A;
   const char* alo = ahi + p.PA * p.M * K2 * es;
   const char* bhi = (const char*)p.B;
   const char* blo = bhi + p.PB * N2 * K2 * es;
   CUtensorMap tah, tal, tbh, tbl;
-  if (!encode3d(&tah, ahi, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, BF16)) return cudaErrorInvalidValue;
-  if (!encode3d(&tal, alo, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, BF16)) return cudaErrorInvalidValue;
-  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, BF16)) return cudaErrorInvalidValue;
-  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, BF16)) return cudaErrorInvalidValue;
+  if (!encode3d(&tah, ahi, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT)) return cudaErrorInvalidValue;
+  if (!encode3d(&tal, alo, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, FMT)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, FMT)) return cudaErrorInvalidValue;
   const int64_t tilesM = (p.M + BM - 1) / BM, tilesN = (N2 + BN - 1) / BN;
   const int64_t grid = tilesM * tilesN * p.PC;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_gemm_tc<BN, STAGES, BF16><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(tah, tal, tbh, tbl, (float*)p.C, p.M, N2,
+  k_gemm_tc<BN, STAGES, FMT><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(tah, tal, tbh, tbl, (float*)p.C, p.M, N2,
                                                                             K2, tilesM, tilesN, p.PC, p.mapA, p.mapB,
                                                                             p.mapA_mode, p.mapB_mode, status);
   return cudaGetLastError();
 }
 
-template <bool BF16>
+template <int FMT>
 static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   const int64_t N2 = 2 * p.N;
-  if (N2 <= 16) return run<16, 6, BF16>(p, status, s);
-  if (N2 <= 32) return run<32, 5, BF16>(p, status, s);
-  if (N2 <= 64) return run<64, 4, BF16>(p, status, s);
-  if (N2 <= 128) return run<128, 3, BF16>(p, status, s);
-  return run<256, 2, BF16>(p, status, s);
+  if (N2 <= 16) return run<16, 6, FMT>(p, status, s);
+  if (N2 <= 32) return run<32, 5, FMT>(p, status, s);
+  if (N2 <= 64) return run<64, 4, FMT>(p, status, s);
+  if (N2 <= 128) return run<128, 3, FMT>(p, status, s);
+  return run<256, 2, FMT>(p, status, s);
+}
+
+template <int FMT>
+static cudaError_t set_attrs() {
+  const cudaError_t r[5] = {set_attr<16, 6, FMT>(), set_attr<32, 5, FMT>(), set_attr<64, 4, FMT>(),
+                            set_attr<128, 3, FMT>(), set_attr<256, 2, FMT>()};
+  for (cudaError_t x : r)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
 }
 
 }  // namespace tc
@@ -453,21 +475,19 @@ static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStrea
 cudaError_t prepare_gemm_tc() {
   // the opt-in shared-memory size, set once per device before any launch (and
   // so before any stream capture)
-  cudaError_t e = cudaSuccess;
-  const cudaError_t r[10] = {tc::set_attr<16, 6, false>(), tc::set_attr<32, 5, false>(),
-                             tc::set_attr<64, 4, false>(),  tc::set_attr<128, 3, false>(),
-                             tc::set_attr<256, 2, false>(), tc::set_attr<16, 6, true>(),
-                             tc::set_attr<32, 5, true>(),   tc::set_attr<64, 4, true>(),
-                             tc::set_attr<128, 3, true>(),  tc::set_attr<256, 2, true>()};
-  for (cudaError_t x : r)
-    if (x != cudaSuccess) e = x;
+  cudaError_t e = tc::set_attrs<0>();
+  const cudaError_t e1 = tc::set_attrs<1>(), e2 = tc::set_attrs<2>();
+  if (e == cudaSuccess) e = e1;
+  if (e == cudaSuccess) e = e2;
   return e;
 }
 
 cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   // row pitch of A (2K elements) must be a multiple of 16 bytes
-  if (p.K < (p.bf16 ? 4 : 2)) return cudaErrorInvalidValue;
-  return p.bf16 ? tc::dispatch<true>(p, status, s) : tc::dispatch<false>(p, status, s);
+  if (p.K < (p.h16 ? 4 : 2)) return cudaErrorInvalidValue;
+  if (p.h16 == 2) return tc::dispatch<2>(p, status, s);
+  if (p.h16 == 1) return tc::dispatch<1>(p, status, s);
+  return tc::dispatch<0>(p, status, s);
 }
 
 }  // namespace tn

@@ -2,6 +2,7 @@
 // FP32 CUDA-core complex GEMM, slice accumulation, amplitude lookup, norms and
 // the group sampler.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdio>
 
@@ -106,7 +107,8 @@ cudaError_t launch_small(const SmallParams& p, cudaStream_t s) {
 // to their positions) come from four 256-entry tables per direction.
 // SPLIT 1: the output is written as two fp32 planes, tf32-rounded hi and the
 // remainder lo; SPLIT 2: two bf16 planes, bf16 hi and the bf16-rounded
-// remainder -- the operand formats of the two tensor-core GEMM engines.
+// remainder; SPLIT 3: two fp16 planes of the value times kFp16Scale -- the
+// operand formats of the three tensor-core GEMM engines.
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
 __device__ __forceinline__ float tf32_rn(float x) {
@@ -165,6 +167,14 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
         const float2 h = make_float2(tf32_rn(v.x), tf32_rn(v.y));
         p.out[dofs + s_out[j]] = h;
         out_lo[dofs + s_out[j]] = make_float2(v.x - h.x, v.y - h.y);
+      } else if (SPLIT == 3) {
+        __half2* fh = (__half2*)p.out;
+        __half2* fl = fh + p.P * p.pstride;
+        const float2 w = make_float2(v.x * kFp16Scale, v.y * kFp16Scale);
+        const __half2 h = __floats2half2_rn(w.x, w.y);
+        const float2 hf = __half22float2(h);
+        fh[dofs + s_out[j]] = h;
+        fl[dofs + s_out[j]] = __floats2half2_rn(w.x - hf.x, w.y - hf.y);
       } else if (SPLIT == 2) {
         __nv_bfloat162* bh = (__nv_bfloat162*)p.out;
         __nv_bfloat162* bl = bh + p.P * p.pstride;
@@ -188,6 +198,7 @@ cudaError_t launch_permute(const PermParams& p, cudaStream_t s) {
                       2 * 1024 * sizeof(uint64_t);
   if (p.split == 1) k_permute<1><<<(unsigned)grid, 256, smem, s>>>(p);
   else if (p.split == 2) k_permute<2><<<(unsigned)grid, 256, smem, s>>>(p);
+  else if (p.split == 3) k_permute<3><<<(unsigned)grid, 256, smem, s>>>(p);
   else k_permute<0><<<(unsigned)grid, 256, smem, s>>>(p);
   return cudaGetLastError();
 }
@@ -251,6 +262,25 @@ __global__ void k_bprep_tc_bf16(BPrepParams p) {
   }
 }
 
+// The same embedding as fp16 hi/lo planes of the value times kFp16Scale.
+__global__ void k_bprep_tc_fp16(BPrepParams p) {
+  const int64_t K2 = 2LL << p.nk, N2 = 2LL << p.nn;
+  const int64_t per = K2 * N2;
+  const int64_t total = p.PB * per;
+  __half* hi = (__half*)p.out;
+  __half* lo = hi + total;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pb = e / per, r = e % per;
+    const int64_t j = r / K2, i = r % K2;
+    const float2 b = p.B[pb * p.b_pstride + p.bk[i >> 1] + p.bn[j >> 1]];
+    const int jc = (int)(j & 1), ic = (int)(i & 1);
+    const float v = (jc == 0 ? (ic == 0 ? b.x : -b.y) : (ic == 0 ? b.y : b.x)) * kFp16Scale;
+    const __half h = __float2half_rn(v);
+    hi[e] = h;
+    lo[e] = __float2half_rn(v - __half2float(h));
+  }
+}
+
 cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s) {
   const int64_t total = p.PB << (p.nk + p.nn);
   const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 8);
@@ -261,7 +291,8 @@ cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s) {
 cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s) {
   const int64_t total = p.PB << (p.nk + p.nn + 2);
   const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 8);
-  if (p.bf16) k_bprep_tc_bf16<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
+  if (p.h16 == 2) k_bprep_tc_fp16<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
+  else if (p.h16 == 1) k_bprep_tc_bf16<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
   else k_bprep_tc<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
   return cudaGetLastError();
 }

@@ -6,6 +6,15 @@
 
 namespace tn {
 
+// Operand scale of the FP16x3 engine.  Every intermediate of a network of
+// unitary gates, basis vectors and basis projectors is a sub-block of a
+// unitary, so its entries have modulus at most 1.  Scaling by 2^15 keeps them
+// below the fp16 maximum (65504) and lifts a typical entry and its split
+// remainder out of the fp16 subnormal range; the GEMM epilogue undoes both
+// operands' scale with 2^-30.  Powers of two: both steps are exact.
+constexpr float kFp16Scale = 32768.0f;
+constexpr float kFp16Unscale = 1.0f / (32768.0f * 32768.0f);
+
 // C[p][m + (n << (rA-nk))] = sum_k A[mapA(p)][insert_K(m) + k-offset] * B[mapB(p)][boffK[k] + boffN[n]]
 struct SmallParams {
   const float2* A; const float2* B; float2* C;
@@ -27,7 +36,8 @@ struct PermParams {
   int n_rest;
   uint8_t rest_in[64], rest_out[64];
   const uint32_t* tab;   // in_off[2^t], out_off[2^t], slot[2^t]
-  int split;             // 1: write tf32 hi plane then lo plane (fp32 pairs); 2: bf16 planes
+  int split;             // 1: write tf32 hi plane then lo plane (fp32 pairs); 2: bf16 planes;
+                         // 3: fp16 planes of the value times kFp16Scale
 };
 
 struct BPrepParams {
@@ -35,7 +45,7 @@ struct BPrepParams {
   int64_t b_pstride, PB;
   int nk, nn;
   const uint32_t* bk; const uint32_t* bn;
-  int bf16;              // tensor-core B: 0 tf32 planes, 1 bf16 planes
+  int h16;               // tensor-core B: 0 tf32 planes, 1 bf16 planes, 2 scaled fp16 planes
 };
 
 // C[p][m][n] = sum_k A[mapA(p)][m][k] B[mapB(p)][k][n]
@@ -45,7 +55,7 @@ struct GemmParams {
   int64_t PA, PB, PC;
   const uint32_t* mapA; const uint32_t* mapB;
   int mapA_mode, mapB_mode;
-  int bf16;              // tensor-core engine: operands are bf16 hi/lo planes
+  int h16;               // tensor-core engine: 0 tf32, 1 bf16, 2 scaled fp16 hi/lo operand planes
 };
 
 struct AccumParams {

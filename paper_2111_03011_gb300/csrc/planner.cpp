@@ -352,6 +352,8 @@ struct TrialResult {
   bool fits = false;
   double cost = 1e300, mx = 1e300;
   std::vector<std::pair<int, int>> order;
+  std::vector<int> legs;   // legs automatic slicing cuts on this order
+  std::string why;
 };
 
 // One randomised greedy trial; trial 0 is the plain greedy (alpha 1, no noise).
@@ -444,6 +446,125 @@ static bool better(const TrialResult& a, const TrialResult& b) {   // is a bette
   return a.mx < b.mx || (a.mx == b.mx && a.cost < b.cost);
 }
 
+// Automatic slicing.  Slicing a bond leg that survives host simplification
+// turns it into a variant axis of the two leaves holding it: the leaf set, and
+// with it any order over the leaves, stays as it is.  For a fixed order the
+// slicer replays the contractions once, then adds legs one at a time: the
+// candidates are the bond legs of the largest intermediate that are wires of
+// the circuit, and the pick is the one with the smallest modelled time of all
+// 2^|S| passes.  It stops when every intermediate fits the cap.
+struct StepLegs {
+  std::vector<int> a, b, c, k;   // legs of A, B, C and the contracted ones
+  double pa = 0, pb = 0, pc = 0; // log2 pattern counts
+};
+
+struct SliceResult {
+  bool ok = false;
+  double cost = 1e300, mx = 1e300;   // modelled time of all passes; largest intermediate
+  std::vector<int> legs;             // sliced legs, in the order they were picked
+  std::string why;
+};
+
+static std::vector<StepLegs> replay_steps(PatternBook& book, const std::vector<GNode>& init,
+                                          const std::vector<std::pair<int, int>>& order) {
+  std::vector<GNode> g = init;
+  std::vector<StepLegs> out;
+  out.reserve(order.size());
+  for (auto& pr : order) {
+    StepLegs st;
+    const GNode &A = g[pr.first], &B = g[pr.second];
+    st.a = A.legs;
+    st.b = B.legs;
+    for (int l : A.legs)
+      if (find_pos(B.legs, l) >= 0) st.k.push_back(l);
+    st.c = sym_diff_bond(A.legs, B.legs);
+    st.pa = std::log2((double)book.count(A.tq));
+    st.pb = std::log2((double)book.count(B.tq));
+    const uint64_t tq = A.tq | B.tq;
+    st.pc = std::log2((double)book.count(tq));
+    GNode C;
+    C.legs = st.c;
+    C.tq = tq;
+    C.lsz = st.pc + (double)st.c.size();
+    g[pr.first] = C;
+    g[pr.second].alive = false;
+    out.push_back(std::move(st));
+  }
+  return out;
+}
+
+static inline int count_sliced(const std::vector<int>& legs, const std::vector<char>& sl) {
+  int n = 0;
+  for (int l : legs) n += sl[l];
+  return n;
+}
+
+static double sliced_step_time(const StepLegs& st, const std::vector<char>& sl, bool tc, double* lc) {
+  const double lA = st.pa + (double)st.a.size() - count_sliced(st.a, sl);
+  const double lB = st.pb + (double)st.b.size() - count_sliced(st.b, sl);
+  const double lC = st.pc + (double)st.c.size() - count_sliced(st.c, sl);
+  const int nk = (int)st.k.size() - count_sliced(st.k, sl);
+  const int ra = (int)st.a.size() - count_sliced(st.a, sl), rb = (int)st.b.size() - count_sliced(st.b, sl);
+  const int nn_small = (lA <= lB ? ra : rb) - nk;
+  if (lc) *lc = lC;
+  return step_time_model(lA, lB, lC, nk, nn_small, tc);
+}
+
+static SliceResult slice_order(const Plan& plan, PatternBook& book, const std::vector<GNode>& init,
+                               const std::vector<std::pair<int, int>>& order, double cap, int budget) {
+  SliceResult r;
+  const bool tc = plan.gemm_engine != TN_GEMM_SIMT_FP32;
+  std::vector<StepLegs> steps = replay_steps(book, init, order);
+  const int nl = (int)plan.legs.size();
+  std::vector<char> sl(nl, 0);
+  std::vector<std::vector<int>> touch(nl);   // leg -> steps whose operands or result carry it
+  for (size_t i = 0; i < steps.size(); ++i) {
+    std::set<int> u(steps[i].a.begin(), steps[i].a.end());
+    u.insert(steps[i].b.begin(), steps[i].b.end());
+    for (int l : u) touch[l].push_back((int)i);
+  }
+  double leaf_mx = 0;
+  for (auto& x : init) leaf_mx = std::max(leaf_mx, x.lsz);
+  std::vector<double> t(steps.size()), lcs(steps.size());
+  double sum = 0;
+  for (size_t i = 0; i < steps.size(); ++i) sum += t[i] = sliced_step_time(steps[i], sl, tc, &lcs[i]);
+  while (true) {
+    int im = -1;
+    double mx = leaf_mx;
+    for (size_t i = 0; i < steps.size(); ++i)
+      if (lcs[i] > mx) { mx = lcs[i]; im = (int)i; }
+    r.mx = mx;
+    if (mx <= cap + 1e-9) break;
+    if (im < 0) { r.why = "a leaf exceeds the cap"; return r; }
+    if ((int)r.legs.size() >= budget) {
+      r.why = "more than " + std::to_string(budget) + " extra edges needed";
+      return r;
+    }
+    int best = -1;
+    double best_sum = 1e300;
+    for (int l : steps[im].c) {
+      if (sl[l] || plan.legs[l].kind != LEG_BOND) continue;
+      if (l >= (int)plan.leg_edge.size() || plan.leg_edge[l].first < 0) continue;
+      sl[l] = 1;
+      double s2 = sum;
+      for (int i : touch[l]) s2 += sliced_step_time(steps[i], sl, tc, nullptr) - t[i];
+      sl[l] = 0;
+      if (s2 < best_sum) { best_sum = s2; best = l; }
+    }
+    if (best < 0) { r.why = "open legs and tail patterns alone exceed the cap"; return r; }
+    sl[best] = 1;
+    r.legs.push_back(best);
+    for (int i : touch[best]) {
+      const double tn_ = sliced_step_time(steps[i], sl, tc, &lcs[i]);
+      sum += tn_ - t[i];
+      t[i] = tn_;
+    }
+  }
+  r.ok = true;
+  r.cost = std::ldexp(sum, (int)r.legs.size());
+  return r;
+}
+
 // Randomised greedy search (restarts).  Each trial repeatedly contracts the
 // connected pair minimising size(C) - alpha * (size(A) + size(B)), with alpha
 // drawn per trial and Gumbel noise of temperature tau on log-scores after the
@@ -452,9 +573,14 @@ static bool better(const TrialResult& a, const TrialResult& b) {   // is a bette
 // modelled time (or, if none fits, the one with the smallest maximum).  Trials
 // are seeded independently and spread over the host's cores; the result does
 // not depend on the number of threads (ties go to the lower trial index).
+//
+// With a slicing budget, a third of the trials run under the cap as above, a
+// third with no cap and a third with the cap raised by 2..7; every trial's
+// order is then sliced to the cap (slice_order) and trials compete on the
+// modelled time of all their passes.
 static int greedy_order(Plan& plan, const std::vector<GNode>& init, double cap, int trials, uint64_t seed,
-                        std::vector<std::pair<int, int>>& best_order, std::string& err) {
-  // on failure best_order still receives the best over-cap order (for slicing)
+                        int budget, std::vector<std::pair<int, int>>& best_order, std::vector<int>& best_legs,
+                        std::string& err) {
   trials = std::max(1, trials);
   const int nthreads = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), std::min(trials, 32)));
   // pattern counts of every tail-qubit subset a trial may meet, warmed serially
@@ -467,7 +593,20 @@ static int greedy_order(Plan& plan, const std::vector<GNode>& init, double cap, 
       PatternBook book;
       book.tails = plan.book.tails;
       for (int trial = t; trial < trials; trial += nthreads) {
-        TrialResult r = greedy_trial(plan, book, init, cap, seed, trial);
+        double tcap = cap;
+        if (budget > 0 && trial % 3 == 1) tcap = 1e9;
+        if (budget > 0 && trial % 3 == 2) tcap = cap + 2 + (trial / 3) % 6;
+        TrialResult r = greedy_trial(plan, book, init, tcap, seed, trial);
+        if (budget > 0) {
+          SliceResult sr = slice_order(plan, book, init, r.order, cap, budget);
+          r.fits = sr.ok;
+          if (sr.ok) {
+            r.cost = sr.cost;
+            r.mx = sr.mx;
+          }
+          r.legs = std::move(sr.legs);
+          r.why = std::move(sr.why);
+        }
         if (best_idx[t] < 0 || better(r, best[t])) {
           best[t] = std::move(r);
           best_idx[t] = trial;
@@ -485,72 +624,12 @@ static int greedy_order(Plan& plan, const std::vector<GNode>& init, double cap, 
   if (bt < 0 || !best[bt].fits) {
     err = "no contraction order found keeps every intermediate under the size cap (best 2^" +
           std::to_string(bt < 0 ? 0.0 : best[bt].mx) + " elements); slice more edges or raise the cap";
-    if (bt >= 0) best_order = best[bt].order;
+    if (budget > 0 && bt >= 0) err += " (automatic slicing: " + best[bt].why + ")";
     return TN_ERR_OOM;
   }
   best_order = best[bt].order;
+  best_legs = best[bt].legs;
   return TN_OK;
-}
-
-// Automatic slicing: replay `order`, then pick bond legs one at a time -- the
-// leg carried by the most over-cap intermediates (ties: the larger summed
-// excess) -- until every intermediate fits the cap.  Only legs that are the
-// input wire of a gate (so that they can be written as a cut edge) qualify.
-static bool choose_slice_legs(const Plan& plan, PatternBook& book, const std::vector<GNode>& init,
-                              const std::vector<std::pair<int, int>>& order, double cap, int max_extra,
-                              std::vector<int>& legs_out, std::string& why) {
-  std::vector<GNode> g = init;
-  std::vector<GNode> inter;
-  for (auto& x : g) inter.push_back(x);
-  for (auto& pr : order) {
-    GNode C;
-    C.legs = sym_diff_bond(g[pr.first].legs, g[pr.second].legs);
-    C.tq = g[pr.first].tq | g[pr.second].tq;
-    C.lsz = std::log2((double)book.count(C.tq)) + (double)C.legs.size();
-    g[pr.first] = C;
-    g[pr.second].alive = false;
-    inter.push_back(C);
-  }
-  std::set<int> sliced;
-  while (true) {
-    std::map<int, std::pair<int, double>> score;   // leg -> (count, excess)
-    bool over = false;
-    for (auto& T : inter) {
-      int removed = 0;
-      for (int l : T.legs) removed += sliced.count(l) ? 1 : 0;
-      const double ex = T.lsz - removed - cap;
-      if (ex <= 1e-9) continue;
-      over = true;
-      int avail = 0;
-      for (int l : T.legs) {
-        if (sliced.count(l) || plan.legs[l].kind != LEG_BOND) continue;
-        if (l >= (int)plan.leg_edge.size() || plan.leg_edge[l].first < 0) continue;
-        auto& sc = score[l];
-        sc.first += 1;
-        sc.second += ex;
-        ++avail;
-      }
-      if (ex > avail + 1e-9) {
-        why = "open legs and tail patterns alone exceed the cap";
-        return false;
-      }
-    }
-    if (!over) break;
-    if ((int)sliced.size() >= max_extra || score.empty()) {
-      why = "more than " + std::to_string(max_extra) + " extra edges needed";
-      return false;
-    }
-    int best = -1;
-    std::pair<int, double> bs{-1, -1.0};
-    for (auto& kv : score)
-      if (kv.second.first > bs.first || (kv.second.first == bs.first && kv.second.second > bs.second)) {
-        bs = kv.second;
-        best = kv.first;
-      }
-    sliced.insert(best);
-  }
-  legs_out.assign(sliced.begin(), sliced.end());
-  return true;
 }
 
 // ---------------------------------------------------------------- step layout
@@ -737,8 +816,9 @@ static int layout_steps(Plan& plan, std::string& err) {
       for (int l : K) target.push_back(l);
       for (int l : M) target.push_back(l);
       Ref aref = big.ref;
-      // bf16 operands need K >= 4 (16-byte rows); K = 2 steps use the tf32 kernel
-      const bool bf16 = plan.gemm_engine == TN_GEMM_TC_BF16X3 && nk >= 2;
+      // 16-bit operands need K >= 4 (16-byte rows); K = 2 steps use the tf32 kernel
+      const int h16 = nk >= 2 ? (plan.gemm_engine == TN_GEMM_TC_BF16X3 ? 1 : plan.gemm_engine == TN_GEMM_TC_FP16X3 ? 2 : 0) : 0;
+      const bool bf16 = h16 != 0;
       const bool tc = plan.gemm_engine != TN_GEMM_SIMT_FP32 && nk >= 1;
       if (tc || target != big.legs) {
         // the tensor-core GEMM reads A as hi/lo planes: always a (possibly
@@ -746,13 +826,13 @@ static int layout_steps(Plan& plan, std::string& err) {
         const int st = (int)plan.steps.size();
         touch(plan, big.ref, st);
         Ref out{1, new_buf(plan, vt_elems(big) * 8 * (tc && !bf16 ? 2 : 1), st)};
-        add_permute(plan, big, target, out, ci, tc ? (bf16 ? 2 : 1) : 0);
+        add_permute(plan, big, target, out, ci, tc ? (h16 == 2 ? 3 : h16 == 1 ? 2 : 1) : 0);
         aref = out;
       }
       // B' prep
       Step p;
       p.kind = tc ? ST_BPREP_TC : ST_BPREP_C;
-      p.bf16 = bf16 ? 1 : 0;
+      p.h16 = h16;
       p.contraction = ci;
       p.a = sml.ref;
       p.rA = (int)sml.legs.size();
@@ -771,7 +851,7 @@ static int layout_steps(Plan& plan, std::string& err) {
       }
       Step g;
       g.kind = tc ? ST_GEMM_TC : ST_GEMM_SIMT;
-      g.bf16 = bf16 ? 1 : 0;
+      g.h16 = h16;
       g.contraction = ci;
       g.a = aref;
       g.b = p.c;
@@ -835,6 +915,58 @@ static void plan_arena(Plan& plan) {
 }
 
 // --------------------------------------------------------------------- driver
+
+// Leaves: the tensors left after simplification, each stored once per value
+// of its sliced (half) legs, and their virtual tensors (device legs only).
+static void build_leaves(Plan& plan, const std::vector<HostTensor>& T) {
+  plan.leaves.clear();
+  for (auto& t : T)
+    if (t.alive) plan.leaves.push_back(t);
+  plan.leaf_info.clear();
+  plan.leaf_arena.clear();
+  plan.vts.clear();
+  for (auto& t : plan.leaves) {
+    LeafInfo li;
+    std::vector<int> half_pos;
+    std::vector<int> dev_legs;
+    for (size_t p = 0; p < t.legs.size(); ++p) {
+      if (plan.legs[t.legs[p]].kind == LEG_HALF) {
+        half_pos.push_back((int)p);
+        li.var_slice_bits.push_back(plan.legs[t.legs[p]].slice_bit);
+      } else dev_legs.push_back(t.legs[p]);
+    }
+    li.size = t.P() * (1LL << dev_legs.size());
+    // align each leaf to 16 complex elements (128 bytes)
+    while (plan.leaf_arena.size() % 16) plan.leaf_arena.push_back(cd(0, 0));
+    li.off = (int64_t)plan.leaf_arena.size();
+    const int nh = (int)half_pos.size();
+    for (int v = 0; v < (1 << nh); ++v) {
+      HostTensor x = t;
+      for (int hh = nh - 1; hh >= 0; --hh) select_leg(x, half_pos[hh], (v >> hh) & 1);
+      plan.leaf_arena.insert(plan.leaf_arena.end(), x.data.begin(), x.data.end());
+    }
+    plan.leaf_info.push_back(li);
+    VTensor vt;
+    vt.legs = dev_legs;
+    vt.tq = t.tq;
+    vt.P = t.P();
+    vt.ref = Ref{0, (int)plan.leaf_info.size() - 1};
+    plan.vts.push_back(vt);
+  }
+}
+
+// Slice `legs` (bond legs between leaves) as internal edges: each becomes a
+// half leg with slice bit k, k+1, ... on both leaves that hold it.
+static void apply_internal_slices(Plan& plan, const std::vector<HostTensor>& T, const std::vector<int>& legs) {
+  plan.n_internal = (int)legs.size();
+  plan.internal_edges.clear();
+  for (size_t i = 0; i < legs.size(); ++i) {
+    plan.legs[legs[i]].kind = LEG_HALF;
+    plan.legs[legs[i]].slice_bit = plan.n_sliced + (int)i;
+    plan.internal_edges.push_back(plan.leg_edge[legs[i]]);
+  }
+  build_leaves(plan, T);
+}
 
 int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
   const int n = in.n_qubits;
@@ -904,11 +1036,29 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
     } else { err = "edge: unknown kind"; return TN_ERR_INVALID; }
   }
   if (k > 40) { err = "at most 40 sliced edges"; return TN_ERR_INVALID; }
-  plan.n_sliced = k - in.n_internal;
-  plan.n_internal = in.n_internal;
+  if (in.gemm_engine == TN_GEMM_TC_FP16X3) {
+    // the FP16x3 engine's fixed operand scale relies on every intermediate
+    // being a sub-block of a unitary (entries of modulus <= 1)
+    for (int g = 0; g < in.n_gates; ++g) {
+      const int d = in.arity[g] == 1 ? 2 : 4;
+      const cd* U = in.mats + (size_t)g * 16;
+      double dev = 0.0;
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+          cd s(0, 0);
+          for (int r = 0; r < d; ++r) s += std::conj(U[r * d + i]) * U[r * d + j];
+          dev = std::max(dev, std::abs(s - cd(i == j ? 1.0 : 0.0, 0.0)));
+        }
+      if (dev > 1e-6) {
+        err = "the FP16x3 engine needs unitary gates (gate " + std::to_string(g) + " is not)";
+        return TN_ERR_INVALID;
+      }
+    }
+  }
+  if (k + in.auto_slice > 62) { err = "sliced edges plus auto_slice above 62"; return TN_ERR_INVALID; }
+  plan.n_sliced = k;
+  plan.n_internal = 0;
   plan.internal_edges.clear();
-  for (size_t e = in.edges.size() - in.n_internal; e < in.edges.size(); ++e)
-    plan.internal_edges.push_back({in.edges[e].gate, in.edges[e].leg});
   plan.n_pinned = pins;
   plan.n_companion = companions;
   plan.companion_factor = comp_factor;
@@ -921,45 +1071,17 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
     if (plan.legs[u.leg].kind == LEG_BOND) plan.leg_edge[u.leg] = {u.gate, u.pos};
   simplify(plan, b.T, in.absorb_log2);
 
-  // leaves
-  plan.leaves.clear();
-  for (auto& t : b.T)
-    if (t.alive) plan.leaves.push_back(t);
-  plan.leaf_info.clear();
-  plan.leaf_arena.clear();
-  plan.vts.clear();
-  for (auto& t : plan.leaves) {
-    LeafInfo li;
-    std::vector<int> half_pos;
-    std::vector<int> dev_legs;
-    for (size_t p = 0; p < t.legs.size(); ++p) {
-      if (plan.legs[t.legs[p]].kind == LEG_HALF) {
-        half_pos.push_back((int)p);
-        li.var_slice_bits.push_back(plan.legs[t.legs[p]].slice_bit);
-      } else dev_legs.push_back(t.legs[p]);
-    }
-    li.size = t.P() * (1LL << dev_legs.size());
-    // align each leaf to 16 complex elements (128 bytes)
-    while (plan.leaf_arena.size() % 16) plan.leaf_arena.push_back(cd(0, 0));
-    li.off = (int64_t)plan.leaf_arena.size();
-    const int nh = (int)half_pos.size();
-    for (int v = 0; v < (1 << nh); ++v) {
-      HostTensor x = t;
-      for (int hh = nh - 1; hh >= 0; --hh) select_leg(x, half_pos[hh], (v >> hh) & 1);
-      plan.leaf_arena.insert(plan.leaf_arena.end(), x.data.begin(), x.data.end());
-    }
-    plan.leaf_info.push_back(li);
-    VTensor vt;
-    vt.legs = dev_legs;
-    vt.tq = t.tq;
-    vt.P = t.P();
-    vt.ref = Ref{0, (int)plan.leaf_info.size() - 1};
-    plan.vts.push_back(vt);
-  }
+  build_leaves(plan, b.T);
   const int nleaf = (int)plan.leaves.size();
 
   // order over slots 0..nleaf-1 (result of (i, j) stored at slot i)
   std::vector<std::pair<int, int>> slot_order;
+  std::vector<GNode> init(nleaf);
+  for (int i = 0; i < nleaf; ++i) {
+    init[i].legs = plan.vts[i].legs;
+    init[i].tq = plan.vts[i].tq;
+    init[i].lsz = std::log2((double)plan.vts[i].P) + (double)plan.vts[i].legs.size();
+  }
   if (in.order) {
     std::vector<char> alive(nleaf, 1);
     for (int64_t p = 0; p < in.n_pairs; ++p) {
@@ -976,38 +1098,20 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
     for (int i = 0; i < nleaf; ++i)
       if (alive[i]) rest.push_back(i);
     for (size_t r = 1; r < rest.size(); ++r) slot_order.push_back({rest[0], rest[r]});
-  } else {
-    std::vector<GNode> init(nleaf);
-    for (int i = 0; i < nleaf; ++i) {
-      init[i].legs = plan.vts[i].legs;
-      init[i].tq = plan.vts[i].tq;
-      init[i].lsz = std::log2((double)plan.vts[i].P) + (double)plan.vts[i].legs.size();
-    }
-    rc = greedy_order(plan, init, plan.cap_log2, in.order_trials, in.order_seed, slot_order, err);
-    if (rc == TN_ERR_OOM && in.auto_slice > 0 && !slot_order.empty()) {
-      // slice the wires chosen on the best over-cap order: they become
-      // trailing SLICE edges whose slice bits are summed inside every slice
-      std::vector<int> legs;
-      std::string why;
-      if (!choose_slice_legs(plan, plan.book, init, slot_order, plan.cap_log2, in.auto_slice, legs, why)) {
-        err += " (automatic slicing: " + why + ")";
+    if (in.auto_slice > 0) {
+      // the caller's order, sliced to the cap
+      SliceResult sr = slice_order(plan, plan.book, init, slot_order, plan.cap_log2, in.auto_slice);
+      if (!sr.ok) {
+        err = "the given order exceeds the size cap (automatic slicing: " + sr.why + ")";
         return TN_ERR_OOM;
       }
-      // Cutting a wire can let host simplification absorb more tensors, so the
-      // order is searched again on the sliced network; what still does not fit
-      // is sliced further from the remaining budget.
-      PlanInput in2 = in;
-      for (int l : legs) in2.edges.push_back({plan.leg_edge[l].first, plan.leg_edge[l].second, TN_EDGE_SLICE, 0});
-      in2.auto_slice = in.auto_slice - (int)legs.size();
-      in2.n_internal = in.n_internal + (int)legs.size();
-      Plan fresh;
-      err.clear();
-      rc = build_plan(in2, fresh, err);
-      if (rc) return rc;
-      plan = std::move(fresh);
-      return TN_OK;
+      if (!sr.legs.empty()) apply_internal_slices(plan, b.T, sr.legs);
     }
+  } else {
+    std::vector<int> cut;
+    rc = greedy_order(plan, init, plan.cap_log2, in.order_trials, in.order_seed, in.auto_slice, slot_order, cut, err);
     if (rc) return rc;
+    if (!cut.empty()) apply_internal_slices(plan, b.T, cut);
   }
   // translate slot pairs to virtual-tensor pairs
   std::vector<int> slot_vt(nleaf);
@@ -1110,7 +1214,7 @@ std::string describe_plan(const Plan& plan, bool with_data) {
       << ",\"PA\":" << st.PA << ",\"PB\":" << st.PB << ",\"PC\":" << st.PC << ",\"macs\":" << st.macs
       << ",\"bytes\":" << st.bytes << ",\"rA\":" << st.rA << ",\"rB\":" << st.rB << ",\"rC\":" << st.rC
       << ",\"a\":[" << st.a.kind << "," << st.a.id << "],\"b\":[" << st.b.kind << "," << st.b.id << "],\"c\":["
-      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"bf16\":" << st.bf16
+      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"h16\":" << st.h16
       << ",\"tab_off\":" << st.tab_off << ",\"n_rest\":" << st.n_rest << ",\"rest_in\":[";
     for (int v = 0; v < st.n_rest; ++v) o << (v ? "," : "") << (int)st.rest_in[v];
     o << "],\"rest_out\":[";

@@ -88,8 +88,8 @@ struct Step {
   uint32_t boffK[16] = {0}, boffN[16] = {0};
   // PERMUTE: tile bits t; tables in meta: in_off[2^t], out_off[2^t], slot[2^t]
   int t_bits = 0;
-  int split = 0;           // PERMUTE: 1 tf32 hi/lo planes, 2 bf16 hi/lo planes (tensor-core GEMM operand)
-  int bf16 = 0;            // BPREP_TC / GEMM_TC: bf16 operand planes
+  int split = 0;           // PERMUTE: 1 tf32 hi/lo planes, 2 bf16, 3 scaled fp16 (tensor-core GEMM operand)
+  int h16 = 0;             // BPREP_TC / GEMM_TC: 16-bit operand planes (0 tf32, 1 bf16, 2 scaled fp16)
   int64_t tab_off = 0;
   int n_rest = 0;
   uint8_t rest_in[64] = {0}, rest_out[64] = {0};
@@ -173,7 +173,6 @@ struct PlanInput {
   int absorb_log2 = 12;
   int small_max_bits = 4;
   int auto_slice = 0;       // at most this many extra sliced edges when no order fits the cap
-  int n_internal = 0;       // trailing SLICE edges that automatic slicing added
 };
 
 int build_plan(const PlanInput& in, Plan& plan, std::string& err);

@@ -15,7 +15,9 @@ def _pats(tails_masked, tq):
     return sorted(set(int(t) & tq for t in tails_masked))
 
 
-def emulate(desc, tails, open_qubits, slices):
+def emulate(desc, tails, open_qubits, slices, on_tensor=None):
+    """Sum over `slices` of the replayed plan; `on_tensor(array)` (optional)
+    sees every leaf variant and every intermediate."""
     n = desc["n_qubits"]
     tail_mask = desc["tail_mask"]
     tm = [int(t) & tail_mask for t in tails]
@@ -40,6 +42,8 @@ def emulate(desc, tails, open_qubits, slices):
             re = np.array(lf["re"][v * size:(v + 1) * size])
             im = np.array(lf["im"][v * size:(v + 1) * size])
             T[i] = (re + 1j * im).reshape(lf["P"], -1)
+            if on_tensor:
+                on_tensor(T[i])
         for (a, b, c) in contr:
             A, B = T[a], T[b]
             la, lb, lc = vts[a]["legs"], vts[b]["legs"], vts[c]["legs"]
@@ -61,6 +65,8 @@ def emulate(desc, tails, open_qubits, slices):
             assert "Z" not in "".join(letter.values())
             Ct = np.einsum(f"{sa},{sb}->{sc}", At, Bt)
             T[c] = Ct.reshape(len(pc), -1)
+            if on_tensor:
+                on_tensor(T[c])
         F = T[desc["final"]["vt"]]
         fp = _pats(tm, tail_mask)
         op = desc["final"]["open_pos"]

@@ -64,8 +64,10 @@ def assert_close(H, ref, tol=REL_L2):
 
 
 ENGINES = [dict(gemm=0), dict(gemm=2), dict(gemm=0, small_max_bits=-1), dict(gemm=2, small_max_bits=-1),
-           dict(gemm=0, small_max_bits=2), dict(gemm=3), dict(gemm=3, small_max_bits=-1)]
-ENGINE_IDS = ["tc", "simt", "tc-allgemm", "simt-allgemm", "tc-small2", "bf16", "bf16-allgemm"]
+           dict(gemm=0, small_max_bits=2), dict(gemm=3), dict(gemm=3, small_max_bits=-1), dict(gemm=4),
+           dict(gemm=4, small_max_bits=-1)]
+ENGINE_IDS = ["tc", "simt", "tc-allgemm", "simt-allgemm", "tc-small2", "bf16", "bf16-allgemm", "fp16",
+              "fp16-allgemm"]
 
 
 def tol_of(eng):
@@ -264,7 +266,7 @@ def test_sliced30_full_size_properties(tn):
 _SLICED30_REF = {}
 
 
-@pytest.mark.parametrize("gemm", [1, 3], ids=["tc3xtf32", "bf16x3"])
+@pytest.mark.parametrize("gemm", [1, 3, 4], ids=["tc3xtf32", "bf16x3", "fp16x3"])
 def test_sliced30_full_size_sampled_groups_vs_oracle(tn, gemm):
     """Full-size workload in the bench's launch configuration (same plan, same
     kernels): one slice contracted for all 64 groups; two sampled groups
@@ -304,7 +306,7 @@ def test_profile_and_reset(tn):
     assert kinds[-1] == -1 and set(kinds[:-1]) <= {0, 1, 2, 3, 4, 5}
 
 
-@pytest.mark.parametrize("gemm", [0, 3], ids=["tc", "bf16"])
+@pytest.mark.parametrize("gemm", [0, 3, 4], ids=["tc", "bf16", "fp16"])
 def test_companion_cuts_parity_and_f_est(tn, gemm):
     """Companion cuts on the GPU path vs the oracle with the partner outputs
     fixed; F_est = prod (1 + sin^2 theta)/2 over the companions."""
@@ -510,7 +512,7 @@ def test_autotuned_plan_parity(tn):
     assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg))
 
 
-@pytest.mark.parametrize("gemm", [0, 3], ids=["tc", "bf16"])
+@pytest.mark.parametrize("gemm", [0, 3, 4], ids=["tc", "bf16", "fp16"])
 def test_automatic_slicing_parity_f_est_profile_and_graph(tn, gemm):
     """A cap that no order meets: the planner slices extra wires, runs every
     internal value inside each user slice, and the head, F_est, the profile
