@@ -304,6 +304,22 @@ def serving_mix(seed=5, n_circuits=6):
     return out
 
 
+def batch_mix(n_circuits=256, seed=7, n_open=6, L=16):
+    """Seeded batch of grid circuits of 16-28 qubits and 8-16 cycles (seeds
+    100, 101, ...), each with `n_open` open qubits and `L` tails, no cut
+    edges: the many-small-circuits batched workload."""
+    rng = np.random.default_rng(seed)
+    shapes = [(4, 4), (3, 6), (4, 5), (3, 7), (4, 6), (5, 5), (4, 7)]
+    out = []
+    for i in range(n_circuits):
+        r, c = shapes[int(rng.integers(len(shapes)))]
+        m = int(rng.integers(8, 17))
+        cfg = config_small(r, c, m, seed=100 + i, n_open=n_open, L=L, n_cut_gates=0, tail_seed=1000 + i)
+        cfg["name"] = f"grid{r}x{c}_m{m}"
+        out.append(cfg)
+    return out
+
+
 def poisson_requests(n_requests, rate_per_s, n_circuits, seed=9):
     """Seeded request stream: arrival times (Poisson), circuit ids, kinds
     (70 % amplitude batches, 30 % sampling) and log-uniform sizes."""

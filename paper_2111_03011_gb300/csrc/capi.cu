@@ -605,21 +605,25 @@ extern "C" int tn_contract_batch(tn_plan_t* const* plans, const tn_range* ranges
   }
   const int n_branches = std::min<int>((int)branch_of_plan.size(), 32);
   for (int i = 0; i < n; ++i) branch[i] %= n_branches;
-  // single-entry cache: the same batch again replays the same graph
-  static thread_local std::vector<tn_plan_t*> last_p;
+  // single-entry cache: the same batch again replays the same graph.  Keyed
+  // on the handles' serials (never reused), not on their addresses.
+  static thread_local std::vector<uint64_t> last_p;
   static thread_local std::vector<int64_t> last_r;
-  static thread_local std::vector<tn_head_t*> last_h;
+  static thread_local std::vector<uint64_t> last_h;
   static thread_local cudaGraphExec_t last_exec = nullptr;
   std::vector<int64_t> rr;
   for (auto& x : R) { rr.push_back(x.begin); rr.push_back(x.end); }
-  if (!(last_exec && last_p == P && last_r == rr && last_h == Hs)) {
+  std::vector<uint64_t> sp, sh;
+  for (auto* x : P) sp.push_back(x->serial);
+  for (auto* x : Hs) sh.push_back(x->serial);
+  if (!(last_exec && last_p == sp && last_r == rr && last_h == sh)) {
     if (last_exec) cudaGraphExecDestroy(last_exec);
     last_exec = nullptr;
     int rc = capture_items(P, R, Hs, branch, n_branches, &last_exec);
     if (rc) { last_exec = nullptr; return rc; }
-    last_p = P;
+    last_p = sp;
     last_r = rr;
-    last_h = Hs;
+    last_h = sh;
   }
   CUDA_TRY(cudaGraphLaunch(last_exec, (cudaStream_t)stream));
   for (int i = 0; i < n; ++i) mark_done(Hs[i], R[i]);

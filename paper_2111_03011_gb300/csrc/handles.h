@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -18,7 +19,17 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
 };
 
+namespace tn {
+// Unique, never reused identity of a plan or head (caches must not key on
+// addresses: a freed handle's address can come back for a new one).
+inline uint64_t next_serial() {
+  static std::atomic<uint64_t> c{1};
+  return c.fetch_add(1);
+}
+}  // namespace tn
+
 struct tn_plan {
+  uint64_t serial = tn::next_serial();
   tn::Plan P;
   double measured_slice_ms = 0.0;
   int autotune_candidates = 0;
@@ -38,6 +49,7 @@ struct tn_plan {
 };
 
 struct tn_head {
+  uint64_t serial = tn::next_serial();
   tn_plan_t* plan = nullptr;
   double2* H = nullptr;
   bool owns = false;

@@ -418,6 +418,18 @@ def test_batch_of_mixed_circuits_in_one_graph(tn):
         assert np.array_equal(read_head(tn, p, hd, cfg), pl)
     with pytest.raises(tn.TNError):
         tn.tn_contract_batch(plans[:2], ranges[:2], [heads[0], heads[0]])
+    # the cached graph is keyed on handle identity: freed plans and heads whose
+    # addresses come back for new ones (same ranges) must not replay it
+    del plans, heads
+    import gc
+    gc.collect()
+    cfgs2 = [ci.config_small(r, c, m, seed=70 + i, n_open=h, L=L, n_cut_gates=cut)
+             for i, (r, c, m, h, L, cut) in enumerate(shapes)]
+    plans2 = [tn.tn_plan(cf["circuit"], cf["open_qubits"], cf["tails"], cf["edges"]) for cf in cfgs2]
+    heads2 = [tn.tn_head_create(p) for p in plans2]
+    tn.tn_contract_batch(plans2, [(0, 1 << tn.tn_plan_get_stats(p)["n_sliced"]) for p in plans2], heads2)
+    for cf, p, hd in zip(cfgs2, plans2, heads2):
+        assert_close(read_head(tn, p, hd, cf), oracle_head(cf))
 
 
 def _server_cases(tn):
