@@ -501,7 +501,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sliced30", choices=["sliced30", "tiny", "grid25", "serve", "batch"])
     ap.add_argument("--circuits", type=int, default=256, help="batch workload: number of circuits")
-    ap.add_argument("--engine", default="tc", choices=["tc", "simt", "bf16", "fp16"])
+    ap.add_argument("--engine", default="fp16", choices=["tc", "simt", "bf16", "fp16"],
+                    help="GEMM-step engine: fp16 = FP16x3 (complex64 accuracy, default), tc = 3xTF32, "
+                         "bf16 = BF16x3 (1e-4), simt = plain complex64 on CUDA cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", type=int, default=4,
                     help="plan candidates timed on the GPU by tn_plan_autotune (0: plain tn_plan)")

@@ -267,7 +267,7 @@ void tn_server_free(tn_server_t* server);   /* drains the queue first */
 int  tn_head_norm(tn_head_t* head, double* norm, double* group_norms, void* stream);
 
 /* Tracing: like tn_contract_slices, but times every launch with CUDA events
- * on `stream` (synchronising after each pass) and returns in step_ms[i] the
+ * on `stream` (synchronising once per 64 passes) and returns in step_ms[i] the
  * summed milliseconds of launch i of the per-pass launch list over the range
  * and every internal pass (i < n_launches >> n_internal_sliced of
  * tn_plan_stats; the last entry is the slice accumulation).  Accumulates

@@ -65,6 +65,7 @@ static void plan_release(tn_plan_t* p) {
     cudaFree(p->d_open);
     cudaFree(p->d_status);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& e : p->prof_events) cudaEventDestroy(e);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (cur >= 0) cudaSetDevice(cur);
   }
@@ -467,23 +468,36 @@ extern "C" int tn_profile_slices(tn_plan_t* plan, tn_range r, tn_head_t* head, v
   for (int64_t i = 0; i < ns; ++i) step_ms[i] = 0.0;
   if (r.begin == r.end) return TN_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  std::vector<cudaEvent_t> ev(2 * ns);
-  for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
-  int status = TN_OK;
+  // events for up to kBatch passes, recorded back to back and read after one
+  // synchronisation per batch (no host round trip between the passes of a batch)
+  constexpr int64_t kBatch = 64;
   const int64_t ni = 1LL << plan->P.n_internal;
-  for (int64_t q = r.begin * ni; q < r.end * ni && status == TN_OK; ++q) {
-    const int64_t s = (q / ni) | ((q % ni) << plan->P.n_sliced);
-    status = run_pass(plan, s, head->H, st, ev.data());
-    if (status) break;
-    cudaError_t e = cudaEventSynchronize(ev[2 * ns - 1]);
-    if (e != cudaSuccess) { status = fail(TN_ERR_CUDA, cudaGetErrorString(e)); break; }
-    for (int64_t i = 0; i < ns; ++i) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
-      step_ms[i] += ms;
-    }
+  const int64_t npass = (r.end - r.begin) * ni;
+  const size_t need = (size_t)(2 * ns * std::min(npass, kBatch));
+  auto& ev = plan->prof_events;
+  while (ev.size() < need) {
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreate(&e));
+    ev.push_back(e);
   }
-  for (auto& e : ev) cudaEventDestroy(e);
+  int status = TN_OK;
+  for (int64_t q0 = 0; q0 < npass && status == TN_OK; q0 += kBatch) {
+    const int64_t nb = std::min(kBatch, npass - q0);
+    for (int64_t j = 0; j < nb && status == TN_OK; ++j) {
+      const int64_t q = r.begin * ni + q0 + j;
+      const int64_t s = (q / ni) | ((q % ni) << plan->P.n_sliced);
+      status = run_pass(plan, s, head->H, st, ev.data() + 2 * ns * j);
+    }
+    if (status) break;
+    cudaError_t e = cudaEventSynchronize(ev[(size_t)(2 * ns * nb - 1)]);
+    if (e != cudaSuccess) { status = fail(TN_ERR_CUDA, cudaGetErrorString(e)); break; }
+    for (int64_t j = 0; j < nb; ++j)
+      for (int64_t i = 0; i < ns; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[(size_t)(2 * ns * j + 2 * i)], ev[(size_t)(2 * ns * j + 2 * i + 1)]);
+        step_ms[i] += ms;
+      }
+  }
   if (status == TN_OK) mark_done(head, r);
   return status;
 }

@@ -19,10 +19,11 @@
 // nearest, so a long K loop accumulated in place drifts (the error grows
 // linearly with K; see Ootomo and Yokota, "Recovering single precision
 // accuracy from Tensor Cores while surpassing the FP32 theoretical peak
-// performance", 2022).  The K loop is therefore cut into chunks -- one k-block
-// (two ping-pong TMEM buffers) for BN <= 128, two k-blocks (one buffer) for
-// BN = 256 -- each accumulated from zero in TMEM and folded by eight drain
-// warps into a TMEM running sum with ordinary FP32 adds.
+// performance", 2022).  The K loop is therefore cut into chunks of one k-block,
+// each accumulated from zero in one of two ping-pong TMEM buffers (2 x BN <= 512
+// columns) and folded by eight drain warps into a running sum held in their
+// registers with ordinary round-to-nearest FP32 adds, while the MMAs of the
+// next chunk fill the other buffer.
 //
 // Roles (320 threads): warps 0-7 drain chunk accumulators into the running sum
 // and write the tile out (two warps per TMEM lane quarter, half the columns
@@ -161,12 +162,8 @@ struct Layout {
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // A hi, A lo, B hi, B lo
   static constexpr int DATA = STAGES * STAGE;
   static constexpr int TOTAL = DATA + 1024 /*align*/ + 256 /*barriers*/;
-  static constexpr uint32_t TMEM_COLS = 512;
-  // BN <= 128: two chunk buffers (ping-pong) + the running sum; BN = 256: one
-  // chunk buffer + the running sum, chunks of two k-blocks
-  static constexpr bool PINGPONG = BN <= 128;
-  static constexpr int CH = PINGPONG ? 1 : 2;
-  static constexpr uint32_t SUM_COL = PINGPONG ? 2 * BN : BN;
+  // two chunk buffers of BN fp32 columns (ping-pong), a power of two >= 32
+  static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
 };
 
 // Tile order: groups of GROUP_M m-tiles; inside a group n-tiles and (when A is
@@ -261,14 +258,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       const uint32_t idesc = idesc_mma<BN, FMT>();
       for (int kb = 0; kb < nkb; ++kb) {
-        // chunk c (CH k-blocks) accumulates in TMEM buffer b from zero
+        // k-block kb accumulates in TMEM buffer b = kb & 1 from zero
         const int s = kb % STAGES, r = kb / STAGES;
-        const int c = kb / Lay::CH;
-        const int b = Lay::PINGPONG ? (c & 1) : 0;
-        const int u = Lay::PINGPONG ? (c >> 1) : c;   // use index of buffer b
-        const bool first = (kb % Lay::CH) == 0;
-        const bool last = (kb % Lay::CH) == Lay::CH - 1 || kb == nkb - 1;
-        if (first && !mbar_wait(&acce[b], (uint32_t)((u & 1) ^ 1), abort_flag)) break;
+        const int b = kb & 1, u = kb >> 1;   // u: use index of buffer b
+        if (!mbar_wait(&acce[b], (uint32_t)((u & 1) ^ 1), abort_flag)) break;
         if (!mbar_wait(&full[s], (uint32_t)(r & 1), abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t d = tmem + (uint32_t)(b * BN);
@@ -280,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const uint32_t o = kk * 32;  // one MMA's K = 32 bytes of each operand row
-          mma<H16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
+          mma<H16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, kk == 0 ? 0u : 1u);
           mma<H16>(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
         }
 #pragma unroll
@@ -289,86 +282,64 @@ __global__ void __launch_bounds__(kThreads, 1)
           mma<H16>(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
         }
         mma_commit(&empty[s]);
-        if (last) mma_commit(&accf[b]);
+        mma_commit(&accf[b]);
       }
     }
   } else {
-    // drain warps 0-7: TMEM lane quarter = warp % 4, column half = warp / 4.
-    // Each warp handles its columns in rounds of up to 4 pieces of 16 columns,
-    // issuing a round's TMEM loads before one wait.
-    constexpr int NPIECE = BN >= 32 ? BN / 32 : 1;   // 16-column pieces per warp
-    constexpr int RP = NPIECE < 4 ? NPIECE : 4;        // pieces per round
+    // drain warps 0-7: TMEM lane quarter = warp % 4, column half = warp / 4;
+    // each thread keeps the running sum of its row's NCOL columns in registers.
+    constexpr int NCOL = BN >= 32 ? BN / 2 : BN;     // columns per warp
+    constexpr int NPIECE = NCOL / 16;                  // 16-column TMEM loads
+    constexpr int RPMAX = BN >= 256 ? 2 : 4;           // loads in flight per wait
+    constexpr int RP = NPIECE < RPMAX ? NPIECE : RPMAX;
     const int q = warp & 3, half = warp >> 2;
     const bool active = BN >= 32 || half == 0;
-    const int col0 = BN >= 32 ? half * (BN / 2) : 0;
+    const int col0 = BN >= 32 ? half * NCOL : 0;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    const uint32_t sum_col = Lay::SUM_COL;
-    const int nch = (nkb + Lay::CH - 1) / Lay::CH;
+    float acc[NCOL];
+#pragma unroll
+    for (int e = 0; e < NCOL; ++e) acc[e] = 0.0f;
     bool ok = true;
-    for (int c = 0; c < nch && ok; ++c) {
-      const int b = Lay::PINGPONG ? (c & 1) : 0;
-      const int u = Lay::PINGPONG ? (c >> 1) : c;
+    for (int c = 0; c < nkb && ok; ++c) {
+      const int b = c & 1, u = c >> 1;
       ok = mbar_wait(&accf[b], (uint32_t)(u & 1), abort_flag);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      if (nch > 1 && active) {
-#pragma unroll 1
-        for (int p0 = 0; p0 < NPIECE; p0 += RP) {
-          uint32_t v[RP][16], w[RP][16];
+      if (active) {
 #pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            const uint32_t col = (uint32_t)(col0 + 16 * (p0 + j));
-            tmem_ld16(tmem + lane_base + (uint32_t)(b * BN) + col, v[j]);
-            if (c > 0) tmem_ld16(tmem + lane_base + sum_col + col, w[j]);
-          }
+        for (int p0 = 0; p0 < NPIECE; p0 += RP) {
+          uint32_t v[RP][16];
+#pragma unroll
+          for (int j = 0; j < RP; ++j)
+            tmem_ld16(tmem + lane_base + (uint32_t)(b * BN) + (uint32_t)(col0 + 16 * (p0 + j)), v[j]);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            if (c > 0) {
+          for (int j = 0; j < RP; ++j)
 #pragma unroll
-              for (int e = 0; e < 16; ++e)
-                v[j][e] = __float_as_uint(__uint_as_float(v[j][e]) + __uint_as_float(w[j][e]));
-            }
-            tmem_st16(tmem + lane_base + sum_col + (uint32_t)(col0 + 16 * (p0 + j)), v[j]);
-          }
+            for (int e = 0; e < 16; ++e) acc[16 * (p0 + j) + e] += __uint_as_float(v[j][e]);
         }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       mbar_arrive(&acce[b]);
     }
     if (ok && active) {
-      // write this warp's columns: from the running sum, or straight from buffer 0 for one chunk
-      const uint32_t src = nch > 1 ? sum_col : 0u;
       const int64_t row = tm * BM + q * 32 + lane;
-      float* crow = C + (pc * M + row) * N2;
-#pragma unroll 1
-      for (int p0 = 0; p0 < NPIECE; p0 += RP) {
-        uint32_t v[RP][16];
+      if (row < M) {
+        float* crow = C + (pc * M + row) * N2;
 #pragma unroll
-        for (int j = 0; j < RP; ++j) tmem_ld16(tmem + lane_base + src + (uint32_t)(col0 + 16 * (p0 + j)), v[j]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (FMT == 2) {
+        for (int pp = 0; pp < NPIECE; ++pp) {
+          float w[16];
 #pragma unroll
-          for (int j = 0; j < RP; ++j)
+          for (int e = 0; e < 16; ++e) w[e] = FMT == 2 ? acc[16 * pp + e] * kFp16Unscale : acc[16 * pp + e];
+          const int64_t col = tn_ * BN + col0 + 16 * pp;
+          if (col + 16 <= N2) {
+            float4* dst = (float4*)(crow + col);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) v[j][e] = __float_as_uint(__uint_as_float(v[j][e]) * kFp16Unscale);
-        }
-        if (row < M) {
+            for (int e = 0; e < 4; ++e) dst[e] = make_float4(w[4 * e], w[4 * e + 1], w[4 * e + 2], w[4 * e + 3]);
+          } else {
 #pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            const int64_t col = tn_ * BN + col0 + 16 * (p0 + j);
-            if (col + 16 <= N2) {
-              float4* dst = (float4*)(crow + col);
-#pragma unroll
-              for (int e = 0; e < 4; ++e)
-                dst[e] = make_float4(__uint_as_float(v[j][4 * e]), __uint_as_float(v[j][4 * e + 1]),
-                                     __uint_as_float(v[j][4 * e + 2]), __uint_as_float(v[j][4 * e + 3]));
-            } else {
-#pragma unroll
-              for (int e = 0; e < 16; ++e)
-                if (col + e < N2) crow[col + e] = __uint_as_float(v[j][e]);
-            }
+            for (int e = 0; e < 16; ++e)
+              if (col + e < N2) crow[col + e] = w[e];
           }
         }
       }

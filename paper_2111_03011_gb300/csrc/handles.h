@@ -34,6 +34,7 @@ struct tn_plan {
   double measured_slice_ms = 0.0;
   int autotune_candidates = 0;
   std::vector<GraphEntry> graphs;     // captured slice ranges (tn_contract_slices_graph)
+  std::vector<cudaEvent_t> prof_events;   // tn_profile_slices: reused timing events
   cudaStream_t cap_stream = nullptr;
   bool on_device = false;
   int device = -1;
