@@ -51,6 +51,15 @@ def _workload(name):
         return ci.config_tiny()
     if name == "grid25":
         return ci.config_grid25()
+    if name == "syc53":
+        # 53-qubit Sycamore topology at reduced depth (8 cycles): 6 open qubits x
+        # 1024 tails; automatic slicing to a 2^30-element cap, so the one slice
+        # runs as 2^n_internal passes
+        circ = ci.make_sycamore_circuit(8, seed=5)
+        n = circ.n_qubits
+        oq = list(range(n - 6, n))
+        return dict(circuit=circ, open_qubits=oq, tails=ci.draw_tails(n, oq, 1024, seed=55), edges=[],
+                    name="sycamore53_m8_open6_L1024", plan_opts=dict(max_log2_elements=30, auto_slice=16))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -139,13 +148,14 @@ def run_ours(args):
     gemm = {"tc": tn.TN_GEMM_TC_3XTF32, "simt": tn.TN_GEMM_SIMT_FP32, "bf16": tn.TN_GEMM_TC_BF16X3,
             "fp16": tn.TN_GEMM_TC_FP16X3}[args.engine]
     t0 = time.time()
+    popts = cfg.get("plan_opts", {})
     if args.autotune > 0:
         plan = tn.tn_plan_autotune(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"],
                                    n_candidates=args.autotune, gemm=gemm,
-                                   order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0)
+                                   order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0, **popts)
     else:
         plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=gemm,
-                          order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0)
+                          order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0, **popts)
     plan_s = time.time() - t0
     st = tn.tn_plan_get_stats(plan)
     k = st["n_sliced"]
@@ -280,6 +290,7 @@ def run_ours(args):
         "data": "synthetic (seeded Sycamore-like circuit; paper's circuit files not used)",
         "config": {"workload": cfg["name"], "qubits": st["n_qubits"], "cycles": cfg["circuit"].cycles,
                    "open_qubits": h, "groups": L, "amplitudes": n_amp, "sliced_edges": k, "slices": n_slices,
+                   "internal_sliced_edges": int(st["n_internal_sliced"]), "passes_per_slice": n_pass,
                    "max_log2_elements": round(st["max_log2_elements"], 2), "gemm_engine": args.engine,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "flushed between timed steps (512 MiB write); intermediates up to 2 GiB exceed L2",
@@ -288,6 +299,7 @@ def run_ours(args):
                    "partial_slices_for_profiling": bool(args.slices)},
         "amplitudes_per_s": round(ws * n_amp / (ms * 1e-3), 1),
         "slices_per_s": round(ws * n_slices / (ms * 1e-3), 2),
+        "ms_per_pass": round(ms / (n_slices * n_pass), 3),
         "tc_macs_per_slice": st["tc_macs"],
         "alg_bytes_per_slice": st["alg_bytes"],
         "e2e": {"value": round(e2e, 3), "unit": "TFLOP/s", "ms_per_step": round(ms_e2e, 3),
@@ -390,6 +402,101 @@ def run_serve(args):
                       "sizes": "amplitude batches 1e3-1e5 (log-uniform), samples 1e2-1e4"},
            "tc_3xtf32": results["tc"], "plain_c64_simt": results["simt"],
            "p99_vs_plain_c64": round(results["tc"]["p99_ms"] / results["simt"]["p99_ms"], 3)}
+    print(json.dumps(out), flush=True)
+
+
+def run_torch(args):
+    """Comparison arm, not the product: the same plan (leaves, order, sparse-
+    state pattern maps from tn_plan_describe) contracted with stock PyTorch
+    complex64 einsum on the GPU -- the software approach of the paper's own
+    runs -- timed like the main arm (64 slices per step)."""
+    import string
+
+    import torch
+
+    import paper_2111_03011_gb300 as tn
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    cfg = _workload(args.workload)
+    popts = cfg.get("plan_opts", {})
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True,
+                      order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0, order_seed=1, **popts)
+    st = tn.tn_plan_get_stats(plan)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    tm = [int(t) & d["tail_mask"] for t in cfg["tails"]]
+    L, h = len(tm), len(cfg["open_qubits"])
+
+    def pats(tq):
+        return sorted(set(t & tq for t in tm))
+
+    leaves, vbits = [], []
+    for lf in d["leaves"]:
+        arr = (np.array(lf["re"]) + 1j * np.array(lf["im"])).astype(np.complex64)
+        leaves.append(torch.from_numpy(arr.reshape(1 << len(lf["var_slice_bits"]), lf["P"], -1)).to(dev))
+        vbits.append(lf["var_slice_bits"])
+    vts = d["vts"]
+    seen, ops = set(), []
+    for stp in d["steps"]:
+        if stp["contraction"] in seen:
+            continue
+        seen.add(stp["contraction"])
+        a, b, c = stp["vt_a"], stp["vt_b"], stp["vt_c"]
+        la, lb, lc = vts[a]["legs"], vts[b]["legs"], vts[c]["legs"]
+        pa, pb, pc = pats(vts[a]["tq"]), pats(vts[b]["tq"]), pats(vts[c]["tq"])
+        mA = [pa.index(x & vts[a]["tq"]) for x in pc]
+        mB = [pb.index(x & vts[b]["tq"]) for x in pc]
+        letter = {}
+        for l in la + lb:
+            letter.setdefault(l, string.ascii_letters[len(letter)])
+        eq = ("Z" + "".join(letter[l] for l in reversed(la)) + ",Z" + "".join(letter[l] for l in reversed(lb)) +
+              "->Z" + "".join(letter[l] for l in reversed(lc)))
+        ops.append((a, b, c, None if mA == list(range(len(pa))) else torch.tensor(mA, device=dev),
+                    None if mB == list(range(len(pb))) else torch.tensor(mB, device=dev), eq,
+                    [len(pc)] + [2] * len(la), [len(pc)] + [2] * len(lb), len(pc)))
+    fin = d["final"]
+    fp = pats(d["tail_mask"])
+    rowidx = torch.tensor([fp.index(t) for t in tm], device=dev)
+    colidx = torch.tensor([sum(1 << fin["open_pos"][j] for j in range(h) if (mu >> j) & 1) for mu in range(1 << h)],
+                          device=dev)
+    H = torch.zeros(L, 1 << h, dtype=torch.complex128, device=dev)
+    k, ni = st["n_sliced"], st["n_internal_sliced"]
+    n_slices = min(1 << k, args.slices) if args.slices else 1 << k
+
+    def one_pass(s):
+        T = {}
+        for i, vb in enumerate(vbits):
+            T[i] = leaves[i][sum(((s >> bit) & 1) << t for t, bit in enumerate(vb))]
+        for (a, b, c, mA, mB, eq, sa, sb, pc) in ops:
+            A = T.pop(a)
+            B = T.pop(b)
+            A = A if mA is None else A.index_select(0, mA)
+            B = B if mB is None else B.index_select(0, mB)
+            T[c] = torch.einsum(eq, A.reshape(sa), B.reshape(sb)).reshape(pc, -1)
+        H.add_(T[fin["vt"]].index_select(0, rowidx).index_select(1, colidx).to(torch.complex128))
+
+    def step():
+        H.zero_()
+        for s in range(n_slices):
+            for t in range(1 << ni):
+                one_pass(s | (t << k))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    out = {"metric": "slice TFLOP/s", "value": round(8.0 * st["tc_macs"] * n_slices / (ms * 1e-3) / 1e12, 3),
+           "unit": "TFLOP/s", "engine": "pytorch complex64 einsum (comparison arm, not the product)",
+           "torch": torch.__version__, "allow_tf32": bool(torch.backends.cuda.matmul.allow_tf32),
+           "ms_per_step": round(ms, 2), "steps": args.steps, "warmup": args.warmup,
+           "config": {"workload": cfg["name"], "slices": n_slices, "order": "the planner's seed-1 order"}}
     print(json.dumps(out), flush=True)
 
 
@@ -499,9 +606,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sliced30", choices=["sliced30", "tiny", "grid25", "serve", "batch"])
+    ap.add_argument("--workload", default="sliced30",
+                    choices=["sliced30", "tiny", "grid25", "syc53", "serve", "batch"])
     ap.add_argument("--circuits", type=int, default=256, help="batch workload: number of circuits")
-    ap.add_argument("--engine", default="fp16", choices=["tc", "simt", "bf16", "fp16"],
+    ap.add_argument("--engine", default="fp16", choices=["tc", "simt", "bf16", "fp16", "torch"],
                     help="GEMM-step engine: fp16 = FP16x3 (complex64 accuracy, default), tc = 3xTF32, "
                          "bf16 = BF16x3 (1e-4), simt = plain complex64 on CUDA cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -520,6 +628,8 @@ def main():
         run_serve(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.engine == "torch":
+        run_torch(args)
     else:
         run_ours(args)
 

@@ -276,3 +276,18 @@ def test_fp16_engine_scale_bound_and_unitarity_check(tn):
         tn.tn_plan(bad, oq, tails, host_only=True, gemm=tn.TN_GEMM_TC_FP16X3)
     assert e.value.code == tn.TN_ERR_INVALID
     tn.tn_plan(bad, oq, tails, host_only=True, gemm=tn.TN_GEMM_TC_3XTF32)
+
+
+def test_sycamore53_topology_replay_matches_oracle(tn):
+    """53-qubit Sycamore-topology circuit at 6 cycles (reduced depth): the
+    replayed plan equals the O2 network oracle on two groups."""
+    circ = ci.make_sycamore_circuit(6, seed=5)
+    n = circ.n_qubits
+    assert n == 53
+    oq = list(range(n - 6, n))
+    tails = ci.draw_tails(n, oq, 8, seed=55)
+    plan = tn.tn_plan(circ, oq, tails, host_only=True, max_log2_elements=24, auto_slice=8)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    H = emulate(d, tails, oq, [t << d["n_sliced"] for t in range(1 << d["n_internal"])])
+    ref = O.network_amplitudes(circ, oq, tails, [], groups=[0, 5])
+    assert np.abs(H[[0, 5]] - ref).max() <= 1e-10 * np.abs(ref).max()
