@@ -547,3 +547,36 @@ def test_automatic_slicing_parity_f_est_profile_and_graph(tn, gemm):
     ms = tn.tn_profile_slices(plan, 0, 4, h2)
     assert ms.shape == (st["n_launches"] >> st["n_internal_sliced"],) and (ms > 0).all()
     assert_close(read_head(tn, plan, h2, cfg), oracle_head(cfg), tol)
+
+
+def _sycamore_case(cycles, n_tails):
+    circ = ci.make_sycamore_circuit(cycles, seed=5)
+    n = circ.n_qubits
+    oq = list(range(n - 6, n))
+    return circ, oq, ci.draw_tails(n, oq, n_tails, seed=55)
+
+
+@pytest.mark.parametrize("gemm", [1, 4], ids=["tc3xtf32", "fp16x3"])
+def test_sycamore53_reduced_depth_parity(tn, gemm):
+    """53-qubit Sycamore topology (reduced depth): 6 cycles against O2 live,
+    8 cycles (auto-sliced to a 2^28 cap) against stored O2 amplitudes written
+    by tests/golden/make_sycamore53_golden.py."""
+    import os
+    circ, oq, tails = _sycamore_case(6, 8)
+    plan = tn.tn_plan(circ, oq, tails, [], gemm=gemm)
+    head = tn.tn_head_create(plan)
+    tn.tn_contract_slices(plan, 0, 1, head)
+    cfg = dict(circuit=circ, open_qubits=oq, tails=tails, edges=[])
+    H = read_head(tn, plan, head, cfg)
+    assert_close(H[[0, 5]], O.network_amplitudes(circ, oq, tails, [], groups=[0, 5]))
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "sycamore53_m8_o2.npz"))
+    circ, oq, tails = _sycamore_case(int(g["cycles"]), len(g["tails"]))
+    assert np.array_equal(np.asarray(tails, dtype=np.uint64), g["tails"])
+    plan = tn.tn_plan(circ, oq, tails, [], gemm=gemm, max_log2_elements=28, auto_slice=12)
+    st = tn.tn_plan_get_stats(plan)
+    assert st["n_internal_sliced"] >= 1
+    head = tn.tn_head_create(plan)
+    tn.tn_contract_slices_graph(plan, 0, 1, head)
+    H = read_head(tn, plan, head, dict(circuit=circ, open_qubits=oq, tails=tails, edges=[]))
+    assert_close(H[list(g["groups"])], g["H"])
+    assert tn.tn_head_fidelity(head) == (1.0, 1)
