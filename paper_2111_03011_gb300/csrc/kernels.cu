@@ -148,42 +148,73 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
   const uint64_t nrest_mask = (1ULL << p.n_rest) - 1;
   const uint64_t total_tiles = (uint64_t)p.P << p.n_rest;
   float2* __restrict__ out_lo = p.out + p.P * p.pstride;
-  for (uint64_t blk = blockIdx.x; blk < total_tiles; blk += gridDim.x) {
+  // Software pipeline: the global loads of the next tile are issued into
+  // registers before the current tile is written out, so reads and writes of
+  // consecutive tiles overlap.  A tile has at most 1024 elements: <= 4 per thread.
+  auto tile_base = [&](uint64_t blk, const float2*& src, int64_t& dofs) {
     const uint64_t pp = blk >> p.n_rest, b = blk & nrest_mask;
     const uint64_t bi = r_in[b & 255] | r_in[256 + ((b >> 8) & 255)] | r_in[512 + ((b >> 16) & 255)] |
                         r_in[768 + ((b >> 24) & 255)];
     const uint64_t bo = r_out[b & 255] | r_out[256 + ((b >> 8) & 255)] | r_out[512 + ((b >> 16) & 255)] |
                         r_out[768 + ((b >> 24) & 255)];
-    const float2* __restrict__ src = p.in + pp * p.pstride + bi;
-    const int64_t dofs = (int64_t)(pp * p.pstride + bo);
+    src = p.in + pp * p.pstride + bi;
+    dofs = (int64_t)(pp * p.pstride + bo);
+  };
+  float2 nxt[4];
+  uint64_t blk = blockIdx.x;
+  const float2* src = nullptr;
+  int64_t dofs = 0;
+  if (blk < total_tiles) {
+    tile_base(blk, src, dofs);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = threadIdx.x + c * 256;
+      if (i < nt) nxt[c] = __ldg(src + s_in[i]);
+    }
+  }
+  for (; blk < total_tiles; blk += gridDim.x) {
+    const int64_t cur_dofs = dofs;
+    __syncthreads();   // the previous tile's reads of `tile` are done
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = threadIdx.x + c * 256;
+      if (i < nt) tile[pad32(i)] = nxt[c];
+    }
     __syncthreads();
-#pragma unroll 4
-    for (int i = threadIdx.x; i < nt; i += blockDim.x) tile[pad32(i)] = __ldg(src + s_in[i]);
-    __syncthreads();
+    const uint64_t nb = blk + gridDim.x;
+    if (nb < total_tiles) {
+      tile_base(nb, src, dofs);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = threadIdx.x + c * 256;
+        if (i < nt) nxt[c] = __ldg(src + s_in[i]);
+      }
+    }
 #pragma unroll 4
     for (int j = threadIdx.x; j < nt; j += blockDim.x) {
       const float2 v = tile[s_slot[j]];
+      const int64_t o = cur_dofs + s_out[j];
       if (SPLIT == 1) {
         const float2 h = make_float2(tf32_rn(v.x), tf32_rn(v.y));
-        p.out[dofs + s_out[j]] = h;
-        out_lo[dofs + s_out[j]] = make_float2(v.x - h.x, v.y - h.y);
+        p.out[o] = h;
+        out_lo[o] = make_float2(v.x - h.x, v.y - h.y);
       } else if (SPLIT == 3) {
         __half2* fh = (__half2*)p.out;
         __half2* fl = fh + p.P * p.pstride;
         const float2 w = make_float2(v.x * kFp16Scale, v.y * kFp16Scale);
         const __half2 h = __floats2half2_rn(w.x, w.y);
         const float2 hf = __half22float2(h);
-        fh[dofs + s_out[j]] = h;
-        fl[dofs + s_out[j]] = __floats2half2_rn(w.x - hf.x, w.y - hf.y);
+        fh[o] = h;
+        fl[o] = __floats2half2_rn(w.x - hf.x, w.y - hf.y);
       } else if (SPLIT == 2) {
         __nv_bfloat162* bh = (__nv_bfloat162*)p.out;
         __nv_bfloat162* bl = bh + p.P * p.pstride;
         const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
         const float2 hf = __bfloat1622float2(h);
-        bh[dofs + s_out[j]] = h;
-        bl[dofs + s_out[j]] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+        bh[o] = h;
+        bl[o] = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
       } else {
-        p.out[dofs + s_out[j]] = v;
+        p.out[o] = v;
       }
     }
   }
@@ -215,69 +246,65 @@ __global__ void k_bprep_c(BPrepParams p) {
   }
 }
 
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
 // Real embedding of B for C_r = A_r B_r with interleaved complex rows:
 // Bt[j][i] (j = 2n + jc output column, i = 2k + ic reduction index) is
-// [[re, -im], [im, re]] in (jc, ic); stored K-major, split into tf32 hi + lo
-// planes.
+// [[re, -im], [im, re]] in (jc, ic); stored K-major as hi and lo planes in the
+// GEMM engine's operand format (FMT 0: tf32-rounded fp32 hi + fp32 remainder;
+// 1: bf16 hi + bf16 remainder; 2: fp16 of the value times kFp16Scale).  One
+// thread per complex element of B: it writes the element's 2 x 2 block as two
+// pairs of adjacent reals (rows 2n and 2n + 1) in each plane; consecutive
+// threads take consecutive k, so every row segment is written contiguously.
+template <int FMT>
+struct Pair;
+template <>
+struct Pair<0> {
+  using T = float2;
+  static __device__ __forceinline__ void split(float a, float b, T& h, T& l) {
+    h = make_float2(tf32_rn(a), tf32_rn(b));
+    l = make_float2(a - h.x, b - h.y);
+  }
+};
+template <>
+struct Pair<1> {
+  using T = __nv_bfloat162;
+  static __device__ __forceinline__ void split(float a, float b, T& h, T& l) {
+    h = __floats2bfloat162_rn(a, b);
+    const float2 f = __bfloat1622float2(h);
+    l = __floats2bfloat162_rn(a - f.x, b - f.y);
+  }
+};
+template <>
+struct Pair<2> {
+  using T = __half2;
+  static __device__ __forceinline__ void split(float a, float b, T& h, T& l) {
+    a *= kFp16Scale;
+    b *= kFp16Scale;
+    h = __floats2half2_rn(a, b);
+    const float2 f = __half22float2(h);
+    l = __floats2half2_rn(a - f.x, b - f.y);
+  }
+};
+
+template <int FMT>
 __global__ void k_bprep_tc(BPrepParams p) {
-  const int64_t K2 = 2LL << p.nk, N2 = 2LL << p.nn;
-  const int64_t per = K2 * N2;
+  using T = typename Pair<FMT>::T;
+  const int64_t K = 1LL << p.nk, N = 1LL << p.nn;
+  const int64_t per = K * N;                  // complex elements per pattern
   const int64_t total = p.PB * per;
-  float* hi = (float*)p.out;
-  float* lo = hi + total;
+  T* hi = (T*)p.out;                          // pairs: [PB][2N][K] pairs of reals
+  T* lo = hi + 2 * total;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pb = e / per, r = e % per;
-    const int64_t j = r / K2, i = r % K2;
-    const float2 b = p.B[pb * p.b_pstride + p.bk[i >> 1] + p.bn[j >> 1]];
-    const int jc = (int)(j & 1), ic = (int)(i & 1);
-    const float v = jc == 0 ? (ic == 0 ? b.x : -b.y) : (ic == 0 ? b.y : b.x);
-    const float h = tf32_round(v);
-    hi[e] = h;
-    lo[e] = v - h;
-  }
-}
-
-// The same embedding as bf16 hi/lo planes for the bf16 engine.
-__global__ void k_bprep_tc_bf16(BPrepParams p) {
-  const int64_t K2 = 2LL << p.nk, N2 = 2LL << p.nn;
-  const int64_t per = K2 * N2;
-  const int64_t total = p.PB * per;
-  __nv_bfloat16* hi = (__nv_bfloat16*)p.out;
-  __nv_bfloat16* lo = hi + total;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pb = e / per, r = e % per;
-    const int64_t j = r / K2, i = r % K2;
-    const float2 b = p.B[pb * p.b_pstride + p.bk[i >> 1] + p.bn[j >> 1]];
-    const int jc = (int)(j & 1), ic = (int)(i & 1);
-    const float v = jc == 0 ? (ic == 0 ? b.x : -b.y) : (ic == 0 ? b.y : b.x);
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[e] = h;
-    lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
-  }
-}
-
-// The same embedding as fp16 hi/lo planes of the value times kFp16Scale.
-__global__ void k_bprep_tc_fp16(BPrepParams p) {
-  const int64_t K2 = 2LL << p.nk, N2 = 2LL << p.nn;
-  const int64_t per = K2 * N2;
-  const int64_t total = p.PB * per;
-  __half* hi = (__half*)p.out;
-  __half* lo = hi + total;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pb = e / per, r = e % per;
-    const int64_t j = r / K2, i = r % K2;
-    const float2 b = p.B[pb * p.b_pstride + p.bk[i >> 1] + p.bn[j >> 1]];
-    const int jc = (int)(j & 1), ic = (int)(i & 1);
-    const float v = (jc == 0 ? (ic == 0 ? b.x : -b.y) : (ic == 0 ? b.y : b.x)) * kFp16Scale;
-    const __half h = __float2half_rn(v);
-    hi[e] = h;
-    lo[e] = __float2half_rn(v - __half2float(h));
+    const int64_t pb = e / per, r = e - pb * per;
+    const int64_t n = r >> p.nk, k = r & (K - 1);
+    const float2 b = p.B[pb * p.b_pstride + p.bk[k] + p.bn[n]];
+    const int64_t o0 = (pb * 2 * N + 2 * n) * K + k;   // pair (2k, 2k+1) of row 2n
+    T h, l;
+    Pair<FMT>::split(b.x, -b.y, h, l);
+    hi[o0] = h;
+    lo[o0] = l;
+    Pair<FMT>::split(b.y, b.x, h, l);
+    hi[o0 + K] = h;                                    // row 2n + 1
+    lo[o0 + K] = l;
   }
 }
 
@@ -289,11 +316,11 @@ cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s) {
 }
 
 cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s) {
-  const int64_t total = p.PB << (p.nk + p.nn + 2);
-  const int64_t grid = std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 8);
-  if (p.h16 == 2) k_bprep_tc_fp16<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
-  else if (p.h16 == 1) k_bprep_tc_bf16<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
-  else k_bprep_tc<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(p);
+  const int64_t total = p.PB << (p.nk + p.nn);
+  const unsigned grid = (unsigned)std::max<int64_t>(std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 16), 1);
+  if (p.h16 == 2) k_bprep_tc<2><<<grid, 256, 0, s>>>(p);
+  else if (p.h16 == 1) k_bprep_tc<1><<<grid, 256, 0, s>>>(p);
+  else k_bprep_tc<0><<<grid, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 
