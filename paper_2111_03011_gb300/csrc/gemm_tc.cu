@@ -43,7 +43,13 @@ namespace tn {
 namespace tc {
 
 constexpr int BM = 128;
-constexpr int BK_BYTES = 128;           // one 128-byte swizzle row of K per k-block
+// K per k-block (one pipeline stage): 64 bytes of each operand row, stored with
+// the 64-byte swizzle, so that a stage is small enough for 4-8 stages to be in
+// flight.  A chunk (one fresh TMEM accumulation) spans CH = 2 k-blocks, i.e.
+// 128 bytes of K: 32 real terms (tf32) or 64 (bf16, fp16).
+constexpr int BK_BYTES = 64;
+constexpr int CH = 128 / BK_BYTES;
+constexpr int KK = BK_BYTES / 32;         // MMAs per product per k-block (32 bytes of K each)
 constexpr int kThreads = 320;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -93,14 +99,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+// UMMA shared-memory descriptor: K-major, BK_BYTES-byte swizzle (128 or 64),
+// 8-row groups 8 * BK_BYTES bytes apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-  d |= (uint64_t)1 << 46;                 // descriptor version
-  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((8 * BK_BYTES) >> 4) << 32;      // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)(BK_BYTES == 128 ? 2 : 4) << 61;  // SWIZZLE_128B : SWIZZLE_64B
   return d;
 }
 
@@ -157,11 +164,13 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 template <int BN, int STAGES>
 struct Layout {
-  static constexpr int A_BYTES = BM * BK_BYTES;        // one 128-row tile, 128 bytes of K per row
+  static constexpr int A_BYTES = BM * BK_BYTES;        // one 128-row tile, BK_BYTES of K per row
   static constexpr int B_BYTES = BN * BK_BYTES;        // one BN-row tile
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // A hi, A lo, B hi, B lo
   static constexpr int DATA = STAGES * STAGE;
   static constexpr int TOTAL = DATA + 1024 /*align*/ + 256 /*barriers*/;
+  static_assert(TOTAL <= 232448, "shared memory per CTA");
+  static_assert(2 * STAGES + 6 <= 32, "barrier area");
   // two chunk buffers of BN fp32 columns (ping-pong), a power of two >= 32
   static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
 };
@@ -215,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t pa = mapA_mode == 0 ? pc : (mapA_mode == 1 ? 0 : (int64_t)mapA[pc]);
   const int64_t pb = mapB_mode == 0 ? pc : (mapB_mode == 1 ? 0 : (int64_t)mapB[pc]);
   constexpr bool H16 = FMT != 0;
-  constexpr int BKE = H16 ? 64 : 32;      // K elements per k-block
+  constexpr int BKE = BK_BYTES / (H16 ? 2 : 4);   // K elements per k-block
   const int nkb = (int)((K2 + BKE - 1) / BKE);
 
   if (threadIdx.x == 0) {
@@ -258,10 +267,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       const uint32_t idesc = idesc_mma<BN, FMT>();
       for (int kb = 0; kb < nkb; ++kb) {
-        // k-block kb accumulates in TMEM buffer b = kb & 1 from zero
+        // chunk c = kb / CH accumulates in TMEM buffer b = c & 1 from zero
         const int s = kb % STAGES, r = kb / STAGES;
-        const int b = kb & 1, u = kb >> 1;   // u: use index of buffer b
-        if (!mbar_wait(&acce[b], (uint32_t)((u & 1) ^ 1), abort_flag)) break;
+        const int c = kb / CH, b = c & 1, u = c >> 1;   // u: use index of buffer b
+        const bool first = kb % CH == 0, last = kb % CH == CH - 1 || kb == nkb - 1;
+        if (first && !mbar_wait(&acce[b], (uint32_t)((u & 1) ^ 1), abort_flag)) break;
         if (!mbar_wait(&full[s], (uint32_t)(r & 1), abort_flag)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t d = tmem + (uint32_t)(b * BN);
@@ -271,18 +281,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         // small correction products first, so that the accumulator is still
         // small while they are added; the hi x hi products come last
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
+        for (int kk = 0; kk < KK; ++kk) {
           const uint32_t o = kk * 32;  // one MMA's K = 32 bytes of each operand row
-          mma<H16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, kk == 0 ? 0u : 1u);
+          mma<H16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
           mma<H16>(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
         }
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
+        for (int kk = 0; kk < KK; ++kk) {
           const uint32_t o = kk * 32;
           mma<H16>(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
         }
         mma_commit(&empty[s]);
-        mma_commit(&accf[b]);
+        if (last) mma_commit(&accf[b]);
       }
     }
   } else {
@@ -300,7 +310,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int e = 0; e < NCOL; ++e) acc[e] = 0.0f;
     bool ok = true;
-    for (int c = 0; c < nkb && ok; ++c) {
+    const int nch = (nkb + CH - 1) / CH;
+    for (int c = 0; c < nch && ok; ++c) {
       const int b = c & 1, u = c >> 1;
       ok = mbar_wait(&accf[b], (uint32_t)(u & 1), abort_flag);
       if (!ok) break;
@@ -386,7 +397,9 @@ static bool encode3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1,
   cuuint32_t box[3] = {b0, b1, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(m, dt, 3, const_cast<void*>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   BK_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -401,7 +414,7 @@ template <int BN, int STAGES, int FMT>
 static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   using Lay = Layout<BN, STAGES>;
   const int64_t K2 = 2 * p.K, N2 = 2 * p.N;
-  const uint32_t BKE = FMT ? 64 : 32;
+  const uint32_t BKE = BK_BYTES / (FMT ? 2 : 4);
   const int64_t es = FMT ? 2 : 4;
   // A: hi plane then lo plane, each [PA][M][2K]; B: hi plane then lo plane, each [PB][2N][2K]
   const char* ahi = (const char*)p.A;
@@ -425,17 +438,17 @@ static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s
 template <int FMT>
 static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   const int64_t N2 = 2 * p.N;
-  if (N2 <= 16) return run<16, 6, FMT>(p, status, s);
-  if (N2 <= 32) return run<32, 5, FMT>(p, status, s);
-  if (N2 <= 64) return run<64, 4, FMT>(p, status, s);
-  if (N2 <= 128) return run<128, 3, FMT>(p, status, s);
-  return run<256, 2, FMT>(p, status, s);
+  if (N2 <= 16) return run<16, 8, FMT>(p, status, s);
+  if (N2 <= 32) return run<32, 8, FMT>(p, status, s);
+  if (N2 <= 64) return run<64, 8, FMT>(p, status, s);
+  if (N2 <= 128) return run<128, 6, FMT>(p, status, s);
+  return run<256, 4, FMT>(p, status, s);
 }
 
 template <int FMT>
 static cudaError_t set_attrs() {
-  const cudaError_t r[5] = {set_attr<16, 6, FMT>(), set_attr<32, 5, FMT>(), set_attr<64, 4, FMT>(),
-                            set_attr<128, 3, FMT>(), set_attr<256, 2, FMT>()};
+  const cudaError_t r[5] = {set_attr<16, 8, FMT>(), set_attr<32, 8, FMT>(), set_attr<64, 8, FMT>(),
+                            set_attr<128, 6, FMT>(), set_attr<256, 4, FMT>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
