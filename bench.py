@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 import circuit_inputs as ci  # noqa: E402
 
 KIND_NAMES = {0: "small_operand", 1: "permute", 2: "bprep_tc", 3: "gemm_tc_3xtf32", 4: "bprep_simt",
-              5: "gemm_simt_fp32", -1: "accumulate"}
+              5: "gemm_simt_fp32", 6: "operand_max", -1: "accumulate"}
 ORDER_TRIALS = 2048
 
 

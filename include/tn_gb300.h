@@ -55,7 +55,10 @@ enum { TN_C64 = 0, TN_C128 = 1 };
  * FP32-accurate (complex64 path, relative L2 <= 1e-5).  SIMT_FP32: CUDA-core
  * FP32 (the plain complex64 reference engine).  TC_BF16X3: tcgen05 kind::f16,
  * bf16 hi/lo split with FP32 accumulation, relative L2 <= 1e-4 (a precision
- * form with twice the tensor rate). */
+ * form with twice the tensor rate).  TC_FP16X3: tcgen05 kind::f16, fp16 hi/lo
+ * split of each operand scaled by a power of two from its maximum (an extra
+ * max pass per operand): fp16 and tf32 both carry 11 significant bits, so it
+ * has the 3xTF32 accuracy (relative L2 <= 1e-5) at the kind::f16 rate. */
 enum { TN_GEMM_AUTO = 0, TN_GEMM_TC_3XTF32 = 1, TN_GEMM_SIMT_FP32 = 2, TN_GEMM_TC_BF16X3 = 3, TN_GEMM_TC_FP16X3 = 4 };
 
 /* One gate, in time order.  arity 1: re/im[0..3] hold the 2x2 matrix
@@ -275,7 +278,8 @@ int  tn_head_norm(tn_head_t* head, double* norm, double* group_norms, void* stre
 int  tn_profile_slices(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, void* stream,
                        double* step_ms, int64_t n_entries);
 /* Kind (tn step kind: 0 small-operand, 1 permute, 2 B prep (tensor core),
- * 3 tensor-core GEMM, 4 B prep (SIMT), 5 SIMT GEMM, -1 accumulation) and the
+ * 3 tensor-core GEMM, 4 B prep (SIMT), 5 SIMT GEMM, 6 operand max (FP16x3
+ * scaling), -1 accumulation) and the
  * algorithmic complex multiply-adds and HBM bytes of launch i of one pass
  * (a slice runs 2^n_internal_sliced passes). */
 int  tn_plan_step_info(const tn_plan_t* plan, int64_t i, int* kind, double* macs, double* bytes);

@@ -64,6 +64,7 @@ static void plan_release(tn_plan_t* p) {
     cudaFree(p->d_tails);
     cudaFree(p->d_open);
     cudaFree(p->d_status);
+    cudaFree(p->d_scale);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     for (auto& e : p->prof_events) cudaEventDestroy(e);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -115,6 +116,10 @@ static int plan_upload(tn_plan_t* p) {
   if (h) CUDA_TRY(cudaMemcpy(p->d_open, P.open_qubits.data(), h * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMalloc(&p->d_status, sizeof(unsigned int)));
   CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(unsigned int)));
+  if (P.n_scale_slots > 0) {
+    CUDA_TRY(cudaMalloc(&p->d_scale, (size_t)P.n_scale_slots * sizeof(unsigned int)));
+    CUDA_TRY(cudaMemset(p->d_scale, 0, (size_t)P.n_scale_slots * sizeof(unsigned int)));
+  }
   return TN_OK;
 }
 
@@ -326,6 +331,10 @@ static inline float2* buf_ptr(const tn_plan_t* p, const tn::Ref& r) {
 // bits of automatically sliced edges).
 static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEvent_t* ev) {
   const tn::Plan& P = p->P;
+  if (P.n_scale_slots > 0) {
+    cudaError_t e = cudaMemsetAsync(p->d_scale, 0, (size_t)P.n_scale_slots * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("scale reset: ") + cudaGetErrorString(e));
+  }
   int si = 0;
   for (const tn::Step& x : P.steps) {
     cudaError_t e = cudaSuccess;
@@ -366,6 +375,7 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         std::memcpy(pp.rest_out, x.rest_out, sizeof(pp.rest_out));
         pp.tab = p->d_meta + x.tab_off;
         pp.split = x.split;
+        pp.scale = x.slot >= 0 ? p->d_scale + x.slot : nullptr;
         e = tn::launch_permute(pp, st);
         break;
       }
@@ -381,6 +391,7 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         bp.bk = p->d_meta + x.bk_off;
         bp.bn = p->d_meta + x.bn_off;
         bp.h16 = x.h16;
+        bp.scale = x.slot >= 0 ? p->d_scale + x.slot : nullptr;
         e = x.kind == tn::ST_BPREP_C ? tn::launch_bprep_c(bp, st) : tn::launch_bprep_tc(bp, st);
         break;
       }
@@ -401,7 +412,17 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         gp.mapA_mode = x.mapA_mode;
         gp.mapB_mode = x.mapB_mode;
         gp.h16 = x.h16;
+        gp.scaleA = x.slot >= 0 ? p->d_scale + x.slot : nullptr;
+        gp.scaleB = x.slotB >= 0 ? p->d_scale + x.slotB : nullptr;
         e = x.kind == tn::ST_GEMM_SIMT ? tn::launch_gemm_simt(gp, st) : tn::launch_gemm_tc(gp, p->d_status, st);
+        break;
+      }
+      case tn::ST_ABSMAX: {
+        tn::AbsmaxParams ap;
+        ap.in = ref_ptr(p, x.a, s);
+        ap.n = x.PA << x.rA;
+        ap.out = p->d_scale + x.slot;
+        e = tn::launch_absmax(ap, st);
         break;
       }
       default:

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
               float* __restrict__ C, int64_t M, int64_t N2, int64_t K2, int64_t tilesM, int64_t tilesN, int64_t PC,
               const uint32_t* __restrict__ mapA, const uint32_t* __restrict__ mapB, int mapA_mode, int mapB_mode,
-              unsigned int* status) {
+              const unsigned int* scaleA, const unsigned int* scaleB, unsigned int* status) {
   using Lay = Layout<BN, STAGES>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -334,6 +334,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(&acce[b]);
     }
     if (ok && active) {
+      // FP16 engine: undo the operands' power-of-two scales (two exact multiplies)
+      const float ua = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleA)) : 1.0f;
+      const float ub = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleB)) : 1.0f;
       const int64_t row = tm * BM + q * 32 + lane;
       if (row < M) {
         float* crow = C + (pc * M + row) * N2;
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int pp = 0; pp < NPIECE; ++pp) {
           float w[16];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) w[e] = FMT == 2 ? acc[16 * pp + e] * kFp16Unscale : acc[16 * pp + e];
+          for (int e = 0; e < 16; ++e) w[e] = FMT == 2 ? (acc[16 * pp + e] * ua) * ub : acc[16 * pp + e];
           const int64_t col = tn_ * BN + col0 + 16 * pp;
           if (col + 16 <= N2) {
             float4* dst = (float4*)(crow + col);
@@ -431,7 +434,8 @@ static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s
   if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
   k_gemm_tc<BN, STAGES, FMT><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(tah, tal, tbh, tbl, (float*)p.C, p.M, N2,
                                                                             K2, tilesM, tilesN, p.PC, p.mapA, p.mapB,
-                                                                            p.mapA_mode, p.mapB_mode, status);
+                                                                            p.mapA_mode, p.mapB_mode, p.scaleA,
+                                                                            p.scaleB, status);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ struct tn_plan {
   uint64_t* d_tails = nullptr;     // tails in group order
   int* d_open = nullptr;
   unsigned int* d_status = nullptr;
+  unsigned int* d_scale = nullptr;   // FP16x3 operand scale slots (zeroed at the start of every pass)
   int64_t n_keys = 0;
 };
 

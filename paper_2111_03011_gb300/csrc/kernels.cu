@@ -107,8 +107,9 @@ cudaError_t launch_small(const SmallParams& p, cudaStream_t s) {
 // to their positions) come from four 256-entry tables per direction.
 // SPLIT 1: the output is written as two fp32 planes, tf32-rounded hi and the
 // remainder lo; SPLIT 2: two bf16 planes, bf16 hi and the bf16-rounded
-// remainder; SPLIT 3: two fp16 planes of the value times kFp16Scale -- the
-// operand formats of the three tensor-core GEMM engines.
+// remainder; SPLIT 3: two fp16 planes of the value times the operand's power-
+// of-two scale (fp16_scale_exp of its ABSMAX slot) -- the operand formats of
+// the three tensor-core GEMM engines.
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
 __device__ __forceinline__ float tf32_rn(float x) {
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
   const uint64_t nrest_mask = (1ULL << p.n_rest) - 1;
   const uint64_t total_tiles = (uint64_t)p.P << p.n_rest;
   float2* __restrict__ out_lo = p.out + p.P * p.pstride;
+  const float sc = SPLIT == 3 ? pow2f(fp16_scale_exp(*p.scale)) : 1.0f;
   // Software pipeline: the global loads of the next tile are issued into
   // registers before the current tile is written out, so reads and writes of
   // consecutive tiles overlap.  A tile has at most 1024 elements: <= 4 per thread.
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
       } else if (SPLIT == 3) {
         __half2* fh = (__half2*)p.out;
         __half2* fl = fh + p.P * p.pstride;
-        const float2 w = make_float2(v.x * kFp16Scale, v.y * kFp16Scale);
+        const float2 w = make_float2(v.x * sc, v.y * sc);
         const __half2 h = __floats2half2_rn(w.x, w.y);
         const float2 hf = __half22float2(h);
         fh[o] = h;
@@ -218,6 +220,34 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
       }
     }
   }
+}
+
+// Scale slot of the FP16x3 engine: max over the operand of |re| and |im|.
+// Non-negative fp32 values order like their bit patterns, so the block maxima
+// are merged with an unsigned atomicMax into the slot (zeroed before the pass).
+__global__ void __launch_bounds__(256) k_absmax(AbsmaxParams p) {
+  __shared__ float red[8];
+  float m = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = __ldg(p.in + i);
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(p.out, __float_as_uint(m));
+  }
+}
+
+cudaError_t launch_absmax(const AbsmaxParams& p, cudaStream_t s) {
+  const int64_t grid = std::max<int64_t>(std::min<int64_t>((p.n + 255) / 256, (int64_t)kSMs * 8), 1);
+  k_absmax<<<(unsigned)grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_permute(const PermParams& p, cudaStream_t s) {
@@ -250,7 +280,7 @@ __global__ void k_bprep_c(BPrepParams p) {
 // Bt[j][i] (j = 2n + jc output column, i = 2k + ic reduction index) is
 // [[re, -im], [im, re]] in (jc, ic); stored K-major as hi and lo planes in the
 // GEMM engine's operand format (FMT 0: tf32-rounded fp32 hi + fp32 remainder;
-// 1: bf16 hi + bf16 remainder; 2: fp16 of the value times kFp16Scale).  One
+// 1: bf16 hi + bf16 remainder; 2: fp16 of the value times the scale sc).  One
 // thread per complex element of B: it writes the element's 2 x 2 block as two
 // pairs of adjacent reals (rows 2n and 2n + 1) in each plane; consecutive
 // threads take consecutive k, so every row segment is written contiguously.
@@ -259,7 +289,7 @@ struct Pair;
 template <>
 struct Pair<0> {
   using T = float2;
-  static __device__ __forceinline__ void split(float a, float b, T& h, T& l) {
+  static __device__ __forceinline__ void split(float a, float b, float, T& h, T& l) {
     h = make_float2(tf32_rn(a), tf32_rn(b));
     l = make_float2(a - h.x, b - h.y);
   }
@@ -267,7 +297,7 @@ struct Pair<0> {
 template <>
 struct Pair<1> {
   using T = __nv_bfloat162;
-  static __device__ __forceinline__ void split(float a, float b, T& h, T& l) {
+  static __device__ __forceinline__ void split(float a, float b, float, T& h, T& l) {
     h = __floats2bfloat162_rn(a, b);
     const float2 f = __bfloat1622float2(h);
     l = __floats2bfloat162_rn(a - f.x, b - f.y);
@@ -276,9 +306,9 @@ struct Pair<1> {
 template <>
 struct Pair<2> {
   using T = __half2;
-  static __device__ __forceinline__ void split(float a, float b, T& h, T& l) {
-    a *= kFp16Scale;
-    b *= kFp16Scale;
+  static __device__ __forceinline__ void split(float a, float b, float sc, T& h, T& l) {
+    a *= sc;
+    b *= sc;
     h = __floats2half2_rn(a, b);
     const float2 f = __half22float2(h);
     l = __floats2half2_rn(a - f.x, b - f.y);
@@ -293,16 +323,17 @@ __global__ void k_bprep_tc(BPrepParams p) {
   const int64_t total = p.PB * per;
   T* hi = (T*)p.out;                          // pairs: [PB][2N][K] pairs of reals
   T* lo = hi + 2 * total;
+  const float sc = FMT == 2 ? pow2f(fp16_scale_exp(*p.scale)) : 1.0f;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pb = e / per, r = e - pb * per;
     const int64_t n = r >> p.nk, k = r & (K - 1);
     const float2 b = p.B[pb * p.b_pstride + p.bk[k] + p.bn[n]];
     const int64_t o0 = (pb * 2 * N + 2 * n) * K + k;   // pair (2k, 2k+1) of row 2n
     T h, l;
-    Pair<FMT>::split(b.x, -b.y, h, l);
+    Pair<FMT>::split(b.x, -b.y, sc, h, l);
     hi[o0] = h;
     lo[o0] = l;
-    Pair<FMT>::split(b.y, b.x, h, l);
+    Pair<FMT>::split(b.y, b.x, sc, h, l);
     hi[o0 + K] = h;                                    // row 2n + 1
     lo[o0 + K] = l;
   }

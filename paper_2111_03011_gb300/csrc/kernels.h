@@ -6,14 +6,30 @@
 
 namespace tn {
 
-// Operand scale of the FP16x3 engine.  Every intermediate of a network of
-// unitary gates, basis vectors and basis projectors is a sub-block of a
-// unitary, so its entries have modulus at most 1.  Scaling by 2^15 keeps them
-// below the fp16 maximum (65504) and lifts a typical entry and its split
-// remainder out of the fp16 subnormal range; the GEMM epilogue undoes both
-// operands' scale with 2^-30.  Powers of two: both steps are exact.
-constexpr float kFp16Scale = 32768.0f;
-constexpr float kFp16Unscale = 1.0f / (32768.0f * 32768.0f);
+// Operand scaling of the FP16x3 engine.  An ABSMAX step writes m = max over a
+// GEMM operand of |re| and |im| (as fp32 bits, by atomicMax) into a scale slot.
+// The split kernels multiply the operand by 2^k with k = 14 - floor(log2 m)
+// (so that |x| 2^k < 2^15 < 65504, the fp16 maximum, while the largest entries
+// and their split remainders keep full fp16 precision); the GEMM epilogue
+// multiplies by 2^-kA 2^-kB.  Powers of two: every scaling is exact.
+__host__ __device__ __forceinline__ int fp16_scale_exp(unsigned int m_bits) {
+  if (m_bits == 0) return 14;                       // all-zero operand
+  int e = (int)((m_bits >> 23) & 0xffu) - 127;      // floor(log2 m) for normal m
+  if (e < -100) e = -100;
+  return 14 - e;                                    // in [14 - 127, 114]
+}
+// 2^k as an fp32, for -126 <= k <= 127 (built from its exponent bits)
+__host__ __device__ __forceinline__ float pow2f(int k) {
+  union { unsigned int u; float f; } x;
+  x.u = (unsigned int)(127 + k) << 23;
+  return x.f;
+}
+
+struct AbsmaxParams {
+  const float2* in;
+  int64_t n;             // complex elements
+  unsigned int* out;     // scale slot (fp32 bits of the running maximum; zeroed per pass)
+};
 
 // C[p][m + (n << (rA-nk))] = sum_k A[mapA(p)][insert_K(m) + k-offset] * B[mapB(p)][boffK[k] + boffN[n]]
 struct SmallParams {
@@ -37,7 +53,8 @@ struct PermParams {
   uint8_t rest_in[64], rest_out[64];
   const uint32_t* tab;   // in_off[2^t], out_off[2^t], slot[2^t]
   int split;             // 1: write tf32 hi plane then lo plane (fp32 pairs); 2: bf16 planes;
-                         // 3: fp16 planes of the value times kFp16Scale
+                         // 3: fp16 planes of the value times 2^k (k from *scale)
+  const unsigned int* scale;   // SPLIT 3: the operand's scale slot
 };
 
 struct BPrepParams {
@@ -46,6 +63,7 @@ struct BPrepParams {
   int nk, nn;
   const uint32_t* bk; const uint32_t* bn;
   int h16;               // tensor-core B: 0 tf32 planes, 1 bf16 planes, 2 scaled fp16 planes
+  const unsigned int* scale;   // h16 == 2: the operand's scale slot
 };
 
 // C[p][m][n] = sum_k A[mapA(p)][m][k] B[mapB(p)][k][n]
@@ -56,6 +74,7 @@ struct GemmParams {
   const uint32_t* mapA; const uint32_t* mapB;
   int mapA_mode, mapB_mode;
   int h16;               // tensor-core engine: 0 tf32, 1 bf16, 2 scaled fp16 hi/lo operand planes
+  const unsigned int* scaleA; const unsigned int* scaleB;   // h16 == 2: the operands' scale slots
 };
 
 struct AccumParams {
@@ -67,6 +86,7 @@ struct AccumParams {
 };
 
 cudaError_t launch_small(const SmallParams& p, cudaStream_t s);
+cudaError_t launch_absmax(const AbsmaxParams& p, cudaStream_t s);
 cudaError_t launch_permute(const PermParams& p, cudaStream_t s);
 cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s);
 cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s);

@@ -668,6 +668,20 @@ static void set_map(Plan& plan, const VTensor& X, const VTensor& C, int& mode, i
   off = meta_push(plan, m);
 }
 
+// max |re|, |im| of X into scale slot `slot` (FP16x3 operand scaling)
+static void add_absmax(Plan& plan, const VTensor& X, int slot, int ci) {
+  Step s;
+  s.kind = ST_ABSMAX;
+  s.a = X.ref;
+  s.rA = (int)X.legs.size();
+  s.PA = X.P;
+  s.slot = slot;
+  s.contraction = ci;
+  s.bytes = 8.0 * (double)vt_elems(X);
+  touch(plan, X.ref, (int)plan.steps.size());
+  plan.steps.push_back(s);
+}
+
 static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& target, Ref out, int ci,
                         int split) {
   Step s;
@@ -820,19 +834,28 @@ static int layout_steps(Plan& plan, std::string& err) {
       const int h16 = nk >= 2 ? (plan.gemm_engine == TN_GEMM_TC_BF16X3 ? 1 : plan.gemm_engine == TN_GEMM_TC_FP16X3 ? 2 : 0) : 0;
       const bool bf16 = h16 != 0;
       const bool tc = plan.gemm_engine != TN_GEMM_SIMT_FP32 && nk >= 1;
+      int slot_a = -1, slot_b = -1;
+      if (h16 == 2) {
+        slot_a = plan.n_scale_slots++;
+        slot_b = plan.n_scale_slots++;
+      }
       if (tc || target != big.legs) {
         // the tensor-core GEMM reads A as hi/lo planes: always a (possibly
         // identity) permute in split mode
+        if (h16 == 2) add_absmax(plan, big, slot_a, ci);
         const int st = (int)plan.steps.size();
         touch(plan, big.ref, st);
         Ref out{1, new_buf(plan, vt_elems(big) * 8 * (tc && !bf16 ? 2 : 1), st)};
         add_permute(plan, big, target, out, ci, tc ? (h16 == 2 ? 3 : h16 == 1 ? 2 : 1) : 0);
+        plan.steps.back().slot = slot_a;
         aref = out;
       }
       // B' prep
       Step p;
       p.kind = tc ? ST_BPREP_TC : ST_BPREP_C;
       p.h16 = h16;
+      p.slot = slot_b;
+      if (h16 == 2) add_absmax(plan, sml, slot_b, ci);
       p.contraction = ci;
       p.a = sml.ref;
       p.rA = (int)sml.legs.size();
@@ -852,6 +875,8 @@ static int layout_steps(Plan& plan, std::string& err) {
       Step g;
       g.kind = tc ? ST_GEMM_TC : ST_GEMM_SIMT;
       g.h16 = h16;
+      g.slot = slot_a;
+      g.slotB = slot_b;
       g.contraction = ci;
       g.a = aref;
       g.b = p.c;
@@ -1036,25 +1061,6 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
     } else { err = "edge: unknown kind"; return TN_ERR_INVALID; }
   }
   if (k > 40) { err = "at most 40 sliced edges"; return TN_ERR_INVALID; }
-  if (in.gemm_engine == TN_GEMM_TC_FP16X3) {
-    // the FP16x3 engine's fixed operand scale relies on every intermediate
-    // being a sub-block of a unitary (entries of modulus <= 1)
-    for (int g = 0; g < in.n_gates; ++g) {
-      const int d = in.arity[g] == 1 ? 2 : 4;
-      const cd* U = in.mats + (size_t)g * 16;
-      double dev = 0.0;
-      for (int i = 0; i < d; ++i)
-        for (int j = 0; j < d; ++j) {
-          cd s(0, 0);
-          for (int r = 0; r < d; ++r) s += std::conj(U[r * d + i]) * U[r * d + j];
-          dev = std::max(dev, std::abs(s - cd(i == j ? 1.0 : 0.0, 0.0)));
-        }
-      if (dev > 1e-6) {
-        err = "the FP16x3 engine needs unitary gates (gate " + std::to_string(g) + " is not)";
-        return TN_ERR_INVALID;
-      }
-    }
-  }
   if (k + in.auto_slice > 62) { err = "sliced edges plus auto_slice above 62"; return TN_ERR_INVALID; }
   plan.n_sliced = k;
   plan.n_internal = 0;
@@ -1214,7 +1220,7 @@ std::string describe_plan(const Plan& plan, bool with_data) {
       << ",\"PA\":" << st.PA << ",\"PB\":" << st.PB << ",\"PC\":" << st.PC << ",\"macs\":" << st.macs
       << ",\"bytes\":" << st.bytes << ",\"rA\":" << st.rA << ",\"rB\":" << st.rB << ",\"rC\":" << st.rC
       << ",\"a\":[" << st.a.kind << "," << st.a.id << "],\"b\":[" << st.b.kind << "," << st.b.id << "],\"c\":["
-      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"h16\":" << st.h16
+      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"h16\":" << st.h16 << ",\"slot\":" << st.slot << ",\"slotB\":" << st.slotB
       << ",\"tab_off\":" << st.tab_off << ",\"n_rest\":" << st.n_rest << ",\"rest_in\":[";
     for (int v = 0; v < st.n_rest; ++v) o << (v ? "," : "") << (int)st.rest_in[v];
     o << "],\"rest_out\":[";

@@ -303,7 +303,7 @@ def test_profile_and_reset(tn):
     tn.tn_contract_slices(plan, 0, 16, head)
     assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg))
     kinds = [tn.tn_plan_step_info(plan, i)[0] for i in range(st["n_launches"])]
-    assert kinds[-1] == -1 and set(kinds[:-1]) <= {0, 1, 2, 3, 4, 5}
+    assert kinds[-1] == -1 and set(kinds[:-1]) <= {0, 1, 2, 3, 4, 5, 6}
 
 
 @pytest.mark.parametrize("gemm", [0, 3, 4], ids=["tc", "bf16", "fp16"])
@@ -580,3 +580,19 @@ def test_sycamore53_reduced_depth_parity(tn, gemm):
     H = read_head(tn, plan, head, dict(circuit=circ, open_qubits=oq, tails=tails, edges=[]))
     assert_close(H[list(g["groups"])], g["H"])
     assert tn.tn_head_fidelity(head) == (1.0, 1)
+
+
+@pytest.mark.parametrize("scale_exp", [-40, -16, 16])
+def test_fp16_engine_dynamic_range(tn, scale_exp):
+    """FP16x3 with per-operand power-of-two scaling keeps complex64 accuracy
+    whatever the magnitude of the network's entries: two gates scaled by
+    2^scale_exp (and so every amplitude by 2^(2 scale_exp)) -- far outside the
+    fp16 range unscaled -- match the oracle at 1e-5."""
+    import copy
+    cfg = ci.config_small(4, 5, 10, seed=13, n_open=8, L=24, n_cut_gates=1)
+    circ = copy.deepcopy(cfg["circuit"])
+    for gi in (5, len(circ.gates) // 2):
+        circ.gates[gi].U = circ.gates[gi].U * 2.0 ** scale_exp
+    cfg = dict(cfg, circuit=circ)
+    plan, head = contract_all(tn, cfg, gemm=tn.TN_GEMM_TC_FP16X3, small_max_bits=-1)
+    assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg))
