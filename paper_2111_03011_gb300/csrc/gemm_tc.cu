@@ -9,9 +9,9 @@
 // hi = round-to-tf32, lo = x - hi.  The BF16 engine takes the same three
 // products of bf16 hi/lo parts on kind::f16 (~2^-16 relative per product, at
 // twice the tensor rate); the FP16 engine takes them of fp16 hi/lo parts of
-// the operands scaled by 2^15 (fp16 and tf32 both carry 11 significant bits,
-// so it keeps the 3xTF32 accuracy at the kind::f16 rate; the scale, exact,
-// is undone in the epilogue).  Both operands arrive pre-split in global
+// the operands scaled by powers of two (fp16 and tf32 both carry 11
+// significant bits, so it keeps the 3xTF32 accuracy at the kind::f16 rate;
+// the scales, exact, are undone in the epilogue).  Both operands arrive pre-split in global
 // memory (A by the split-mode permute, B by k_bprep_tc), so the kernel is a
 // plain TMA -> MMA pipeline.
 //
@@ -19,7 +19,7 @@
 // nearest, so a long K loop accumulated in place drifts (the error grows
 // linearly with K; see Ootomo and Yokota, "Recovering single precision
 // accuracy from Tensor Cores while surpassing the FP32 theoretical peak
-// performance", 2022).  The K loop is therefore cut into chunks of one k-block,
+// performance", 2022).  The K loop is therefore cut into chunks of 128 bytes of K,
 // each accumulated from zero in one of two ping-pong TMEM buffers (2 x BN <= 512
 // columns) and folded by eight drain warps into a running sum held in their
 // registers with ordinary round-to-nearest FP32 adds, while the MMAs of the
@@ -27,7 +27,8 @@
 //
 // Roles (320 threads): warps 0-7 drain chunk accumulators into the running sum
 // and write the tile out (two warps per TMEM lane quarter, half the columns
-// each), warp 8 issues TMA loads, warp 9 owns TMEM and issues the MMAs.  One CTA computes a 128 x BN tile of C_r.  Every mbarrier wait is
+// each), warp 8 issues TMA loads, warp 9 owns TMEM and issues the MMAs.  One
+// CTA computes a 128 x BN tile of C_r.  Every mbarrier wait is
 // bounded; on timeout the CTA records a status code and leaves its loops
 // instead of hanging.
 #include <cuda.h>
