@@ -116,9 +116,12 @@ static int plan_upload(tn_plan_t* p) {
   if (h) CUDA_TRY(cudaMemcpy(p->d_open, P.open_qubits.data(), h * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMalloc(&p->d_status, sizeof(unsigned int)));
   CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(unsigned int)));
-  if (P.n_scale_slots > 0) {
-    CUDA_TRY(cudaMalloc(&p->d_scale, (size_t)P.n_scale_slots * sizeof(unsigned int)));
-    CUDA_TRY(cudaMemset(p->d_scale, 0, (size_t)P.n_scale_slots * sizeof(unsigned int)));
+  const size_t n_static = P.scale_static.size(), n_slots = n_static + (size_t)P.n_scale_slots;
+  if (n_slots > 0) {
+    CUDA_TRY(cudaMalloc(&p->d_scale, n_slots * sizeof(unsigned int)));
+    CUDA_TRY(cudaMemset(p->d_scale, 0, n_slots * sizeof(unsigned int)));
+    if (n_static)
+      CUDA_TRY(cudaMemcpy(p->d_scale, P.scale_static.data(), n_static * sizeof(unsigned int), cudaMemcpyHostToDevice));
   }
   return TN_OK;
 }
@@ -327,12 +330,20 @@ static inline float2* buf_ptr(const tn_plan_t* p, const tn::Ref& r) {
   return (float2*)(p->d_arena + p->P.bufs[r.id].off);
 }
 
+// FP16x3 scale slot -> device address (static slots first, then the per-pass ones)
+static unsigned int* scale_ptr(const tn_plan_t* p, int slot) {
+  if (slot == -1) return nullptr;
+  const int64_t n_static = (int64_t)p->P.scale_static.size();
+  return p->d_scale + (slot >= 0 ? n_static + slot : (int64_t)(-(slot + 2)));
+}
+
 // One pass of the launch list for the full slice id s (user bits, then the
 // bits of automatically sliced edges).
 static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEvent_t* ev) {
   const tn::Plan& P = p->P;
   if (P.n_scale_slots > 0) {
-    cudaError_t e = cudaMemsetAsync(p->d_scale, 0, (size_t)P.n_scale_slots * sizeof(unsigned int), st);
+    cudaError_t e = cudaMemsetAsync(p->d_scale + P.scale_static.size(), 0,
+                                    (size_t)P.n_scale_slots * sizeof(unsigned int), st);
     if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("scale reset: ") + cudaGetErrorString(e));
   }
   int si = 0;
@@ -360,6 +371,7 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         sp.mapB = p->d_meta + x.mapB_off;
         sp.mapA_mode = x.mapA_mode;
         sp.mapB_mode = x.mapB_mode;
+        sp.amax = scale_ptr(p, x.max_slot);
         e = tn::launch_small(sp, st);
         break;
       }
@@ -375,7 +387,7 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         std::memcpy(pp.rest_out, x.rest_out, sizeof(pp.rest_out));
         pp.tab = p->d_meta + x.tab_off;
         pp.split = x.split;
-        pp.scale = x.slot >= 0 ? p->d_scale + x.slot : nullptr;
+        pp.scale = scale_ptr(p, x.slot);
         e = tn::launch_permute(pp, st);
         break;
       }
@@ -391,7 +403,7 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         bp.bk = p->d_meta + x.bk_off;
         bp.bn = p->d_meta + x.bn_off;
         bp.h16 = x.h16;
-        bp.scale = x.slot >= 0 ? p->d_scale + x.slot : nullptr;
+        bp.scale = scale_ptr(p, x.slot);
         e = x.kind == tn::ST_BPREP_C ? tn::launch_bprep_c(bp, st) : tn::launch_bprep_tc(bp, st);
         break;
       }
@@ -412,8 +424,9 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         gp.mapA_mode = x.mapA_mode;
         gp.mapB_mode = x.mapB_mode;
         gp.h16 = x.h16;
-        gp.scaleA = x.slot >= 0 ? p->d_scale + x.slot : nullptr;
-        gp.scaleB = x.slotB >= 0 ? p->d_scale + x.slotB : nullptr;
+        gp.scaleA = scale_ptr(p, x.slot);
+        gp.scaleB = scale_ptr(p, x.slotB);
+        gp.amax = scale_ptr(p, x.max_slot);
         e = x.kind == tn::ST_GEMM_SIMT ? tn::launch_gemm_simt(gp, st) : tn::launch_gemm_tc(gp, p->d_status, st);
         break;
       }
@@ -421,7 +434,7 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         tn::AbsmaxParams ap;
         ap.in = ref_ptr(p, x.a, s);
         ap.n = x.PA << x.rA;
-        ap.out = p->d_scale + x.slot;
+        ap.out = scale_ptr(p, x.slot);
         e = tn::launch_absmax(ap, st);
         break;
       }

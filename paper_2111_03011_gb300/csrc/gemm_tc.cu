@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
               float* __restrict__ C, int64_t M, int64_t N2, int64_t K2, int64_t tilesM, int64_t tilesN, int64_t PC,
               const uint32_t* __restrict__ mapA, const uint32_t* __restrict__ mapB, int mapA_mode, int mapB_mode,
-              const unsigned int* scaleA, const unsigned int* scaleB, unsigned int* status) {
+              const unsigned int* scaleA, const unsigned int* scaleB, unsigned int* amax_out,
+              unsigned int* status) {
   using Lay = Layout<BN, STAGES>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* acce = bars + 2 * STAGES + 2;   // chunk drained (drain -> MMA)     [2]
   volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * STAGES + 4);
   volatile int* abort_flag = (volatile int*)(bars + 2 * STAGES + 5);
+  unsigned int* s_amax = (unsigned int*)(bars + 2 * STAGES + 6);   // CTA maximum of the output tile
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t pc, tm, tn_;
@@ -238,6 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&acce[b], 256);
     }
     *abort_flag = 0;
+    *s_amax = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 9) {
@@ -339,6 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float ua = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleA)) : 1.0f;
       const float ub = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleB)) : 1.0f;
       const int64_t row = tm * BM + q * 32 + lane;
+      float tmax = 0.0f;
       if (row < M) {
         float* crow = C + (pc * M + row) * N2;
 #pragma unroll
@@ -347,6 +351,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int e = 0; e < 16; ++e) w[e] = FMT == 2 ? (acc[16 * pp + e] * ua) * ub : acc[16 * pp + e];
           const int64_t col = tn_ * BN + col0 + 16 * pp;
+          if (amax_out) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (col + e < N2) tmax = fmaxf(tmax, fabsf(w[e]));
+          }
           if (col + 16 <= N2) {
             float4* dst = (float4*)(crow + col);
 #pragma unroll
@@ -358,11 +367,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      if (amax_out) {
+        // warp maximum, then the CTA maximum in shared memory (one global
+        // atomic per CTA after the final barrier)
+        const unsigned int mask = __activemask();
+        const unsigned int m = __reduce_max_sync(mask, __float_as_uint(tmax));
+        if (lane == __ffs(mask) - 1) atomicMax(s_amax, m);
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) atomicOr(status, 1u);
+  if (amax_out && threadIdx.x == 0 && *s_amax) atomicMax(amax_out, *s_amax);
   if (warp == 9) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lay::TMEM_COLS));
@@ -436,7 +453,7 @@ static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s
   k_gemm_tc<BN, STAGES, FMT><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(tah, tal, tbh, tbl, (float*)p.C, p.M, N2,
                                                                             K2, tilesM, tilesN, p.PC, p.mapA, p.mapB,
                                                                             p.mapA_mode, p.mapB_mode, p.scaleA,
-                                                                            p.scaleB, status);
+                                                                            p.scaleB, p.amax, status);
   return cudaGetLastError();
 }
 

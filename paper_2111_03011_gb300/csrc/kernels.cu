@@ -44,6 +44,9 @@ __global__ void __launch_bounds__(256) k_small(SmallParams p) {
     offK[k] = o;
   }
   const int64_t rowsC = p.M;  // C stride of the n index
+  __shared__ unsigned int s_amax;
+  if (threadIdx.x == 0) s_amax = 0u;
+  float tmax = 0.0f;
   for (int64_t pc = blockIdx.y; pc < p.PC; pc += gridDim.y) {
     const int64_t pa = map_p(p.mapA_mode, p.mapA, pc);
     const int64_t pb = map_p(p.mapB_mode, p.mapB, pc);
@@ -71,8 +74,17 @@ __global__ void __launch_bounds__(256) k_small(SmallParams p) {
 #pragma unroll
         for (int k = 0; k < KK; ++k) acc = cmul_add(acc, a[k], Bs[k][n]);
         Cp[m + (int64_t)n * rowsC] = acc;
+        tmax = fmaxf(tmax, fmaxf(fabsf(acc.x), fabsf(acc.y)));
       }
     }
+  }
+  if (p.amax) {
+    // block maximum of the output (FP16x3 scale of the next GEMM operand)
+    unsigned int b = __reduce_max_sync(0xffffffffu, __float_as_uint(tmax));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_amax, b);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(p.amax, s_amax);
   }
 }
 

@@ -42,6 +42,7 @@ struct SmallParams {
   uint32_t boffK[16], boffN[16];
   const uint32_t* mapA; const uint32_t* mapB;
   int mapA_mode, mapB_mode;  // 0 identity, 1 zero, 2 table
+  unsigned int* amax;        // non-null: atomicMax of the output's max |re|, |im| (fp32 bits)
 };
 
 // out[p][bo + out_off[j]] = in[p][bi + in_off[slot[j]]], (bi, bo) from the rest bits
@@ -75,6 +76,7 @@ struct GemmParams {
   int mapA_mode, mapB_mode;
   int h16;               // tensor-core engine: 0 tf32, 1 bf16, 2 scaled fp16 hi/lo operand planes
   const unsigned int* scaleA; const unsigned int* scaleB;   // h16 == 2: the operands' scale slots
+  unsigned int* amax;    // non-null: atomicMax of the output's max |re|, |im| (fp32 bits)
 };
 
 struct AccumParams {

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <random>
 #include <set>
@@ -741,7 +742,36 @@ static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& ta
 static int layout_steps(Plan& plan, std::string& err) {
   plan.steps.clear();
   plan.bufs.clear();
+  plan.n_scale_slots = 0;
+  plan.scale_static.clear();
+  std::map<int, int> producer;   // workspace buffer id -> index of the step that writes it
   int ci = 0;
+  // FP16x3 scale slot of a GEMM operand X: a leaf's maximum is known on the
+  // host (static slot, over all its slice variants); an intermediate written
+  // by a tensor-core GEMM or a small-operand step has its maximum recorded by
+  // that step's epilogue; anything else gets an ABSMAX pass.
+  auto operand_slot = [&](const VTensor& X) -> int {
+    if (X.ref.kind == 0) {
+      const LeafInfo& li = plan.leaf_info[X.ref.id];
+      const int64_t n = li.size << li.var_slice_bits.size();
+      float m = 0.0f;
+      for (int64_t e = 0; e < n; ++e) {
+        const cd& v = plan.leaf_arena[(size_t)(li.off + e)];
+        m = std::max(m, std::max(std::fabs((float)v.real()), std::fabs((float)v.imag())));
+      }
+      uint32_t bits;
+      std::memcpy(&bits, &m, sizeof(bits));
+      plan.scale_static.push_back(bits);
+      return -(int)plan.scale_static.size() - 1;
+    }
+    const int slot = plan.n_scale_slots++;
+    auto it = producer.find(X.ref.id);
+    if (it != producer.end() && (plan.steps[it->second].kind == ST_GEMM_TC || plan.steps[it->second].kind == ST_SMALL))
+      plan.steps[it->second].max_slot = slot;
+    else
+      add_absmax(plan, X, slot, ci);
+    return slot;
+  };
   for (auto& pr : plan.order) {
     const int i = pr.first, j = pr.second;
     VTensor A = plan.vts[i], B = plan.vts[j];
@@ -824,6 +854,7 @@ static int layout_steps(Plan& plan, std::string& err) {
       s.c = Ref{1, new_buf(plan, eC * 8, st)};
       C.ref = s.c;
       plan.steps.push_back(s);
+      producer[s.c.id] = (int)plan.steps.size() - 1;
     } else {
       // A' = big permuted to [K][M] (K legs low) unless already so
       std::vector<int> target;
@@ -835,14 +866,10 @@ static int layout_steps(Plan& plan, std::string& err) {
       const bool bf16 = h16 != 0;
       const bool tc = plan.gemm_engine != TN_GEMM_SIMT_FP32 && nk >= 1;
       int slot_a = -1, slot_b = -1;
-      if (h16 == 2) {
-        slot_a = plan.n_scale_slots++;
-        slot_b = plan.n_scale_slots++;
-      }
       if (tc || target != big.legs) {
         // the tensor-core GEMM reads A as hi/lo planes: always a (possibly
         // identity) permute in split mode
-        if (h16 == 2) add_absmax(plan, big, slot_a, ci);
+        if (h16 == 2) slot_a = operand_slot(big);
         const int st = (int)plan.steps.size();
         touch(plan, big.ref, st);
         Ref out{1, new_buf(plan, vt_elems(big) * 8 * (tc && !bf16 ? 2 : 1), st)};
@@ -854,8 +881,8 @@ static int layout_steps(Plan& plan, std::string& err) {
       Step p;
       p.kind = tc ? ST_BPREP_TC : ST_BPREP_C;
       p.h16 = h16;
+      if (h16 == 2) slot_b = operand_slot(sml);
       p.slot = slot_b;
-      if (h16 == 2) add_absmax(plan, sml, slot_b, ci);
       p.contraction = ci;
       p.a = sml.ref;
       p.rA = (int)sml.legs.size();
@@ -895,6 +922,7 @@ static int layout_steps(Plan& plan, std::string& err) {
       g.c = Ref{1, new_buf(plan, eC * 8, st)};
       C.ref = g.c;
       plan.steps.push_back(g);
+      producer[g.c.id] = (int)plan.steps.size() - 1;
     }
     for (auto& s : plan.steps)
       if (s.contraction == ci) { s.vt_a = i; s.vt_b = j; s.vt_c = (int)plan.vts.size(); }
@@ -1220,7 +1248,7 @@ std::string describe_plan(const Plan& plan, bool with_data) {
       << ",\"PA\":" << st.PA << ",\"PB\":" << st.PB << ",\"PC\":" << st.PC << ",\"macs\":" << st.macs
       << ",\"bytes\":" << st.bytes << ",\"rA\":" << st.rA << ",\"rB\":" << st.rB << ",\"rC\":" << st.rC
       << ",\"a\":[" << st.a.kind << "," << st.a.id << "],\"b\":[" << st.b.kind << "," << st.b.id << "],\"c\":["
-      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"h16\":" << st.h16 << ",\"slot\":" << st.slot << ",\"slotB\":" << st.slotB
+      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"h16\":" << st.h16 << ",\"slot\":" << st.slot << ",\"slotB\":" << st.slotB << ",\"max_slot\":" << st.max_slot
       << ",\"tab_off\":" << st.tab_off << ",\"n_rest\":" << st.n_rest << ",\"rest_in\":[";
     for (int v = 0; v < st.n_rest; ++v) o << (v ? "," : "") << (int)st.rest_in[v];
     o << "],\"rest_out\":[";

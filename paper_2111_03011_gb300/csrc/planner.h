@@ -91,8 +91,11 @@ struct Step {
   int t_bits = 0;
   int split = 0;           // PERMUTE: 1 tf32 hi/lo planes, 2 bf16, 3 scaled fp16 (tensor-core GEMM operand)
   int h16 = 0;             // BPREP_TC / GEMM_TC: 16-bit operand planes (0 tf32, 1 bf16, 2 scaled fp16)
+  // FP16x3 scale slots: -1 none, j >= 0 the j-th per-pass slot (zeroed at the
+  // start of every pass), <= -2 the static slot -(slot + 2) (a leaf's maximum)
   int slot = -1;           // ABSMAX: slot written; PERMUTE (split 3), BPREP (h16 2), GEMM (h16 2): A's slot
   int slotB = -1;          // GEMM (h16 2): B's slot
+  int max_slot = -1;       // GEMM_TC / SMALL: also write the output's max |re|, |im| into this slot
   int64_t tab_off = 0;
   int n_rest = 0;
   uint8_t rest_in[64] = {0}, rest_out[64] = {0};
@@ -127,7 +130,8 @@ struct Plan {
   uint64_t open_mask = 0, tail_mask = 0;
   int n_sliced = 0, n_pinned = 0, n_companion = 0;
   int n_internal = 0;              // slice bits added by automatic slicing (summed inside every slice)
-  int n_scale_slots = 0;           // FP16x3 operand scale slots (two per GEMM step)
+  int n_scale_slots = 0;           // FP16x3 per-pass operand scale slots
+  std::vector<uint32_t> scale_static;   // FP16x3 static slots: fp32 bits of a leaf operand's max |re|, |im|
   std::vector<std::pair<int, int>> leg_edge;   // bond leg -> (gate, input leg) that consumes it
   std::vector<std::pair<int, int>> internal_edges;   // (gate, leg) of the SLICE edges automatic slicing added
   double companion_factor = 1.0;   // product of the companion cuts' kept norm fractions

@@ -248,34 +248,38 @@ def test_automatic_slicing_counts_and_limits(tn):
 
 def test_fp16_engine_scale_slots(tn):
     """The FP16x3 engine scales each GEMM operand by a power of two from its
-    maximum: every fp16 GEMM step has an operand-max step for A before A's
-    split permute and one for B before B's prep, with the slots the GEMM reads;
-    the other engines have none.  Unitarity is not required (a gate scaled by
-    2^-40 plans the same way)."""
+    maximum.  Every fp16 GEMM step reads two distinct slots: a leaf operand's
+    maximum is a static slot computed on the host; an intermediate's slot is
+    written, earlier in the pass, either by the epilogue of the step that
+    produced it (tensor-core GEMM or small-operand step) or by an operand-max
+    step -- exactly one writer each.  The other engines use no slots, and
+    unitarity is not required (a gate scaled by 2^-40 plans the same way)."""
     import copy
     cfg = _auto_cfg()
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True,
-                      gemm=tn.TN_GEMM_TC_FP16X3, small_max_bits=-1)
-    steps = tn.tn_plan_describe(plan)["steps"]
-    gemms = [i for i, s_ in enumerate(steps) if s_["kind"] == 3 and s_["h16"] == 2]
-    assert gemms
-    slots = set()
-    for gi in gemms:
-        g = steps[gi]
-        sa, sb = g["slot"], g["slotB"]
-        assert sa >= 0 and sb >= 0 and sa != sb and not ({sa, sb} & slots)
-        slots |= {sa, sb}
-        before = steps[:gi]
-        perm = [i for i, s_ in enumerate(before) if s_["kind"] == 1 and s_["split"] == 3 and s_["slot"] == sa]
-        prep = [i for i, s_ in enumerate(before) if s_["kind"] == 2 and s_["slot"] == sb]
-        amax_a = [i for i, s_ in enumerate(before) if s_["kind"] == 6 and s_["slot"] == sa]
-        amax_b = [i for i, s_ in enumerate(before) if s_["kind"] == 6 and s_["slot"] == sb]
-        assert len(perm) == len(prep) == len(amax_a) == len(amax_b) == 1
-        assert amax_a[0] < perm[0] and amax_b[0] < prep[0]
-        assert steps[amax_a[0]]["a"] == steps[perm[0]]["a"] and steps[amax_b[0]]["a"] == steps[prep[0]]["a"]
+    for small in (-1, 0):
+        plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True,
+                          gemm=tn.TN_GEMM_TC_FP16X3, small_max_bits=small)
+        steps = tn.tn_plan_describe(plan)["steps"]
+        gemms = [i for i, s_ in enumerate(steps) if s_["kind"] == 3 and s_["h16"] == 2]
+        assert gemms
+        seen = set()
+        for gi in gemms:
+            g = steps[gi]
+            for sl, consumer_kind in ((g["slot"], 1), (g["slotB"], 2)):
+                assert sl != -1 and sl not in seen
+                seen.add(sl)
+                users = [i for i, s_ in enumerate(steps[:gi]) if s_["kind"] == consumer_kind and s_["slot"] == sl]
+                assert len(users) == 1
+                if sl <= -2:
+                    continue
+                writers = [i for i, s_ in enumerate(steps) if (s_["kind"] == 6 and s_["slot"] == sl) or
+                           (s_["kind"] in (0, 3) and s_["max_slot"] == sl)]
+                assert len(writers) == 1 and writers[0] < users[0]
+        assert any(s_["max_slot"] >= 0 for s_ in steps)
     for eng in (tn.TN_GEMM_TC_3XTF32, tn.TN_GEMM_TC_BF16X3, tn.TN_GEMM_SIMT_FP32):
         p2 = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True, gemm=eng)
-        assert all(s_["kind"] != 6 for s_ in tn.tn_plan_describe(p2)["steps"])
+        assert all(s_["kind"] != 6 and s_["max_slot"] == -1 and s_["slot"] == -1
+                   for s_ in tn.tn_plan_describe(p2)["steps"])
     bad = copy.deepcopy(cfg["circuit"])
     bad.gates[3].U = bad.gates[3].U * 2.0 ** -40
     tn.tn_plan(bad, cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True, gemm=tn.TN_GEMM_TC_FP16X3)
