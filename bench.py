@@ -274,6 +274,20 @@ def run_ours(args):
                 "peak_note": f"{peak_src} hbm_gbs"}
     roof["dominant_launch_ms"] = round(per_launch[i_dom], 4)
     roof["kernel_time_share"] = {k2: round(v / tot, 4) for k2, v in sorted(kind_totals.items(), key=lambda x: -x[1])}
+    # path roofline: sum over launches of max(flops / peak of the step's engine,
+    # algorithmic bytes / HBM) against the sum of their live times
+    tf32_split = peaks["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
+    f16_split = peaks["bf16_tflops_sustained"] / 3.0
+    simt_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    t_roof = 0.0
+    for i in range(n_launch):
+        kk, m_i, b_i = tn.tn_plan_step_info(plan, i)
+        pk = {3: f16_split if args.engine in ("bf16", "fp16") else tf32_split, 5: simt_peak}.get(kk)
+        t_flop = 8.0 * m_i / (pk * 1e12) if pk else 0.0
+        t_roof += max(t_flop, b_i / (peaks["hbm_gbs"] * 1e9))
+    roof["path_fraction"] = round(t_roof / (tot * 1e-3), 4)
+    roof["path_fraction_note"] = ("sum of per-launch rooflines max(8 MACs / engine peak, bytes / HBM) over the sum "
+                                  "of their live times; GEMM steps of K = 2 counted at the split engine's peak")
 
     out = {
         "metric": "slice TFLOP/s",

@@ -44,13 +44,27 @@ namespace tn {
 namespace tc {
 
 constexpr int BM = 128;
-// K per k-block (one pipeline stage): 64 bytes of each operand row, stored with
-// the 64-byte swizzle, so that a stage is small enough for 4-8 stages to be in
-// flight.  A chunk (one fresh TMEM accumulation) spans CH = 2 k-blocks, i.e.
-// 128 bytes of K: 32 real terms (tf32) or 64 (bf16, fp16).
-constexpr int BK_BYTES = 64;
-constexpr int CH = 128 / BK_BYTES;
-constexpr int KK = BK_BYTES / 32;         // MMAs per product per k-block (32 bytes of K each)
+// K per k-block (one pipeline stage), KB bytes of each operand row: 128 (the
+// 128-byte swizzle) or 64 (the 64-byte swizzle; stages half the size, twice
+// as many in flight, half the MMAs per k-block).  A chunk (one fresh TMEM
+// accumulation) always spans 128 bytes of K: 32 real terms (tf32) or 64
+// (bf16, fp16), i.e. 128 / KB k-blocks.
+// Choice per instantiation (measured on the 30-qubit plan): 128-byte
+// k-blocks for the 16-bit formats up to BN = 128, where the MMAs are short
+// and the per-k-block issue cost shows; 64-byte ones for tf32 and for BN = 256,
+// where more stages in flight hide the TMA latency.
+__host__ __device__ constexpr int kb_bytes(int BN, int FMT) { return (FMT == 0 || BN >= 256) ? 64 : 128; }
+// stages that fit 227 KB of shared memory for a 128 x BN tile
+__host__ __device__ constexpr int kb_stages(int BN, int KB) {
+  return KB == 128 ? (BN <= 16 ? 6 : BN <= 32 ? 5 : BN <= 64 ? 4 : BN <= 128 ? 3 : 2)
+                   : (BN <= 64 ? 8 : BN <= 128 ? 6 : 4);
+}
+
+template <int KB>
+struct KBlock {
+  static constexpr int CH = 128 / KB;     // k-blocks per chunk
+  static constexpr int KK = KB / 32;      // MMAs per product per k-block (32 bytes of K each)
+};
 constexpr int kThreads = 320;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -100,15 +114,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// UMMA shared-memory descriptor: K-major, BK_BYTES-byte swizzle (128 or 64),
-// 8-row groups 8 * BK_BYTES bytes apart.
+// UMMA shared-memory descriptor: K-major, KB-byte swizzle (128 or 64), 8-row
+// groups 8 * KB bytes apart.
+template <int KB>
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)((8 * BK_BYTES) >> 4) << 32;      // stride byte offset
+  d |= (uint64_t)((8 * KB) >> 4) << 32;            // stride byte offset
   d |= (uint64_t)1 << 46;                          // descriptor version
-  d |= (uint64_t)(BK_BYTES == 128 ? 2 : 4) << 61;  // SWIZZLE_128B : SWIZZLE_64B
+  d |= (uint64_t)(KB == 128 ? 2 : 4) << 61;        // SWIZZLE_128B : SWIZZLE_64B
   return d;
 }
 
@@ -163,10 +178,10 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int KB>
 struct Layout {
-  static constexpr int A_BYTES = BM * BK_BYTES;        // one 128-row tile, BK_BYTES of K per row
-  static constexpr int B_BYTES = BN * BK_BYTES;        // one BN-row tile
+  static constexpr int A_BYTES = BM * KB;              // one 128-row tile, KB bytes of K per row
+  static constexpr int B_BYTES = BN * KB;              // one BN-row tile
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;  // A hi, A lo, B hi, B lo
   static constexpr int DATA = STAGES * STAGE;
   static constexpr int TOTAL = DATA + 1024 /*align*/ + 256 /*barriers*/;
@@ -209,7 +224,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t* __restrict__ mapA, const uint32_t* __restrict__ mapB, int mapA_mode, int mapB_mode,
               const unsigned int* scaleA, const unsigned int* scaleB, unsigned int* amax_out,
               unsigned int* status) {
-  using Lay = Layout<BN, STAGES>;
+  constexpr int KB = kb_bytes(BN, FMT);
+  using Lay = Layout<BN, STAGES, KB>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + Lay::DATA);
@@ -227,7 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t pa = mapA_mode == 0 ? pc : (mapA_mode == 1 ? 0 : (int64_t)mapA[pc]);
   const int64_t pb = mapB_mode == 0 ? pc : (mapB_mode == 1 ? 0 : (int64_t)mapB[pc]);
   constexpr bool H16 = FMT != 0;
-  constexpr int BKE = BK_BYTES / (H16 ? 2 : 4);   // K elements per k-block
+  constexpr int BKE = KB / (H16 ? 2 : 4);   // K elements per k-block
+  constexpr int CH = KBlock<KB>::CH, KK = KBlock<KB>::KK;
   const int nkb = (int)((K2 + BKE - 1) / BKE);
 
   if (threadIdx.x == 0) {
@@ -287,13 +304,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int kk = 0; kk < KK; ++kk) {
           const uint32_t o = kk * 32;  // one MMA's K = 32 bytes of each operand row
-          mma<H16>(d, sdesc(a_hi + o), sdesc(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
-          mma<H16>(d, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
+          mma<H16>(d, sdesc<KB>(a_hi + o), sdesc<KB>(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
+          mma<H16>(d, sdesc<KB>(a_lo + o), sdesc<KB>(b_hi + o), idesc, 1u);
         }
 #pragma unroll
         for (int kk = 0; kk < KK; ++kk) {
           const uint32_t o = kk * 32;
-          mma<H16>(d, sdesc(a_hi + o), sdesc(b_hi + o), idesc, 1u);
+          mma<H16>(d, sdesc<KB>(a_hi + o), sdesc<KB>(b_hi + o), idesc, 1u);
         }
         mma_commit(&empty[s]);
         if (last) mma_commit(&accf[b]);
@@ -354,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (amax_out) {
 #pragma unroll
             for (int e = 0; e < 16; ++e)
-              if (col + e < N2) tmax = fmaxf(tmax, fabsf(w[e]));
+              if (col + e < N2) tmax = fmaxf(tmax, fabsf(acc[16 * pp + e]));
           }
           if (col + 16 <= N2) {
             float4* dst = (float4*)(crow + col);
@@ -371,6 +388,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // warp maximum, then the CTA maximum in shared memory (one global
         // atomic per CTA after the final barrier)
         const unsigned int mask = __activemask();
+        // unscaling by powers of two is monotonic: scale the maximum once
+        if (FMT == 2) tmax = (tmax * ua) * ub;
         const unsigned int m = __reduce_max_sync(mask, __float_as_uint(tmax));
         if (lane == __ffs(mask) - 1) atomicMax(s_amax, m);
       }
@@ -406,7 +425,7 @@ static EncodeTiledFn get_encode() {
 }
 
 static bool encode3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
-                     uint32_t b1, int fmt) {
+                     uint32_t b1, int fmt, int kb) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[3] = {d0, d1, d2};
@@ -419,7 +438,7 @@ static bool encode3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1,
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(m, dt, 3, const_cast<void*>(base), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   BK_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   kb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -427,15 +446,17 @@ static bool encode3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1,
 
 template <int BN, int STAGES, int FMT>
 static cudaError_t set_attr() {
-  using Lay = Layout<BN, STAGES>;
+  constexpr int KB = kb_bytes(BN, FMT);
+  using Lay = Layout<BN, STAGES, KB>;
   return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL);
 }
 
 template <int BN, int STAGES, int FMT>
 static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s) {
-  using Lay = Layout<BN, STAGES>;
+  constexpr int KB = kb_bytes(BN, FMT);
+  using Lay = Layout<BN, STAGES, KB>;
   const int64_t K2 = 2 * p.K, N2 = 2 * p.N;
-  const uint32_t BKE = BK_BYTES / (FMT ? 2 : 4);
+  const uint32_t BKE = KB / (FMT ? 2 : 4);
   const int64_t es = FMT ? 2 : 4;
   // A: hi plane then lo plane, each [PA][M][2K]; B: hi plane then lo plane, each [PB][2N][2K]
   const char* ahi = (const char*)p.A;
@@ -443,10 +464,10 @@ static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s
   const char* bhi = (const char*)p.B;
   const char* blo = bhi + p.PB * N2 * K2 * es;
   CUtensorMap tah, tal, tbh, tbl;
-  if (!encode3d(&tah, ahi, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT)) return cudaErrorInvalidValue;
-  if (!encode3d(&tal, alo, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT)) return cudaErrorInvalidValue;
-  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, FMT)) return cudaErrorInvalidValue;
-  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, FMT)) return cudaErrorInvalidValue;
+  if (!encode3d(&tah, ahi, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT, KB)) return cudaErrorInvalidValue;
+  if (!encode3d(&tal, alo, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT, KB)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, FMT, KB)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, FMT, KB)) return cudaErrorInvalidValue;
   const int64_t tilesM = (p.M + BM - 1) / BM, tilesN = (N2 + BN - 1) / BN;
   const int64_t grid = tilesM * tilesN * p.PC;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -460,17 +481,20 @@ static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s
 template <int FMT>
 static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   const int64_t N2 = 2 * p.N;
-  if (N2 <= 16) return run<16, 8, FMT>(p, status, s);
-  if (N2 <= 32) return run<32, 8, FMT>(p, status, s);
-  if (N2 <= 64) return run<64, 8, FMT>(p, status, s);
-  if (N2 <= 128) return run<128, 6, FMT>(p, status, s);
-  return run<256, 4, FMT>(p, status, s);
+  if (N2 <= 16) return run<16, kb_stages(16, kb_bytes(16, FMT)), FMT>(p, status, s);
+  if (N2 <= 32) return run<32, kb_stages(32, kb_bytes(32, FMT)), FMT>(p, status, s);
+  if (N2 <= 64) return run<64, kb_stages(64, kb_bytes(64, FMT)), FMT>(p, status, s);
+  if (N2 <= 128) return run<128, kb_stages(128, kb_bytes(128, FMT)), FMT>(p, status, s);
+  return run<256, kb_stages(256, kb_bytes(256, FMT)), FMT>(p, status, s);
 }
 
 template <int FMT>
 static cudaError_t set_attrs() {
-  const cudaError_t r[5] = {set_attr<16, 8, FMT>(), set_attr<32, 8, FMT>(), set_attr<64, 8, FMT>(),
-                            set_attr<128, 6, FMT>(), set_attr<256, 4, FMT>()};
+  const cudaError_t r[5] = {set_attr<16, kb_stages(16, kb_bytes(16, FMT)), FMT>(),
+                            set_attr<32, kb_stages(32, kb_bytes(32, FMT)), FMT>(),
+                            set_attr<64, kb_stages(64, kb_bytes(64, FMT)), FMT>(),
+                            set_attr<128, kb_stages(128, kb_bytes(128, FMT)), FMT>(),
+                            set_attr<256, kb_stages(256, kb_bytes(256, FMT)), FMT>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
