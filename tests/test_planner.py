@@ -298,3 +298,28 @@ def test_sycamore53_topology_replay_matches_oracle(tn):
     H = emulate(d, tails, oq, [t << d["n_sliced"] for t in range(1 << d["n_internal"])])
     ref = O.network_amplitudes(circ, oq, tails, [], groups=[0, 5])
     assert np.abs(H[[0, 5]] - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_automatic_slicing_of_a_given_order(tn):
+    """A caller's order over the cap is sliced to fit (same leaves, same order)
+    and still replays to the oracle slice by slice; without auto_slice the
+    same order is refused with TN_ERR_OOM."""
+    cfg = _auto_cfg()
+    free = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), host_only=True,
+                      max_log2_elements=30)
+    order = tn.tn_plan_order(free)
+    big = tn.tn_plan_get_stats(free)["max_log2_elements"]
+    cap = big - 2
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), order=order, host_only=True,
+                   max_log2_elements=cap)
+    assert e.value.code == tn.TN_ERR_OOM
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], _edges(cfg), order=order, host_only=True,
+                      max_log2_elements=cap, auto_slice=8)
+    st = tn.tn_plan_get_stats(plan)
+    assert st["n_internal_sliced"] >= 1 and st["max_log2_elements"] <= cap + 1e-9
+    assert np.array_equal(tn.tn_plan_order(plan), order)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    k, ni = st["n_sliced"], st["n_internal_sliced"]
+    H = emulate(d, cfg["tails"], cfg["open_qubits"], [3 | (t << k) for t in range(1 << ni)])
+    assert np.abs(H - _oracle_H(cfg, slice_range=(3, 4))).max() < 1e-12
