@@ -210,7 +210,17 @@ static int build_network(const PlanInput& in, Plan& plan, Builder& b, std::strin
   // final boundary: open legs, tail projectors with a pattern axis
   for (int q = 0; q < n; ++q) {
     int j = find_pos(plan.open_qubits, q);
-    if (j >= 0) {
+    if (j >= 0 && plan.legs[wire[q]].kind == LEG_HALF) {
+      // the open qubit's last wire is fixed by a companion cut of its last
+      // gate: an identity tensor carries the fixed value to a fresh open leg
+      // (its variant v is the unit vector e_v on that leg)
+      int ol = b.new_leg(LEG_OPEN);
+      plan.legs[ol].open_index = j;
+      HostTensor t;
+      t.legs = {wire[q], ol};
+      t.data = {cd(1, 0), cd(0, 0), cd(0, 0), cd(1, 0)};
+      b.T.push_back(t);
+    } else if (j >= 0) {
       plan.legs[wire[q]].kind = LEG_OPEN;
       plan.legs[wire[q]].open_index = j;
     } else {

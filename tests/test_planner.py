@@ -323,3 +323,75 @@ def test_automatic_slicing_of_a_given_order(tn):
     k, ni = st["n_sliced"], st["n_internal_sliced"]
     H = emulate(d, cfg["tails"], cfg["open_qubits"], [3 | (t << k) for t in range(1 << ni)])
     assert np.abs(H - _oracle_H(cfg, slice_range=(3, 4))).max() < 1e-12
+
+
+@pytest.mark.parametrize("case", range(16))
+def test_random_plans_replay_to_the_oracle(tn, case):
+    """Seeded random cases over everything the host planner combines: generic
+    two-qubit gates in both orientations, random open sets and tail counts,
+    SLICE / PIN / COMPANION edges on random gates, host absorption caps, the
+    small-operand threshold, engines (leaf variants and, for FP16x3, scale
+    slots), automatic slicing under a tight cap -- each replayed on the host
+    and compared with the state-vector oracle over a random slice range."""
+    rng = np.random.default_rng(1000 + case)
+    n = int(rng.integers(4, 9))
+    circ = ci.make_random_2q_circuit(n, int(rng.integers(2, 5)), seed=2000 + case)
+    n_open = int(rng.integers(0, min(n, 5) + 1))
+    oq = sorted(int(q) for q in rng.choice(n, n_open, replace=False))
+    L = int(rng.integers(1, min(8, 1 << (n - n_open)) + 1))
+    tails = ci.draw_tails(n, oq, L, seed=3000 + case)
+    twoq = [i for i, g in enumerate(circ.gates) if g.arity == 2]
+    picks = rng.choice(len(twoq), min(len(twoq), int(rng.integers(0, 4))), replace=False)
+    edges, used = [], set()
+    for p in picks:
+        g = twoq[int(p)]
+        leg = int(rng.integers(0, 2))
+        kind = int(rng.choice([tn.TN_EDGE_SLICE, tn.TN_EDGE_PIN, tn.TN_EDGE_COMPANION]))
+        if (g, leg) in used:
+            continue
+        used.add((g, leg))
+        edges.append((g, leg, kind, int(rng.integers(0, 2)) if kind == tn.TN_EDGE_PIN else 0))
+    gemm = int(rng.choice([tn.TN_GEMM_TC_3XTF32, tn.TN_GEMM_TC_FP16X3, tn.TN_GEMM_TC_BF16X3, tn.TN_GEMM_SIMT_FP32]))
+    kw = dict(host_only=True, gemm=gemm, max_host_absorb_log2=int(rng.choice([0, 2, 12])),
+              small_max_bits=int(rng.choice([-1, 2, 4])))
+    free = tn.tn_plan(circ, oq, tails, edges, **kw)
+    big = tn.tn_plan_get_stats(free)["max_log2_elements"]
+    leaves = tn.tn_plan_describe(free)["leaves"]
+    floor = max([np.log2(len(set(int(t) for t in tails))) + n_open] +
+                [np.log2(lf["P"]) + len(lf["dev_legs"]) for lf in leaves])
+    cap = max(float(np.ceil(floor)), big - float(rng.integers(0, 3)))
+    plan = tn.tn_plan(circ, oq, tails, edges, max_log2_elements=cap, auto_slice=12, **kw)
+    st = tn.tn_plan_get_stats(plan)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    k, ni = st["n_sliced"], st["n_internal_sliced"]
+    b = int(rng.integers(0, 1 << k))
+    e = int(rng.integers(b + 1, (1 << k) + 1))
+    H = emulate(d, tails, oq, [s | (t << k) for s in range(b, e) for t in range(1 << ni)])
+    se = [(g, l, True) if kd == tn.TN_EDGE_COMPANION else (g, l) for (g, l, kd, v) in edges
+          if kd != tn.TN_EDGE_PIN]
+    pins = [(g, l, v) for (g, l, kd, v) in edges if kd == tn.TN_EDGE_PIN]
+    ref = O.sparse_state_from_vector(O.sliced_statevector(circ, se, pins=pins, slice_range=(b, e)), oq, tails)
+    scale = max(np.abs(ref).max(), 1e-300)
+    assert np.abs(H - ref).max() <= 1e-11 * scale
+
+
+def test_companion_fixing_an_open_qubit_final_wire(tn):
+    """A companion cut on a qubit pair's last gate fixes the partner's output --
+    here an open qubit's final wire: the amplitudes whose open bit differs from
+    the slice's value vanish in that slice (oracle: the post-gate projector)."""
+    c = ci.make_random_2q_circuit(5, 3, seed=77)
+    last = max(i for i, g in enumerate(c.gates) if g.arity == 2)
+    g = c.gates[last]
+    oq = sorted({g.q0, g.q1})                       # both outputs of the last gate are open
+    tails = ci.draw_tails(5, oq, 3, seed=5)
+    edges = [(last, 0, tn.TN_EDGE_COMPANION, 0)]
+    plan = tn.tn_plan(c, oq, tails, edges, host_only=True)
+    d = tn.tn_plan_describe(plan, with_data=True)
+    for s in (0, 1):
+        H = emulate(d, tails, oq, [s])
+        ref = O.sparse_state_from_vector(O.sliced_statevector(c, [(last, 0, True)], slice_range=(s, s + 1)),
+                                         oq, tails)
+        assert np.abs(H - ref).max() < 1e-12
+        j = oq.index(g.q1)                          # the partner of leg 0 is q1
+        assert all(abs(H[gi, mu]) < 1e-15 for gi in range(len(tails)) for mu in range(1 << len(oq))
+                   if ((mu >> j) & 1) != s)
