@@ -155,6 +155,12 @@ static int build_network(const PlanInput& in, Plan& plan, Builder& b, std::strin
         const int q = c.first == 0 ? q0 : q1;
         const auto& E = in.edges[c.second];
         int old = wire[q];
+        if (plan.legs[old].kind == LEG_HALF) {
+          // the wire is already fixed by a companion cut of the previous gate
+          err = "edge: gate " + std::to_string(gi) + " leg " + std::to_string(c.first) +
+                " cuts a wire that a companion cut already fixes";
+          return TN_ERR_INVALID;
+        }
         int nw = b.new_leg(LEG_HALF);
         plan.legs[old].kind = LEG_HALF;
         if (E.kind == TN_EDGE_SLICE || E.kind == TN_EDGE_COMPANION) {
@@ -239,7 +245,6 @@ static int build_network(const PlanInput& in, Plan& plan, Builder& b, std::strin
       int l = t.legs[pos];
       if (plan.legs[l].kind == LEG_HALF && b.pin_of_leg[l] >= 0) select_leg(t, pos, b.pin_of_leg[l]);
     }
-  (void)err;
   return TN_OK;
 }
 

@@ -395,3 +395,22 @@ def test_companion_fixing_an_open_qubit_final_wire(tn):
         j = oq.index(g.q1)                          # the partner of leg 0 is q1
         assert all(abs(H[gi, mu]) < 1e-15 for gi in range(len(tails)) for mu in range(1 << len(oq))
                    if ((mu >> j) & 1) != s)
+
+
+def test_cut_on_a_wire_fixed_by_a_companion_is_rejected(tn):
+    """A companion cut fixes the partner qubit's output wire; a second cut on
+    that same wire (the next gate's input) is a conflicting request and is
+    refused with TN_ERR_INVALID rather than silently decoupling the wire."""
+    c = ci.make_random_2q_circuit(4, 3, seed=9)
+    twoq = [i for i, g in enumerate(c.gates) if g.arity == 2]
+    g0 = twoq[0]
+    partner = c.gates[g0].q1
+    nxt = next(i for i in range(g0 + 1, len(c.gates)) if partner in (c.gates[i].q0, c.gates[i].q1))
+    leg = 0 if c.gates[nxt].q0 == partner else 1
+    oq = [0, 1]
+    tails = ci.draw_tails(4, oq, 2, seed=1)
+    for kind in (tn.TN_EDGE_SLICE, tn.TN_EDGE_PIN):
+        with pytest.raises(tn.TNError) as e:
+            tn.tn_plan(c, oq, tails, [(g0, 0, tn.TN_EDGE_COMPANION, 0), (nxt, leg, kind, 0)], host_only=True)
+        assert e.value.code == tn.TN_ERR_INVALID
+    tn.tn_plan(c, oq, tails, [(g0, 0, tn.TN_EDGE_COMPANION, 0)], host_only=True)
