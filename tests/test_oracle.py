@@ -357,3 +357,36 @@ def test_frugal_sampling_exact_when_bound_holds_and_xeb():
     mu = (s & np.uint64(l - 1)).astype(np.int64)
     x = 2 ** n_q * P[np.arange(L), mu]
     assert abs(x.mean() - 1 - (l - 1) / (l + 1)) < 3 * x.std() / math.sqrt(L) + 0.01
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_random_cases_two_oracle_routes_agree(case):
+    """O1 (state vector with projectors) and O2 (its own network builder and
+    tensordot order) agree on seeded random circuits with random open sets,
+    tails, sliced edges on one- and two-qubit gates, pins and companion cuts,
+    over a random slice range."""
+    rng = np.random.default_rng(90000 + case)
+    n = int(rng.integers(3, 7))
+    c = ci.make_random_2q_circuit(n, int(rng.integers(1, 4)), seed=91000 + case)
+    n_open = int(rng.integers(0, n))
+    oq = sorted(int(q) for q in rng.choice(n, n_open, replace=False))
+    tails = ci.draw_tails(n, oq, int(rng.integers(1, min(5, 1 << (n - n_open)) + 1)), seed=92000 + case)
+    se, pins, used = [], [], set()
+    for _ in range(int(rng.integers(1, 5))):
+        g = int(rng.integers(0, len(c.gates)))
+        leg = int(rng.integers(0, c.gates[g].arity))
+        if (g, leg) in used:
+            continue
+        used.add((g, leg))
+        r = rng.random()
+        if r < 0.3:
+            pins.append((g, leg, int(rng.integers(0, 2))))
+        elif r < 0.6 and c.gates[g].arity == 2 and (g, 1 - leg) not in used:
+            se.append((g, leg, True))
+        else:
+            se.append((g, leg))
+    b = int(rng.integers(0, 1 << len(se)))
+    e = int(rng.integers(b + 1, (1 << len(se)) + 1))
+    H1 = O.sparse_state_from_vector(O.sliced_statevector(c, se, pins=pins, slice_range=(b, e)), oq, tails)
+    H2 = O.network_amplitudes(c, oq, tails, se, pins=pins, slice_range=(b, e))
+    assert np.abs(H1 - H2).max() <= 1e-12 * max(np.abs(H1).max(), 1e-300)
