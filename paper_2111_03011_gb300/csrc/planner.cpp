@@ -100,7 +100,6 @@ static void select_leg(HostTensor& T, int pos, int v) {
   T.legs.erase(T.legs.begin() + pos);
 }
 
-static double log2_size(const HostTensor& T) { return std::log2((double)T.P()) + (double)T.legs.size(); }
 
 // --------------------------------------------------------------- network build
 

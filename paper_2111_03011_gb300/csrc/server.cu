@@ -123,7 +123,7 @@ int64_t head_bytes_of(tn_plan_t* p) {
 }
 
 // Enqueue one request's device work on its slot (the head is, or will be, ready).
-int enqueue_op(tn_server* sv, Slot& s, Request* q, Circuit& c) {
+int enqueue_op(Slot& s, Request* q, Circuit& c) {
   const tn_request& r = q->r;
   tn_plan_t* p = c.plan;
   const int h = (int)p->P.open_qubits.size();
@@ -301,7 +301,7 @@ void dispatcher(tn_server* sv) {
           cudaEventRecord(c.ready, s.stream);
         }
       }
-      if (rc == TN_OK) rc = enqueue_op(sv, s, q, c);
+      if (rc == TN_OK) rc = enqueue_op(s, q, c);
       if (rc != TN_OK) {
         q->status = rc;
         q->err = "server: enqueue failed";
