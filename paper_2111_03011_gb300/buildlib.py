@@ -58,6 +58,17 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if not force and not _stale():
         return LIBPATH
     os.makedirs(OBJDIR, exist_ok=True)
+    # one builder at a time across processes (e.g. test workers importing the
+    # package together); a waiter finds the library fresh and returns
+    import fcntl
+    with open(os.path.join(LIBDIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not _stale():
+            return LIBPATH
+        return _build_locked(verbose, ptxas_verbose)
+
+
+def _build_locked(verbose: bool, ptxas_verbose: bool) -> str:
     nvcc = _nvcc()
     jobs = []
     for s in CU_SOURCES:
@@ -74,8 +85,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
                      "-c", os.path.join(CSRC, s), "-o", o])
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
-    link = [nvcc, "-shared", *ARCH, "-cudart", "static", "-Xcompiler", "-pthread", "-o", LIBPATH, *_objs()]
+    tmp = LIBPATH + ".tmp"
+    link = [nvcc, "-shared", *ARCH, "-cudart", "static", "-Xcompiler", "-pthread", "-o", tmp, *_objs()]
     logs.append(_run(link))
+    os.replace(tmp, LIBPATH)          # a concurrent loader never sees a partial file
     if verbose:
         for l in logs:
             if l.strip():
