@@ -173,7 +173,26 @@ int  tn_head_set_fidelity(tn_head_t* head, double f_est);
 
 /* Contract slices [begin, end) and add them into the head (FP64).  Asynchronous
  * on `stream`.  A slice already accumulated into this head is rejected
- * (TN_ERR_INVALID) -- ranges are additive and may come from several calls. */
+ * (TN_ERR_INVALID) -- ranges are additive and may come from several calls.
+ * If a launch fails part-way, the whole slices enqueued before it stay
+ * recorded (a retry of the rest of the range is accepted; tn_last_error names
+ * them); if the failure leaves a slice partly accumulated (between the passes
+ * of an automatically sliced plan), the head becomes invalid: every later
+ * call on it returns TN_ERR_INVALID until tn_head_reset.
+ *
+ * Bounded waits.  Every mbarrier wait of the tensor-core GEMM gives up after a
+ * fixed number of polls and sets the plan's device status word instead of
+ * hanging.  The calls that synchronise a stream for a head (tn_amplitudes,
+ * tn_head_norm, tn_sample, tn_sample_ex) read that word after their own work;
+ * a set word is cleared, the head marked invalid and TN_ERR_TIMEOUT returned.
+ *
+ * Fault injection (tests; host side only).  The environment variable
+ * TN_FAULT_INJECT, read on every check, arms one fault: "alloc" (device
+ * allocations of tn_plan and tn_head_create fail with TN_ERR_OOM before any
+ * CUDA call), "slice:S" or "slice:S:T" (the contraction fails with
+ * TN_ERR_CUDA before pass T, default 0, of user slice S), "status" (every
+ * successful tn_contract_slices sets the plan's device status word, as a wait
+ * that gave up would). */
 int  tn_contract_slices(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, void* stream);
 
 /* Batched form.  tn_contract_slices_graph: the same result as
@@ -184,7 +203,9 @@ int  tn_contract_slices(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, 
  * share its workspace), so many small contractions overlap on the GPU; the
  * last batch's graph is cached per thread and replayed when the same batch is
  * submitted again.  Both asynchronous on `stream`; both reject slices already
- * accumulated into a head, and a batch rejects a head listed twice. */
+ * accumulated into a head, and a batch rejects a head listed twice.  Items
+ * with an empty range record nothing.  tn_contract_slices_graph keeps at most
+ * 16 captured ranges per plan and drops the least recently replayed one. */
 int  tn_contract_slices_graph(tn_plan_t* plan, tn_range slice_range, tn_head_t* head, void* stream);
 int  tn_contract_batch(tn_plan_t* const* plans, const tn_range* ranges, tn_head_t* const* heads, int n,
                        void* stream);
@@ -300,9 +321,11 @@ int  tn_plan_step_info(const tn_plan_t* plan, int64_t i, int* kind, double* macs
  * The per-group partial sums live in one fixed device array of
  * TN_NOALLOC_MAX_GROUPS doubles inside the library, which every GPU that loads
  * the library holds until the process exits; larger n_groups are rejected with
- * TN_ERR_INVALID.  The first call on a device looks up that array's device
- * address (once per device, with that device current); make that first call
- * before any stream capture.  All calls share the array and it keeps the last
+ * TN_ERR_INVALID.  A call looks up that array's device address with the
+ * device current; outside a stream capture it does so on every call (so the
+ * address stays right after cudaDeviceReset), inside a capture it uses the
+ * address found by an earlier call on that device, so make the first call on
+ * a device before any stream capture.  All calls share the array and it keeps the last
  * call's contents: calls whose kernels overlap on the GPU (different streams,
  * or different host threads) race on it, so serialise them. */
 int  tn_head_norm_noalloc(const void* head_c128, int64_t n_groups, int n_open, double* norm_out, void* stream);

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -47,6 +48,38 @@ namespace tn {
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace tn
 
+namespace tn {
+// Host-side fault injection: TN_FAULT_INJECT is read on every check, so a
+// test can arm and disarm a fault between calls.
+static std::string fault_env() {
+  const char* e = std::getenv("TN_FAULT_INJECT");
+  return e ? std::string(e) : std::string();
+}
+bool fault_alloc() { return fault_env() == "alloc"; }
+bool fault_slice(int64_t s, int64_t t) {
+  const std::string f = fault_env();
+  if (f.rfind("slice:", 0) != 0) return false;
+  long long S = -1, T = 0;
+  if (std::sscanf(f.c_str() + 6, "%lld:%lld", &S, &T) < 1) return false;
+  return s == S && t == T;
+}
+bool fault_status() { return fault_env() == "status"; }
+
+// After the caller's stream is synchronised: a nonzero device status word of
+// the plan means a bounded wait of a tensor-core GEMM gave up in some
+// contraction of this plan since the last check.  The word is cleared, the
+// head marked invalid and TN_ERR_TIMEOUT returned.
+static int report_status(tn_head_t* h, unsigned int word, cudaStream_t st) {
+  if (!word) return TN_OK;
+  cudaMemsetAsync(h->plan->d_status, 0, sizeof(unsigned int), st);
+  cudaStreamSynchronize(st);
+  h->invalid = true;
+  return fail(TN_ERR_TIMEOUT,
+              "a bounded device wait in a contraction of this plan gave up (status " + std::to_string(word) +
+                  "); the head is invalid until tn_head_reset");
+}
+}  // namespace tn
+
 extern "C" const char* tn_last_error(void) { return g_err.c_str(); }
 extern "C" const char* tn_version(void) { return kVersion; }
 
@@ -77,6 +110,7 @@ extern "C" void tn_plan_free(tn_plan_t* plan) { plan_release(plan); }
 
 static int plan_upload(tn_plan_t* p) {
   tn::Plan& P = p->P;
+  if (tn::fault_alloc()) return fail(TN_ERR_OOM, "device allocation failed (injected: TN_FAULT_INJECT=alloc)");
   CUDA_TRY(cudaGetDevice(&p->device));
   CUDA_TRY(tn::prepare_gemm_tc());
   std::vector<float2> leaves(P.leaf_arena.size());
@@ -245,6 +279,7 @@ extern "C" int tn_head_create(tn_plan_t* plan, void* dev_c128, tn_head_t** out) 
   if (!plan || !out) return fail(TN_ERR_INVALID, "NULL argument");
   *out = nullptr;
   if (!plan->on_device) return fail(TN_ERR_INVALID, "plan was made host_only");
+  if (tn::fault_alloc()) return fail(TN_ERR_OOM, "head allocation failed (injected: TN_FAULT_INJECT=alloc)");
   tn_head* h = new tn_head();
   h->plan = plan;
   const int64_t L = (int64_t)plan->P.tails_raw.size();
@@ -293,6 +328,7 @@ extern "C" int tn_head_reset(tn_head_t* h, void* stream) {
   h->done.clear();
   h->slices_done = 0;
   h->f_override = false;
+  h->invalid = false;
   return TN_OK;
 }
 
@@ -461,13 +497,20 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
 }
 
 // User slice s: every value t of the automatically sliced edges, slice id
-// s | t << k, each pass accumulating into H.
-static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st) {
+// s | t << k, each pass accumulating into H.  *passes_done (if given) counts
+// the passes enqueued whole: a failing pass fails before its accumulation
+// launch, so exactly those passes reach H.
+static int run_slice(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, int64_t* passes_done = nullptr) {
   const int64_t ni = 1LL << p->P.n_internal;
   for (int64_t t = 0; t < ni; ++t) {
+    if (passes_done) *passes_done = t;
+    if (tn::fault_slice(s, t))
+      return fail(TN_ERR_CUDA, "injected failure before pass " + std::to_string(t) + " of slice " + std::to_string(s) +
+                                   " (TN_FAULT_INJECT)");
     int rc = run_pass(p, s | (t << p->P.n_sliced), H, st, nullptr);
     if (rc) return rc;
   }
+  if (passes_done) *passes_done = ni;
   return TN_OK;
 }
 
@@ -475,6 +518,8 @@ static int check_range(tn_plan_t* plan, tn_range r, tn_head_t* head) {
   if (!plan || !head) return fail(TN_ERR_INVALID, "NULL argument");
   if (head->plan != plan) return fail(TN_ERR_INVALID, "head belongs to another plan");
   if (!plan->on_device) return fail(TN_ERR_INVALID, "plan was made host_only");
+  if (head->invalid)
+    return fail(TN_ERR_INVALID, "head is invalid after a failed or timed-out contraction; call tn_head_reset");
   const int64_t ns = 1LL << plan->P.n_sliced;
   if (r.begin < 0 || r.end > ns || r.begin > r.end) return fail(TN_ERR_INVALID, "slice range outside [0, 2^k)");
   auto it = head->done.upper_bound(r.begin);
@@ -489,6 +534,7 @@ static int check_range(tn_plan_t* plan, tn_range r, tn_head_t* head) {
 }
 
 static void mark_done(tn_head_t* head, tn_range r) {
+  if (r.begin >= r.end) return;   // an empty range records nothing (and must not replace [b, e))
   head->done[r.begin] = r.end;
   head->slices_done += r.end - r.begin;
 }
@@ -515,12 +561,14 @@ extern "C" int tn_profile_slices(tn_plan_t* plan, tn_range r, tn_head_t* head, v
     ev.push_back(e);
   }
   int status = TN_OK;
+  int64_t passes_run = 0;
   for (int64_t q0 = 0; q0 < npass && status == TN_OK; q0 += kBatch) {
     const int64_t nb = std::min(kBatch, npass - q0);
     for (int64_t j = 0; j < nb && status == TN_OK; ++j) {
       const int64_t q = r.begin * ni + q0 + j;
       const int64_t s = (q / ni) | ((q % ni) << plan->P.n_sliced);
       status = run_pass(plan, s, head->H, st, ev.data() + 2 * ns * j);
+      if (status == TN_OK) ++passes_run;
     }
     if (status) break;
     cudaError_t e = cudaEventSynchronize(ev[(size_t)(2 * ns * nb - 1)]);
@@ -533,6 +581,7 @@ extern "C" int tn_profile_slices(tn_plan_t* plan, tn_range r, tn_head_t* head, v
       }
   }
   if (status == TN_OK) mark_done(head, r);
+  else if (passes_run > 0) head->invalid = true;   // H holds an unrecorded part of the range
   return status;
 }
 
@@ -560,11 +609,23 @@ extern "C" int tn_contract_slices(tn_plan_t* plan, tn_range r, tn_head_t* head, 
   if (rc) return rc;
   if (r.begin == r.end) return TN_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  for (int64_t s = r.begin; s < r.end; ++s) {
-    rc = run_slice(plan, s, head->H, st);
-    if (rc) return rc;
+  int64_t done_end = r.end;
+  rc = tn::enqueue_slices(plan, r, head->H, st, &done_end);
+  if (rc) {
+    // the whole slices enqueued before the failure stay recorded (a retry of
+    // the rest is accepted); a slice left partly accumulated invalidates H
+    if (done_end < 0) {
+      head->invalid = true;
+      g_err += "; the head holds part of a slice and is invalid until tn_head_reset";
+    } else {
+      mark_done(head, {r.begin, done_end});
+      g_err += "; slices [" + std::to_string(r.begin) + ", " + std::to_string(done_end) + ") were accumulated";
+    }
+    return rc;
   }
   mark_done(head, r);
+  if (tn::fault_status())   // injected: as if a bounded wait of this contraction had given up
+    CUDA_TRY(cudaMemsetAsync(plan->d_status, 1, sizeof(unsigned int), st));
   return TN_OK;
 }
 
@@ -624,9 +685,19 @@ extern "C" int tn_contract_slices_graph(tn_plan_t* plan, tn_range r, tn_head_t* 
     g.H = head->H;
     rc = capture_items({plan}, {r}, {head}, {0}, 1, &g.exec);
     if (rc) return rc;
+    // bounded cache: the least recently replayed graph goes (an in-flight
+    // executable graph is freed by CUDA once its launch completes)
+    constexpr size_t kGraphCache = 16;
+    if (plan->graphs.size() >= kGraphCache) {
+      auto lru = std::min_element(plan->graphs.begin(), plan->graphs.end(),
+                                  [](const GraphEntry& a, const GraphEntry& b) { return a.last_use < b.last_use; });
+      cudaGraphExecDestroy(lru->exec);
+      plan->graphs.erase(lru);
+    }
     plan->graphs.push_back(g);
     hit = &plan->graphs.back();
   }
+  hit->last_use = ++plan->graph_clock;
   CUDA_TRY(cudaGraphLaunch(hit->exec, (cudaStream_t)stream));
   mark_done(head, r);
   return TN_OK;
@@ -698,6 +769,7 @@ extern "C" int tn_amplitudes(tn_head_t* h, const uint64_t* bitstrings, int64_t n
   if (!h || (n > 0 && (!bitstrings || !out))) return fail(TN_ERR_INVALID, "NULL argument");
   if (n < 0) return fail(TN_ERR_INVALID, "n < 0");
   if (dtype != TN_C64 && dtype != TN_C128) return fail(TN_ERR_INVALID, "dtype must be TN_C64 or TN_C128");
+  if (h->invalid) return fail(TN_ERR_INVALID, "head is invalid after a failed or timed-out contraction");
   if (n == 0) return TN_OK;
   tn_plan_t* p = h->plan;
   cudaStream_t st = (cudaStream_t)stream;
@@ -725,7 +797,10 @@ extern "C" int tn_amplitudes(tn_head_t* h, const uint64_t* bitstrings, int64_t n
   unsigned long long status = 0;
   CUDA_TRY(cudaMemcpyAsync(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
   if (!dev_out) CUDA_TRY(cudaMemcpyAsync(out, d_out, (size_t)n * esz, cudaMemcpyDeviceToHost, st));
+  unsigned int word = 0;
+  CUDA_TRY(cudaMemcpyAsync(&word, p->d_status, sizeof(word), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (int rc = tn::report_status(h, word, st)) return rc;
   if (status != ~0ULL)
     return fail(TN_ERR_NOT_IN_STATE, "bitstring " + std::to_string(status) + " has a tail that is not a group");
   return TN_OK;
@@ -733,14 +808,17 @@ extern "C" int tn_amplitudes(tn_head_t* h, const uint64_t* bitstrings, int64_t n
 
 extern "C" int tn_head_norm(tn_head_t* h, double* norm, double* group_norms, void* stream) {
   if (!h) return fail(TN_ERR_INVALID, "NULL head");
+  if (h->invalid) return fail(TN_ERR_INVALID, "head is invalid after a failed or timed-out contraction");
   tn_plan_t* p = h->plan;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t L = (int64_t)p->P.tails_raw.size();
   CUDA_TRY(tn::launch_group_norms(h->H, L, (int)p->P.open_qubits.size(), h->d_Z, h->d_N, st));
   if (norm) CUDA_TRY(cudaMemcpyAsync(norm, h->d_N, sizeof(double), cudaMemcpyDeviceToHost, st));
   if (group_norms) CUDA_TRY(cudaMemcpyAsync(group_norms, h->d_Z, (size_t)L * sizeof(double), cudaMemcpyDeviceToHost, st));
+  unsigned int word = 0;
+  CUDA_TRY(cudaMemcpyAsync(&word, p->d_status, sizeof(word), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
-  return TN_OK;
+  return tn::report_status(h, word, st);
 }
 
 static int sample_impl(tn_head_t* h, int64_t n, double target_fidelity, uint64_t seed, int method, int64_t param,
@@ -766,6 +844,7 @@ static int sample_impl(tn_head_t* h, int64_t n, double target_fidelity, uint64_t
       (method == TN_SAMPLE_FRUGAL && param > (1LL << 20)))
     return fail(TN_ERR_INVALID, "sampling parameter out of range");
   if (n < 0) return fail(TN_ERR_INVALID, "n < 0");
+  if (h->invalid) return fail(TN_ERR_INVALID, "head is invalid after a failed or timed-out contraction");
   if (n == 0) return TN_OK;
   tn_plan_t* p = h->plan;
   double f_head = 0.0;
@@ -798,16 +877,23 @@ static int sample_impl(tn_head_t* h, int64_t n, double target_fidelity, uint64_t
   sp.param = param;
   CUDA_TRY(tn::launch_sample(sp, st));
   if (!dev_out) CUDA_TRY(cudaMemcpyAsync(out, d_out, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+  unsigned int word = 0;
+  CUDA_TRY(cudaMemcpyAsync(&word, p->d_status, sizeof(word), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
-  return TN_OK;
+  return tn::report_status(h, word, st);
 }
 
 namespace tn {
-int enqueue_slices(tn_plan_t* plan, tn_range r, double2* H, cudaStream_t stream) {
+int enqueue_slices(tn_plan_t* plan, tn_range r, double2* H, cudaStream_t stream, int64_t* done_end) {
   for (int64_t s = r.begin; s < r.end; ++s) {
-    int rc = run_slice(plan, s, H, stream);
-    if (rc) return rc;
+    int64_t t = 0;
+    int rc = run_slice(plan, s, H, stream, &t);
+    if (rc) {
+      if (done_end) *done_end = t == 0 ? s : -1;
+      return rc;
+    }
   }
+  if (done_end) *done_end = r.end;
   return TN_OK;
 }
 int check_slice_range(tn_plan_t* plan, tn_range r, tn_head_t* head) { return check_range(plan, r, head); }

@@ -17,6 +17,7 @@ struct GraphEntry {
   int64_t begin = 0, end = 0;
   void* H = nullptr;
   cudaGraphExec_t exec = nullptr;
+  uint64_t last_use = 0;              // LRU stamp (the per-plan cache keeps kGraphCache entries)
 };
 
 namespace tn {
@@ -30,6 +31,7 @@ inline uint64_t next_serial() {
 
 struct tn_plan {
   uint64_t serial = tn::next_serial();
+  uint64_t graph_clock = 0;            // LRU clock of `graphs`
   tn::Plan P;
   double measured_slice_ms = 0.0;
   int autotune_candidates = 0;
@@ -57,6 +59,9 @@ struct tn_head {
   bool owns = false;
   std::map<int64_t, int64_t> done;   // begin -> end of accumulated slice ranges
   int64_t slices_done = 0;
+  // set when H may hold part of a slice (a call failed between the passes of
+  // one slice) or a bounded device wait gave up; cleared by tn_head_reset
+  bool invalid = false;
   bool f_override = false;
   double f_value = 0.0;
   // scratch
@@ -71,7 +76,17 @@ struct tn_head {
 namespace tn {
 void set_last_error(const std::string& msg);
 // Enqueue the slices of `r` of `plan` into H on `stream` (no range checks).
-int enqueue_slices(tn_plan_t* plan, tn_range r, double2* H, cudaStream_t stream);
+// On failure *done_end (if given) is the end of the leading sub-range whose
+// slices were enqueued whole, or -1 if a slice was left partly accumulated.
+int enqueue_slices(tn_plan_t* plan, tn_range r, double2* H, cudaStream_t stream, int64_t* done_end = nullptr);
+// Host-side fault injection (environment variable TN_FAULT_INJECT): true if
+// the named fault is armed.  "alloc": device allocations of plans and heads
+// fail; "slice:S[:T]": the contraction fails before pass T (default 0) of
+// user slice S; "status": each plain contraction call sets the plan's device
+// status word, as a bounded wait that gave up would.
+bool fault_alloc();
+bool fault_slice(int64_t s, int64_t t);
+bool fault_status();
 // Range checks and bookkeeping of tn_contract_slices.
 int check_slice_range(tn_plan_t* plan, tn_range r, tn_head_t* head);
 void mark_slices_done(tn_head_t* head, tn_range r);

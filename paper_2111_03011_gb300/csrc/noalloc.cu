@@ -46,16 +46,24 @@ extern "C" int tn_head_norm_noalloc(const void* head_c128, int64_t n_groups, int
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(TN_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  // Host code sees only a stand-in for the array: its device address is
+  // looked up with the device current.  Outside a stream capture it is looked
+  // up again on every call (cheap, and it allocates nothing), so an address
+  // made stale by cudaDeviceReset (which reloads the module) is never used;
+  // inside a capture the address cached by an earlier call is used.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+  if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[dev]) {
-      // host code sees only a stand-in for the array: fetch its device address
-      // once per device, with that device current
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_group_sums);
       if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_dev_ptr[dev] = (double*)p;
+    } else if (!g_dev_ptr[dev]) {
+      return fail(TN_ERR_INVALID, "the first call on a device must come before any stream capture");
     }
     scratch = g_dev_ptr[dev];
   }

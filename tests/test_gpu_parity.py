@@ -135,6 +135,26 @@ def test_slice_ranges_additive_and_fidelity(tn):
         tn.tn_contract_slices(plan, 0, 17, head)
 
 
+def test_pinned_edges_fidelity_estimate_and_parity(tn):
+    """Method, edge breaking: each PIN edge halves F_est, so a head over a kept
+    range reports F_est = 2^-n_pinned * kept / 2^k; its amplitudes are the
+    oracle's with the same pins and kept slices."""
+    c = ci.make_grid_circuit(4, 4, 8, seed=11)
+    cut = ci.mid_circuit_cut_edges(c, 3)
+    edges = [(g, l, ci.EDGE_PIN, 0) for (g, l, _, _) in cut[:3]] + \
+            [(g, l, ci.EDGE_SLICE, 0) for (g, l, _, _) in cut[3:]]
+    oq = [12, 13, 14, 15]
+    cfg = dict(circuit=c, open_qubits=oq, tails=ci.draw_tails(16, oq, 8, seed=3), edges=edges)
+    for gemm in (1, 4):
+        plan, head = contract_all(tn, cfg, slice_range=(0, 5), gemm=gemm)
+        st = tn.tn_plan_get_stats(plan)
+        assert st["n_pinned"] == 3 and st["n_sliced"] == 3
+        f, done = tn.tn_head_fidelity(head)
+        assert done == 5 and math.isclose(f, 2.0 ** -3 * 5 / 8, rel_tol=1e-15)
+        assert math.isclose(f, O.f_estimate(3, 5, 8), rel_tol=1e-15)
+        assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg, (0, 5)))
+
+
 def test_amplitudes_lookup_dtypes_and_missing(tn):
     import torch
     cfg = ci.config_small(3, 4, 6, seed=5, n_open=4, L=6, n_cut_gates=1)

@@ -208,6 +208,86 @@ def test_sampler_categorical_frequencies_and_mixing():
     assert abs(frac_high - 0.75 * (1 - 8 / 2 ** 20)) < 0.02
 
 
+def test_philox_known_answer_vectors():
+    """Philox-4x32-10 against the published known-answer vectors of the
+    Random123 distribution (Salmon et al., SC'11): counter and key all zero,
+    all ones, and the pi-digit counter/key."""
+    kat = [((0, 0, 0, 0), (0, 0), (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+           ((0xffffffff,) * 4, (0xffffffff,) * 2, (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+           ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+            (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1))]
+    for ctr, key, want in kat:
+        assert O.philox4x32_10(ctr, key) == want
+
+
+def test_linear_xeb_formula():
+    """F_XEB = 2^n <P(s_i)> - 1 (Supplement, validation section) through
+    oracle.linear_xeb, pinned by three closed forms: a computational-basis
+    state sampled exactly scores 2^n - 1; uniformly random bitstrings score 0
+    in expectation; exact samples of a random 16-qubit state score
+    2^n sum P^2 - 1 in expectation (samples drawn with NumPy's own
+    categorical sampler, not the oracle's)."""
+    n = 16
+    P = np.zeros(1 << n)
+    P[12345] = 1.0
+    assert O.linear_xeb(n, P[[12345] * 10]) == 2.0 ** n - 1
+    c = ci.make_grid_circuit(4, 4, 14, seed=31)
+    P = np.abs(O.statevector(c)) ** 2
+    rng = np.random.default_rng(17)
+    N = 40000
+    u = rng.integers(0, 1 << n, N)
+    x = 2.0 ** n * P[u]
+    assert abs(O.linear_xeb(n, P[u])) < 3 * x.std() / math.sqrt(N)
+    s = rng.choice(1 << n, size=N, p=P / P.sum())
+    x = 2.0 ** n * P[s]
+    expect = 2.0 ** n * (P * P).sum() - 1
+    assert abs(O.linear_xeb(n, P[s]) - expect) < 3 * x.std() / math.sqrt(N)
+    assert 0.8 < expect < 1.2
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+def test_pinned_edges_halve_fidelity(seed):
+    """Method, edge breaking: each broken (pinned) edge halves the fidelity, so
+    K pins give F_true ~ f_estimate(K, 1, 1) = 2^-K; the squared norm of the
+    pinned state also tracks 2^-K.  Bands measured on these seeded 16-qubit
+    circuits (ratios 0.95-1.06 for K <= 6); a dropped or doubled factor 2
+    falls far outside them."""
+    c = ci.make_grid_circuit(4, 4, 12, seed=seed)
+    edges = [(g, l) for (g, l, k, v) in ci.mid_circuit_cut_edges(c, 3)]
+    psi = O.statevector(c)
+    for K in range(1, 7):
+        hat = O.statevector(c, [(g, l, 0) for (g, l) in edges[:K]])
+        f = O.f_estimate(K, 1, 1)
+        assert 0.85 < O.fidelity(psi, hat) / f < 1.15, K
+        assert 0.85 < np.vdot(hat, hat).real / f < 1.15, K
+    # with slices: K pins and a kept fraction multiply
+    se = edges[2:4]
+    hat = O.sliced_statevector(c, se, pins=[(g, l, 0) for (g, l) in edges[:2]], slice_range=(0, 2))
+    f = O.f_estimate(2, 2, 4)
+    assert math.isclose(f, 2 ** -2 * 0.5)
+    assert 0.75 < O.fidelity(psi, hat) / f < 1.3
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_c_statevector_matches_numpy_and_brute_force(seed):
+    """The in-place C route of O1 (used for the 30-qubit golden values) equals
+    the NumPy route with cuts and companion cuts, and the brute-force
+    Kronecker route on small circuits; norm 1 without cuts."""
+    from oracle.statevector_c import overlap, statevector_inplace
+    c = ci.make_random_2q_circuit(6, 5, seed=seed)
+    twoq = c.two_qubit_gates()
+    cuts = [(twoq[2], 0, 1), (twoq[4], 1, 0)]
+    a = statevector_inplace(c, cuts)
+    assert np.abs(a - O.brute_force_state(c, cuts)).max() < 1e-13
+    g = ci.make_grid_circuit(4, 4, 10, seed=seed)
+    e = [(gg, l, v) for (gg, l, k, v) in ci.mid_circuit_cut_edges(g, 2, value=1)]
+    post = [(e[0][0], 1, 1)]
+    assert np.abs(statevector_inplace(g, e[:3], post) - O.statevector(g, e[:3], post)).max() < 1e-13
+    psi = statevector_inplace(g)
+    ov, nn = overlap(psi, psi)
+    assert abs(nn - 1) < 1e-12 and abs(ov - 1) < 1e-12
+
+
 def test_philox_words_uniform():
     words = []
     for i in range(4000):
@@ -252,7 +332,13 @@ def test_paper_complexity_and_walltime():
 
 def test_paper_fidelity_estimate():
     f = GOLDEN["fidelity"]
-    F = 2.0 ** -f["K_broken_edges"] * f["rank_one_factor"]
+    # the paper's estimate through the oracle's own formula: K broken edges and
+    # 21 companion edges whose factors multiply to the printed rank-one factor
+    # (equal thetas, solved from ((1 + sin^2 theta)/2)^21 = factor)
+    per = f["rank_one_factor"] ** (1.0 / f["n_companions"])
+    th = math.asin(math.sqrt(2 * per - 1))
+    F = O.f_estimate(f["K_broken_edges"], 1, 1, [th] * f["n_companions"])
+    assert math.isclose(F, 2.0 ** -f["K_broken_edges"] * f["rank_one_factor"], rel_tol=1e-12)
     assert abs(F - f["F_estimate"]) < 0.00005
     # the estimate's structure: 2^-K, kept fraction, companion factors
     th = [math.pi / 2 - 0.1] * 3

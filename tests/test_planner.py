@@ -149,6 +149,24 @@ def test_invalid_inputs_rejected(tn):
     assert e.value.code == tn.TN_ERR_INVALID
 
 
+def test_injected_allocation_failure(tn, monkeypatch):
+    """Host-side fault injection: with TN_FAULT_INJECT=alloc the plan's device
+    upload fails with TN_ERR_OOM before any CUDA call (so this runs without a
+    GPU); host-only planning is unaffected, and disarming restores it."""
+    cfg = ci.config_small(3, 4, 6, seed=5, n_open=4, L=6, n_cut_gates=1)
+    monkeypatch.setenv("TN_FAULT_INJECT", "alloc")
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    assert e.value.code == tn.TN_ERR_OOM and "injected" in str(e.value)
+    p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True)
+    assert tn.tn_plan_get_stats(p)["n_sliced"] == 2
+    monkeypatch.delenv("TN_FAULT_INJECT")
+    try:
+        tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])   # succeeds on a GPU
+    except tn.TNError as e:
+        assert e.code == tn.TN_ERR_CUDA          # without a device the real upload fails in CUDA
+
+
 def test_size_cap_enforced(tn):
     cfg = ci.config_small(4, 4, 8, seed=11, n_open=16, L=1, n_cut_gates=0)
     with pytest.raises(tn.TNError) as e:
