@@ -15,6 +15,14 @@ complex multiply-add, T_c the plan's algorithmic count), device-resident
 inputs; `e2e` is the same metric through the C ABI with host buffers.
 `--impl reference` times the CPU oracle on a bounded sample of the same
 workload instead.
+
+Several GPUs (`--gpus N`, one process per GPU under torch.distributed.run,
+which bench.py starts itself when no launcher did): the kept slice range is
+split into contiguous per-rank ranges, each rank contracts its range into its
+own head, and one host-side sum-reduce of the heads (gloo) gives rank 0 the
+full head, which it looks up, normalises and samples.  Strong scaling: the
+whole job is the same 64 slices at every N.  `--replicas` instead runs the
+whole workload on every GPU (weak scaling).
 """
 from __future__ import annotations
 
@@ -112,6 +120,34 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def workload_config(cfg, n_slices):
+    """The workload as both arms print it: circuit and sparse-state sizes
+    only (no implementation detail), plus how the GPU arm treats L2."""
+    circ = cfg["circuit"]
+    h, L = len(cfg["open_qubits"]), len(cfg["tails"])
+    k = sum(1 for e in cfg["edges"] if e[2] in (ci.EDGE_SLICE, ci.EDGE_COMPANION))
+    return {"workload": cfg["name"], "qubits": circ.n_qubits, "cycles": circ.cycles, "open_qubits": h,
+            "groups": L, "amplitudes": L << h, "sliced_edges": k, "slices": n_slices,
+            "l2": "GPU arm: L2 flushed between timed steps (512 MiB write); intermediates up to 2 GiB exceed L2"}
+
+
+def _free_port():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _spawn_ranks(n):
+    """--gpus N with no launcher around this process: run N ranks of this same
+    command under torch.distributed.run (one process per GPU)."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -143,6 +179,8 @@ def run_ours(args):
 
     import paper_2111_03011_gb300 as tn
 
+    from paper_2111_03011_gb300.shard import reduce_heads, slice_share
+
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -152,13 +190,21 @@ def run_ours(args):
             "fp16": tn.TN_GEMM_TC_FP16X3}[args.engine]
     t0 = time.time()
     popts = cfg.get("plan_opts", {})
-    if args.autotune > 0:
+    trials = ORDER_TRIALS if args.workload == "sliced30" else 0
+    if rank == 0 and args.autotune > 0:
         plan = tn.tn_plan_autotune(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"],
-                                   n_candidates=args.autotune, gemm=gemm,
-                                   order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0, **popts)
-    else:
+                                   n_candidates=args.autotune, gemm=gemm, order_trials=trials, **popts)
+    elif rank == 0:
         plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=gemm,
-                          order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0, **popts)
+                          order_trials=trials, **popts)
+    if ws > 1:
+        # every rank contracts with rank 0's plan: its order goes to the others
+        import torch.distributed as dist
+        box = [tn.tn_plan_order(plan).tolist() if rank == 0 else None]
+        dist.broadcast_object_list(box, src=0)
+        if rank != 0:
+            plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=gemm,
+                              order=np.array(box[0], dtype=np.int32).reshape(-1, 2), **popts)
     plan_s = time.time() - t0
     st = tn.tn_plan_get_stats(plan)
     k = st["n_sliced"]
@@ -184,7 +230,12 @@ def run_ours(args):
     smp_dev = torch.empty(n_samples, dtype=torch.int64, device=dev)
     amp_host = torch.empty(n_amp, dtype=torch.complex128).pin_memory()
     smp_host = torch.empty(n_samples, dtype=torch.int64).pin_memory()
-    head = tn.tn_head_create(plan)
+    head_buf = torch.zeros((L, 1 << h), dtype=torch.complex128, device=dev)
+    head = tn.tn_head_create(plan, head_buf)
+    sharded = ws > 1 and not args.replicas
+    b0, e0_ = slice_share(0, n_slices, rank, ws) if sharded else (0, n_slices)
+    my_slices = e0_ - b0
+    head_host = torch.empty((L, 1 << h), dtype=torch.complex128).pin_memory() if sharded else None
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     n_pass = 1 << int(st["n_internal_sliced"])     # passes of the launch list per slice
     n_launch = int(st["n_launches"]) // n_pass     # launches of one pass
@@ -193,13 +244,25 @@ def run_ours(args):
 
     def step(host_io, profile):
         tn.tn_head_reset(head, stream)
-        if profile:
-            step_ms_acc[:] += tn.tn_profile_slices(plan, 0, n_slices, head, stream)
+        if my_slices == 0:
+            pass
+        elif profile:
+            step_ms_acc[:] += tn.tn_profile_slices(plan, b0, e0_, head, stream)
         elif use_graph:
             # the step's slices replay as one captured CUDA graph (captured in warm-up)
-            tn.tn_contract_slices_graph(plan, 0, n_slices, head, stream)
+            tn.tn_contract_slices_graph(plan, b0, e0_, head, stream)
         else:
-            tn.tn_contract_slices(plan, 0, n_slices, head, stream)
+            tn.tn_contract_slices(plan, b0, e0_, head, stream)
+        if sharded:
+            # the exchange step: sum of the ranks' heads on the host (gloo);
+            # rank 0 continues with the full head
+            head_host.copy_(head_buf, non_blocking=True)
+            stream.synchronize()
+            reduce_heads(head_host)
+            if rank != 0:
+                return
+            head_buf.copy_(head_host, non_blocking=True)
+            tn.tn_head_set_fidelity(head, n_slices / (1 << k))
         if host_io:
             tn.tn_amplitudes(head, bits_pinned, out=amp_host, dtype=tn.TN_C128, stream=stream)
             tn.tn_head_norm(head, stream=stream)
@@ -236,11 +299,14 @@ def run_ours(args):
     clocks = clk.summary()
 
     flops_step = 8.0 * st["tc_macs"] * n_slices
-    value = ws * flops_step / (ms * 1e-3) / 1e12
-    e2e = ws * flops_step / (ms_e2e * 1e-3) / 1e12
+    jobs = ws if (ws > 1 and not sharded) else 1          # replicas each run the whole workload
+    value = jobs * flops_step / (ms * 1e-3) / 1e12
+    e2e = jobs * flops_step / (ms_e2e * 1e-3) / 1e12
+    if rank != 0:
+        return
     peaks, peak_src = _peaks()
     # dominant launch over the timed steps
-    per_launch = step_ms_acc / args.steps / (n_slices * n_pass)   # ms per launch
+    per_launch = step_ms_acc / args.steps / (max(my_slices, 1) * n_pass)   # ms per launch
     i_dom = int(np.argmax(per_launch))
     kind, macs, abytes = tn.tn_plan_step_info(plan, i_dom)
     t_dom = per_launch[i_dom] * 1e-3
@@ -307,25 +373,24 @@ def run_ours(args):
         "warmup": args.warmup,
         "ms_per_step": round(ms, 3),
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if sharded else "weak",
         "vs_baseline": None,
         "dtype": {"bf16": "c64 (bf16x3 GEMM steps)", "fp16": "c64 (fp16x3 GEMM steps)"}.get(args.engine, "c64"),
         "data": "synthetic (seeded Sycamore-like circuit; paper's circuit files not used)",
-        "config": {"workload": cfg["name"], "qubits": st["n_qubits"], "cycles": cfg["circuit"].cycles,
-                   "open_qubits": h, "groups": L, "amplitudes": n_amp, "sliced_edges": k, "slices": n_slices,
-                   "internal_sliced_edges": int(st["n_internal_sliced"]), "passes_per_slice": n_pass,
-                   "max_log2_elements": round(st["max_log2_elements"], 2), "gemm_engine": args.engine,
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "l2": "flushed between timed steps (512 MiB write); intermediates up to 2 GiB exceed L2",
-                   "execution": ("each step replays its slices as one captured CUDA graph (tn_contract_slices_graph)"
-                                 if use_graph else "plain launches (tn_contract_slices)") +
-                                "; the roofline's per-launch times come from a separate timed region of plain "
-                                "launches with CUDA events around each (tn_profile_slices)",
-                   "plan_seconds": round(plan_s, 2), "order_trials": ORDER_TRIALS,
-                   "autotune_candidates": st["autotune_candidates"],
-                   "partial_slices_for_profiling": bool(args.slices)},
-        "amplitudes_per_s": round(ws * n_amp / (ms * 1e-3), 1),
-        "slices_per_s": round(ws * n_slices / (ms * 1e-3), 2),
+        "config": workload_config(cfg, n_slices),
+        "parallelism": (f"slice ranges sharded over {ws} GPUs, heads summed on the host (gloo)" if sharded else
+                        f"replicas x{ws}" if ws > 1 else "single GPU"),
+        "run": {"internal_sliced_edges": int(st["n_internal_sliced"]), "passes_per_slice": n_pass,
+                "max_log2_elements": round(st["max_log2_elements"], 2), "gemm_engine": args.engine,
+                "execution": ("each step replays its slices as one captured CUDA graph (tn_contract_slices_graph)"
+                              if use_graph else "plain launches (tn_contract_slices)") +
+                             "; the roofline's per-launch times come from a separate timed region of plain "
+                             "launches with CUDA events around each (tn_profile_slices)",
+                "plan_seconds": round(plan_s, 2), "order_trials": ORDER_TRIALS,
+                "autotune_candidates": st["autotune_candidates"], "rank0_slices": [b0, e0_],
+                "partial_slices_for_profiling": bool(args.slices)},
+        "amplitudes_per_s": round(jobs * n_amp / (ms * 1e-3), 1),
+        "slices_per_s": round(jobs * n_slices / (ms * 1e-3), 2),
         "ms_per_pass": round(ms / (n_slices * n_pass), 3),
         "tc_macs_per_slice": st["tc_macs"],
         "alg_bytes_per_slice": st["alg_bytes"],
@@ -335,29 +400,40 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clocks,
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(cfg, st)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg)
+    print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(cfg, st, repeats=1):
-    """The oracle (O2 tensordot contraction) on one group of one slice of the
-    same workload; scaled to slice TFLOP/s with the plan's algorithmic flops
-    per (slice, group)."""
+def _oracle_unit(cfg, i):
+    """The oracle (O2, complex128 numpy tensordot) on (slice i mod 2^k, group
+    i mod L) of the workload; returns its complex multiply-adds."""
     import oracle as O
     se = [(g, l) for (g, l, k, v) in cfg["edges"] if k == ci.EDGE_SLICE]
+    k, L = len(se), len(cfg["tails"])
+    stats = {}
+    s = i % (1 << k)
+    O.network_amplitudes(cfg["circuit"], cfg["open_qubits"], cfg["tails"], se, slice_range=(s, s + 1),
+                         groups=[i % L], stats=stats)
+    return stats["complex_macs"]
+
+
+def _oracle_sample_text(cfg):
+    return (f"one (group, slice) unit of {cfg['name']} ({1 << len(cfg['open_qubits'])} amplitude contributions) per "
+            f"step: complex128 numpy tensordot on the oracle's own contraction order; flops = 8 x the oracle's "
+            f"own complex multiply-adds")
+
+
+def cpu_baseline(cfg, repeats=1):
+    """The oracle on one (group, slice) unit of the same workload, as slice
+    TFLOP/s counted on the oracle's own contraction (8 flops per complex
+    multiply-add of its tensordots)."""
     t0 = time.time()
-    for r in range(repeats):
-        O.network_amplitudes(cfg["circuit"], cfg["open_qubits"], cfg["tails"], se, slice_range=(r, r + 1),
-                             groups=[r])
-    dt = (time.time() - t0) / repeats
-    L = int(st["n_tails"])
-    flops_unit = 8.0 * st["tc_macs"] / L
-    return {"value": round(flops_unit / dt / 1e12, 6), "unit": "TFLOP/s", "cores": os.cpu_count(),
-            "kind": "oracle", "seconds_per_unit": round(dt, 2),
-            "sample": f"one group x one slice ({1 << len(cfg['open_qubits'])} amplitude contributions) of "
-                      f"{cfg['name']}, complex128 numpy tensordot; flops = plan T_c per slice / L groups"}
+    macs = sum(_oracle_unit(cfg, r) for r in range(repeats))
+    dt = time.time() - t0
+    return {"value": round(8.0 * macs / dt / 1e12, 6), "unit": "TFLOP/s", "cores": os.cpu_count(),
+            "kind": "oracle", "seconds_per_unit": round(dt / repeats, 2), "complex_macs_per_unit": macs / repeats,
+            "sample": _oracle_sample_text(cfg)}
 
 
 def run_serve(args):
@@ -590,39 +666,29 @@ def run_batch(args):
 
 
 def run_reference(args):
+    """The CPU oracle as the reference arm (the paper ships no code): one
+    (group, slice) unit per step, on the host cores; the product library is
+    not loaded."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import paper_2111_03011_gb300 as tn
     cfg = _workload(args.workload)
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True,
-                      order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0)
-    st = tn.tn_plan_get_stats(plan)
-    import oracle as O
-    se = [(g, l) for (g, l, k, v) in cfg["edges"] if k == ci.EDGE_SLICE]
-    L = int(st["n_tails"])
-    k = len(se)
-
-    def unit(i):
-        O.network_amplitudes(cfg["circuit"], cfg["open_qubits"], cfg["tails"], se,
-                             slice_range=(i % (1 << k), i % (1 << k) + 1), groups=[i % L])
-
+    k = sum(1 for e in cfg["edges"] if e[2] in (ci.EDGE_SLICE, ci.EDGE_COMPANION))
+    n_slices = min(1 << k, args.slices) if args.slices else 1 << k
     for i in range(args.warmup):
-        unit(i)
+        _oracle_unit(cfg, i)
     t0 = time.time()
-    for i in range(args.steps):
-        unit(args.warmup + i)
+    macs = sum(_oracle_unit(cfg, args.warmup + i) for i in range(args.steps))
     dt = (time.time() - t0) / args.steps
-    v = 8.0 * st["tc_macs"] / L / dt / 1e12
-    sample = (f"one group x one slice of {cfg['name']} per step (complex128 numpy tensordot); "
-              f"flops = plan T_c per slice / L groups")
+    v = 8.0 * macs / args.steps / dt / 1e12
     out = {"impl": "reference", "metric": "slice TFLOP/s", "value": round(v, 6), "unit": "TFLOP/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 1),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-           "data": "synthetic", "config": {"workload": cfg["name"]},
+           "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak", "vs_baseline": None,
+           "dtype": "c128", "data": "synthetic", "config": workload_config(cfg, n_slices),
            "cpu_baseline": {"value": round(v, 6), "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": sample},
+                            "seconds_per_unit": round(dt, 2), "complex_macs_per_unit": macs / args.steps,
+                            "sample": _oracle_sample_text(cfg)},
            "e2e": {"value": round(v, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -646,9 +712,17 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--slices", type=int, default=0,
                     help="contract only the first N slices per step (for ncu launch lists; not a bench number)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs, run the whole workload on each (weak scaling) instead of sharding "
+                         "its slices")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(_spawn_ranks(args.gpus))
+    if ws != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={ws}: launch one process per GPU")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serve":

@@ -140,13 +140,16 @@ def _find_order(shapes, out_set, trials=24, seed=0):
     return best[1]
 
 
-def _pairwise(A, la, B, lb, out_set):
+def _pairwise(A, la, B, lb, out_set, stats=None):
     shared = [l for l in la if l in lb and l not in out_set]
     C = np.tensordot(A, B, axes=([la.index(l) for l in shared], [lb.index(l) for l in shared]))
+    if stats is not None:     # complex multiply-adds of this tensordot: |A| |B| / |shared|
+        stats["complex_macs"] = stats.get("complex_macs", 0.0) + float(A.size) * float(B.size) / float(
+            np.prod([A.shape[la.index(l)] for l in shared]) if shared else 1.0)
     return C, [l for l in la if l not in shared] + [l for l in lb if l not in shared]
 
 
-def _absorb_small(T, out_set):
+def _absorb_small(T, out_set, stats=None):
     """Contract every tensor with at most two labels into a neighbour (exact)."""
     changed = True
     while changed and len(T) > 1:
@@ -164,31 +167,32 @@ def _absorb_small(T, out_set):
             o = min(nbrs, key=lambda x: T[x][0].size)
             A, la = T.pop(o)
             B, lb = T.pop(tid)
-            T[o] = _pairwise(A, la, B, lb, out_set)
+            T[o] = _pairwise(A, la, B, lb, out_set, stats)
             changed = True
             break
 
 
-def _contract(net, out_labels):
+def _contract(net, out_labels, stats=None):
     T = net.tensors
     out_set = set(out_labels)
-    _absorb_small(T, out_set)
+    _absorb_small(T, out_set, stats)
     order = _find_order({i: l for i, (_, l) in T.items()}, out_set)
     for (a, b, c) in order:
         A, la = T.pop(a)
         B, lb = T.pop(b)
-        T[c] = _pairwise(A, la, B, lb, out_set)
+        T[c] = _pairwise(A, la, B, lb, out_set, stats)
     (arr, labs), = T.values()
     return arr, labs
 
 
 def network_amplitudes(circ, open_qubits, tails, sliced_edges=(), pins=(), slice_range=None,
-                       groups=None) -> np.ndarray:
+                       groups=None, stats=None) -> np.ndarray:
     """H[g][mu] for the selected groups (all by default), mu bit j = open_qubits[j].
 
     sliced_edges: [(gate, leg)] or [(gate, leg, companion)] enumerated as slice id
     bits (a companion also fixes the partner output, as in sliced_statevector);
-    pins: [(gate, leg, value)]."""
+    pins: [(gate, leg, value)].  stats: optional dict; its "complex_macs" entry
+    is increased by the complex multiply-adds of every tensordot."""
     h = len(open_qubits)
     k = len(sliced_edges)
     if slice_range is None:
@@ -207,7 +211,7 @@ def network_amplitudes(circ, open_qubits, tails, sliced_edges=(), pins=(), slice
                     post.append((e[0], 1 - e[1], v))
             cuts += list(pins)
             net, out_labels = _build(circ, cuts, open_qubits, tails[g], post)
-            arr, labs = _contract(net, out_labels)
+            arr, labs = _contract(net, out_labels, stats)
             # order axes as (open[h-1], ..., open[0]) so C-order flattening gives mu
             perm = [labs.index(out_labels[j]) for j in range(h - 1, -1, -1)]
             arr = np.transpose(arr, perm) if h else arr

@@ -155,6 +155,30 @@ def test_pinned_edges_fidelity_estimate_and_parity(tn):
         assert_close(read_head(tn, plan, head, cfg), oracle_head(cfg, (0, 5)))
 
 
+def test_slice_shares_sum_to_the_full_head(tn):
+    """The multi-GPU split on one GPU: three heads over bench.py's contiguous
+    shares of the 16 slices, summed on the host, equal the full contraction
+    (and the oracle); each head's F_est counts its own share."""
+    from paper_2111_03011_gb300.shard import slice_share
+    cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=4)
+    total = 0
+    parts = []
+    for r in range(3):
+        b, e = slice_share(0, 16, r, 3)
+        h = tn.tn_head_create(plan)
+        tn.tn_contract_slices_graph(plan, b, e, h)
+        assert tn.tn_head_fidelity(h) == ((e - b) / 16, e - b)
+        parts.append(read_head(tn, plan, h, cfg))
+        total += e - b
+    assert total == 16
+    full = tn.tn_head_create(plan)
+    tn.tn_contract_slices(plan, 0, 16, full)
+    Hf = read_head(tn, plan, full, cfg)
+    assert_close(sum(parts), Hf, 1e-6)
+    assert_close(sum(parts), oracle_head(cfg))
+
+
 def test_amplitudes_lookup_dtypes_and_missing(tn):
     import torch
     cfg = ci.config_small(3, 4, 6, seed=5, n_open=4, L=6, n_cut_gates=1)
