@@ -37,6 +37,7 @@ PATTERN_ABCD = "ABCDCDAB"
 # kinds of a cut edge (match the C ABI's TN_EDGE_* values)
 EDGE_SLICE = 0
 EDGE_PIN = 1
+EDGE_COMPANION = 2
 
 
 @dataclass

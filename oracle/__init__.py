@@ -9,8 +9,9 @@ plain, slow, complex128 NumPy written from the paper's definitions:
                        matrix E of the Method section, generalised to value v);
 * ``network``       -- O2: an independent tensor-network builder contracted
                        pairwise with ``numpy.tensordot``, one group at a time;
-* ``metrics``       -- fidelity, the fidelity estimate, linear XEB, the
-                       Porter-Thomas check, the GPU-efficiency formula;
+* ``metrics``       -- fidelity, the fidelity estimate, linear and
+                       logarithmic XEB, entropies, the Porter-Thomas check,
+                       the GPU-efficiency formula;
 * ``sampler``       -- the group sampler and its Philox-4x32-10 generator.
 
 The oracle shares no code with the CUDA path; both read the seeded inputs of
@@ -20,5 +21,6 @@ from .statevector import (statevector, sliced_statevector, sparse_state_from_vec
                           brute_force_state, bitstring_index)
 from .network import network_amplitudes
 from .metrics import (fidelity, f_estimate, companion_factor, linear_xeb, expected_group_sampler_xeb,
-                      porter_thomas_ks, gpu_efficiency, normalised_probabilities)
+                      porter_thomas_ks, gpu_efficiency, normalised_probabilities, log_xeb, entropy,
+                      entropy_from_samples, group_sampling_law, EULER_GAMMA)
 from .sampler import philox4x32_10, sample_groups, sample_groups_mcmc

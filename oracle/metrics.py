@@ -41,6 +41,44 @@ def linear_xeb(n_qubits: int, ideal_probs) -> float:
     return float((2.0 ** n_qubits) * p.mean() - 1.0)
 
 
+EULER_GAMMA = 0.5772156649015329
+
+
+def log_xeb(n_qubits: int, ideal_probs) -> float:
+    """Logarithmic XEB, log(2^n) + gamma + <log P(s_i)> (the logarithmic
+    cross-entropy benchmark the Supplement's validation figure reports beside
+    the linear one).  With x = 2^n P Porter-Thomas distributed, samples drawn
+    from P have E[log x] = 1 - gamma and uniform samples E[log x] = -gamma, so
+    the benchmark is 1 for ideal sampling and 0 for uniform guessing."""
+    p = np.asarray(ideal_probs, dtype=np.float64)
+    return float(n_qubits * math.log(2.0) + EULER_GAMMA + np.log(p).mean())
+
+
+def entropy(p) -> float:
+    """Shannon entropy -sum p log p (natural log) of a distribution; zero
+    entries contribute nothing.  The input is normalised first."""
+    p = np.asarray(p, dtype=np.float64).ravel()
+    p = p / p.sum()
+    nz = p[p > 0]
+    return float(-(nz * np.log(nz)).sum())
+
+
+def entropy_from_samples(probs_at_samples) -> float:
+    """Entropy estimated from samples s_i of a distribution p: -<log p(s_i)>,
+    whose expectation over s_i ~ p is the entropy of p (the sample estimate of
+    the Supplement's entropy figure)."""
+    q = np.asarray(probs_at_samples, dtype=np.float64)
+    return float(-np.log(q).mean())
+
+
+def group_sampling_law(H: np.ndarray) -> np.ndarray:
+    """Probability of each sparse-state member under one-sample-per-group
+    sampling, each group drawn equally often: |H[g][mu]|^2 / (L sum_nu
+    |H[g][nu]|^2)."""
+    w = np.abs(np.asarray(H)) ** 2
+    return w / (w.sum(axis=1, keepdims=True) * w.shape[0])
+
+
 def expected_group_sampler_xeb(H: np.ndarray, P_ideal: np.ndarray, n_qubits: int) -> float:
     """Exact expectation of the linear XEB of one-sample-per-group sampling:
     each group g drawn once with weights |H[g][mu]|^2 / sum_nu |H[g][nu]|^2,

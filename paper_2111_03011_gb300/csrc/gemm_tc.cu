@@ -27,10 +27,21 @@
 //
 // Roles (320 threads): warps 0-7 drain chunk accumulators into the running sum
 // and write the tile out (two warps per TMEM lane quarter, half the columns
-// each), warp 8 issues TMA loads, warp 9 owns TMEM and issues the MMAs.  One
-// CTA computes a 128 x BN tile of C_r.  Every mbarrier wait is
-// bounded; on timeout the CTA records a status code and leaves its loops
-// instead of hanging.
+// each), warp 8 issues TMA loads, warp 9 owns TMEM and issues the MMAs.  The
+// kernel is persistent: one CTA per SM walks 128 x BN tiles of C_r with a
+// stride of the grid, its pipeline and chunk counters running on across
+// tiles, so the loads and MMAs of the next tile proceed while the drain warps
+// write the previous tile out of their registers.
+//
+// Patterns folded into N: when every pattern shares A (the sparse-state
+// batch of one big tensor against many small ones) and 2N is narrower than
+// the tile, one tile covers BN / 2N consecutive patterns side by side (each
+// pattern's B rows loaded as its own box), so narrow steps still run
+// 256-wide MMAs.
+//
+// Every mbarrier wait is bounded; on timeout the CTA records a status code,
+// leaves its loops, waits (again bounded) for its TMA loads and MMAs still in
+// flight, frees its TMEM and exits instead of hanging.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -106,6 +117,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return false;
 }
 
+// Bounded wait that ignores the abort flag: used on the way out, to let
+// copies and MMAs already issued finish before the CTA frees its resources.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_try(bar, parity)) return;
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
@@ -171,7 +189,7 @@ struct Layout {
   static constexpr int DATA = STAGES * STAGE;
   static constexpr int TOTAL = DATA + 1024 /*align*/ + 256 /*barriers*/;
   static_assert(TOTAL <= 232448, "shared memory per CTA");
-  static_assert(2 * STAGES + 6 <= 32, "barrier area");
+  static_assert(2 * STAGES + 8 <= 32, "barrier area");
   // two chunk buffers of BN fp32 columns (ping-pong), a power of two >= 32
   static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
 };
@@ -206,9 +224,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
               const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
               float* __restrict__ C, int64_t M, int64_t N2, int64_t K2, int64_t tilesM, int64_t tilesN, int64_t PC,
-              const uint32_t* __restrict__ mapA, const uint32_t* __restrict__ mapB, int mapA_mode, int mapB_mode,
-              const unsigned int* scaleA, const unsigned int* scaleB, unsigned int* amax_out,
-              unsigned int* status) {
+              int64_t PCg, int fold, const uint32_t* __restrict__ mapA, const uint32_t* __restrict__ mapB,
+              int mapA_mode, int mapB_mode, const unsigned int* scaleA, const unsigned int* scaleB,
+              unsigned int* amax_out, unsigned int* status) {
   constexpr int KB = kb_bytes(BN, FMT);
   using Lay = Layout<BN, STAGES, KB>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -218,19 +236,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty = bars + STAGES;          // stage consumed [STAGES]
   uint64_t* accf = bars + 2 * STAGES;       // chunk accumulated (MMA -> drain) [2]
   uint64_t* acce = bars + 2 * STAGES + 2;   // chunk drained (drain -> MMA)     [2]
-  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * STAGES + 4);
-  volatile int* abort_flag = (volatile int*)(bars + 2 * STAGES + 5);
-  unsigned int* s_amax = (unsigned int*)(bars + 2 * STAGES + 6);   // CTA maximum of the output tile
+  uint64_t* mma_done = bars + 2 * STAGES + 4;   // every issued MMA complete (before TMEM is freed)
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = (volatile int*)(bars + 2 * STAGES + 6);
+  unsigned int* s_amax = (unsigned int*)(bars + 2 * STAGES + 7);   // CTA maximum of its output tiles
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t pc, tm, tn_;
-  tile_coords(blockIdx.x, tilesM, tilesN, PC, mapA_mode == 1 && PC > 1, pc, tm, tn_);
-  const int64_t pa = mapA_mode == 0 ? pc : (mapA_mode == 1 ? 0 : (int64_t)mapA[pc]);
-  const int64_t pb = mapB_mode == 0 ? pc : (mapB_mode == 1 ? 0 : (int64_t)mapB[pc]);
+  const bool a_shared = mapA_mode == 1 && PC > 1;
+  const int64_t n_tiles = tilesM * tilesN * PCg;
+  const int br = BN / fold;                 // B rows per pattern box (2N when folded)
   constexpr bool H16 = FMT != 0;
   constexpr int BKE = KB / (H16 ? 2 : 4);   // K elements per k-block
   constexpr int CH = KBlock<KB>::CH, KK = KBlock<KB>::KK;
   const int nkb = (int)((K2 + BKE - 1) / BKE);
+  const int nch = (nkb + CH - 1) / CH;
+  // tile t -> first pattern pc0 of its group, m-tile, n-tile
+  auto coords = [&](int64_t t, int64_t& pc0, int64_t& tm, int64_t& tn_) {
+    int64_t pg;
+    tile_coords(t, tilesM, tilesN, PCg, a_shared, pg, tm, tn_);
+    pc0 = pg * fold;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -241,6 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 256);
     }
+    mbar_init(mma_done, 1);
     *abort_flag = 0;
     *s_amax = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -258,47 +284,84 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 8) {
     if (lane == 0) {
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES, r = kb / STAGES;
-        if (!mbar_wait(&empty[s], (uint32_t)((r & 1) ^ 1), abort_flag)) break;
-        uint8_t* st = smem + s * Lay::STAGE;
-        mbar_expect_tx(&full[s], (uint32_t)Lay::STAGE);
-        tma_load_3d(st, &tmAhi, &full[s], kb * BKE, (int)(tm * BM), (int)pa);
-        tma_load_3d(st + Lay::A_BYTES, &tmAlo, &full[s], kb * BKE, (int)(tm * BM), (int)pa);
-        tma_load_3d(st + 2 * Lay::A_BYTES, &tmBhi, &full[s], kb * BKE, (int)(tn_ * BN), (int)pb);
-        tma_load_3d(st + 2 * Lay::A_BYTES + Lay::B_BYTES, &tmBlo, &full[s], kb * BKE, (int)(tn_ * BN), (int)pb);
+      uint32_t it = 0;          // k-blocks issued by this CTA (all tiles)
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        int64_t pc0, tm, tn_;
+        coords(t, pc0, tm, tn_);
+        const int64_t pa = mapA_mode == 0 ? pc0 : (mapA_mode == 1 ? 0 : (int64_t)mapA[pc0]);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = (int)(it % STAGES);
+          const uint32_t r = it / STAGES;
+          if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
+          uint8_t* st = smem + s * Lay::STAGE;
+          mbar_expect_tx(&full[s], (uint32_t)Lay::STAGE);
+          tma_load_3d(st, &tmAhi, &full[s], kb * BKE, (int)(tm * BM), (int)pa);
+          tma_load_3d(st + Lay::A_BYTES, &tmAlo, &full[s], kb * BKE, (int)(tm * BM), (int)pa);
+          for (int f = 0; f < fold; ++f) {
+            // a pattern past the last one loads pattern PC - 1 again: its
+            // columns are computed but never stored
+            const int64_t pcf = pc0 + f < PC ? pc0 + f : PC - 1;
+            const int64_t pb = mapB_mode == 0 ? pcf : (mapB_mode == 1 ? 0 : (int64_t)mapB[pcf]);
+            uint8_t* sb = st + 2 * Lay::A_BYTES + f * br * KB;
+            tma_load_3d(sb, &tmBhi, &full[s], kb * BKE, (int)(tn_ * br), (int)pb);
+            tma_load_3d(sb + Lay::B_BYTES, &tmBlo, &full[s], kb * BKE, (int)(tn_ * br), (int)pb);
+          }
+          ++it;
+        }
+      }
+      if (!ok) {
+        // only the last STAGES issued k-blocks can still be landing
+        for (uint32_t j = it > (uint32_t)STAGES ? it - STAGES : 0; j < it; ++j)
+          mbar_drain(&full[j % STAGES], (j / STAGES) & 1);
       }
     }
   } else if (warp == 9) {
     if (lane == 0) {
       const uint32_t idesc = idesc_mma<BN, FMT>();
-      for (int kb = 0; kb < nkb; ++kb) {
-        // chunk c = kb / CH accumulates in TMEM buffer b = c & 1 from zero
-        const int s = kb % STAGES, r = kb / STAGES;
-        const int c = kb / CH, b = c & 1, u = c >> 1;   // u: use index of buffer b
-        const bool first = kb % CH == 0, last = kb % CH == CH - 1 || kb == nkb - 1;
-        if (first && !mbar_wait(&acce[b], (uint32_t)((u & 1) ^ 1), abort_flag)) break;
-        if (!mbar_wait(&full[s], (uint32_t)(r & 1), abort_flag)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t d = tmem + (uint32_t)(b * BN);
-        const uint32_t st = smem_u32(smem + s * Lay::STAGE);
-        const uint32_t a_hi = st, a_lo = st + Lay::A_BYTES;
-        const uint32_t b_hi = st + 2 * Lay::A_BYTES, b_lo = b_hi + Lay::B_BYTES;
-        // small correction products first, so that the accumulator is still
-        // small while they are added; the hi x hi products come last
+      uint32_t it = 0, cc = 0;   // k-blocks and chunks consumed by this CTA (all tiles)
+      bool ok = true, issued = false;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        for (int kb = 0; kb < nkb; ++kb) {
+          // chunk cc accumulates in TMEM buffer b = cc & 1 from zero
+          const int s = (int)(it % STAGES);
+          const uint32_t r = it / STAGES;
+          const int b = (int)(cc & 1);
+          const uint32_t u = cc >> 1;   // use index of buffer b
+          const bool first = kb % CH == 0, last = kb % CH == CH - 1 || kb == nkb - 1;
+          if (first && !mbar_wait(&acce[b], (u & 1) ^ 1, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&full[s], r & 1, abort_flag)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t d = tmem + (uint32_t)(b * BN);
+          const uint32_t st = smem_u32(smem + s * Lay::STAGE);
+          const uint32_t a_hi = st, a_lo = st + Lay::A_BYTES;
+          const uint32_t b_hi = st + 2 * Lay::A_BYTES, b_lo = b_hi + Lay::B_BYTES;
+          // small correction products first, so that the accumulator is still
+          // small while they are added; the hi x hi products come last
 #pragma unroll
-        for (int kk = 0; kk < KK; ++kk) {
-          const uint32_t o = kk * 32;  // one MMA's K = 32 bytes of each operand row
-          mma<H16>(d, sdesc<KB>(a_hi + o), sdesc<KB>(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
-          mma<H16>(d, sdesc<KB>(a_lo + o), sdesc<KB>(b_hi + o), idesc, 1u);
-        }
+          for (int kk = 0; kk < KK; ++kk) {
+            const uint32_t o = kk * 32;  // one MMA's K = 32 bytes of each operand row
+            mma<H16>(d, sdesc<KB>(a_hi + o), sdesc<KB>(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
+            mma<H16>(d, sdesc<KB>(a_lo + o), sdesc<KB>(b_hi + o), idesc, 1u);
+          }
 #pragma unroll
-        for (int kk = 0; kk < KK; ++kk) {
-          const uint32_t o = kk * 32;
-          mma<H16>(d, sdesc<KB>(a_hi + o), sdesc<KB>(b_hi + o), idesc, 1u);
+          for (int kk = 0; kk < KK; ++kk) {
+            const uint32_t o = kk * 32;
+            mma<H16>(d, sdesc<KB>(a_hi + o), sdesc<KB>(b_hi + o), idesc, 1u);
+          }
+          issued = true;
+          mma_commit(&empty[s]);
+          if (last) {
+            mma_commit(&accf[b]);
+            ++cc;
+          }
+          ++it;
         }
-        mma_commit(&empty[s]);
-        if (last) mma_commit(&accf[b]);
+      }
+      // every issued MMA has completed before TMEM is freed (also on abort)
+      if (issued) {
+        mma_commit(mma_done);
+        mbar_drain(mma_done, 0);
       }
     }
   } else {
@@ -312,72 +375,81 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool active = BN >= 32 || half == 0;
     const int col0 = BN >= 32 ? half * NCOL : 0;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    float acc[NCOL];
-#pragma unroll
-    for (int e = 0; e < NCOL; ++e) acc[e] = 0.0f;
+    // FP16 engine: undo the operands' power-of-two scales (two exact multiplies)
+    const float ua = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleA)) : 1.0f;
+    const float ub = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleB)) : 1.0f;
+    float tmax = 0.0f;
+    uint32_t cc = 0;
     bool ok = true;
-    const int nch = (nkb + CH - 1) / CH;
-    for (int c = 0; c < nch && ok; ++c) {
-      const int b = c & 1, u = c >> 1;
-      ok = mbar_wait(&accf[b], (uint32_t)(u & 1), abort_flag);
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (active) {
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      int64_t pc0, tm, tn_;
+      coords(t, pc0, tm, tn_);
+      float acc[NCOL];
 #pragma unroll
-        for (int p0 = 0; p0 < NPIECE; p0 += RP) {
-          uint32_t v[RP][16];
+      for (int e = 0; e < NCOL; ++e) acc[e] = 0.0f;
+      for (int c = 0; c < nch; ++c) {
+        const int b = (int)(cc & 1);
+        const uint32_t u = cc >> 1;
+        ok = mbar_wait(&accf[b], u & 1, abort_flag);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (active) {
 #pragma unroll
-          for (int j = 0; j < RP; ++j)
-            tmem_ld16(tmem + lane_base + (uint32_t)(b * BN) + (uint32_t)(col0 + 16 * (p0 + j)), v[j]);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          for (int p0 = 0; p0 < NPIECE; p0 += RP) {
+            uint32_t v[RP][16];
 #pragma unroll
-          for (int j = 0; j < RP; ++j)
+            for (int j = 0; j < RP; ++j)
+              tmem_ld16(tmem + lane_base + (uint32_t)(b * BN) + (uint32_t)(col0 + 16 * (p0 + j)), v[j]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int e = 0; e < 16; ++e) acc[16 * (p0 + j) + e] += __uint_as_float(v[j][e]);
+            for (int j = 0; j < RP; ++j)
+#pragma unroll
+              for (int e = 0; e < 16; ++e) acc[16 * (p0 + j) + e] += __uint_as_float(v[j][e]);
+          }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        mbar_arrive(&acce[b]);
+        ++cc;
       }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      mbar_arrive(&acce[b]);
-    }
-    if (ok && active) {
-      // FP16 engine: undo the operands' power-of-two scales (two exact multiplies)
-      const float ua = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleA)) : 1.0f;
-      const float ub = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleB)) : 1.0f;
+      if (!ok || !active) continue;
+      // the tile's rows go out from registers while the MMAs of the next
+      // tile fill the (now drained) TMEM buffers
       const int64_t row = tm * BM + q * 32 + lane;
-      float tmax = 0.0f;
-      if (row < M) {
+      if (row >= M) continue;
+#pragma unroll
+      for (int pp = 0; pp < NPIECE; ++pp) {
+        const int cl = col0 + 16 * pp;             // column within the tile
+        const int f = cl / br;                     // pattern of the fold
+        const int64_t pc = pc0 + f;
+        const int64_t col = tn_ * br + (cl - f * br);
+        if (pc >= PC) continue;
         float* crow = C + (pc * M + row) * N2;
+        float w[16];
 #pragma unroll
-        for (int pp = 0; pp < NPIECE; ++pp) {
-          float w[16];
+        for (int e = 0; e < 16; ++e) w[e] = FMT == 2 ? (acc[16 * pp + e] * ua) * ub : acc[16 * pp + e];
+        if (amax_out) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) w[e] = FMT == 2 ? (acc[16 * pp + e] * ua) * ub : acc[16 * pp + e];
-          const int64_t col = tn_ * BN + col0 + 16 * pp;
-          if (amax_out) {
+          for (int e = 0; e < 16; ++e)
+            if (col + e < N2) tmax = fmaxf(tmax, fabsf(acc[16 * pp + e]));
+        }
+        if (col + 16 <= N2) {
+          float4* dst = (float4*)(crow + col);
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (col + e < N2) tmax = fmaxf(tmax, fabsf(acc[16 * pp + e]));
-          }
-          if (col + 16 <= N2) {
-            float4* dst = (float4*)(crow + col);
+          for (int e = 0; e < 4; ++e) dst[e] = make_float4(w[4 * e], w[4 * e + 1], w[4 * e + 2], w[4 * e + 3]);
+        } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) dst[e] = make_float4(w[4 * e], w[4 * e + 1], w[4 * e + 2], w[4 * e + 3]);
-          } else {
-#pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (col + e < N2) crow[col + e] = w[e];
-          }
+          for (int e = 0; e < 16; ++e)
+            if (col + e < N2) crow[col + e] = w[e];
         }
       }
-      if (amax_out) {
-        // warp maximum, then the CTA maximum in shared memory (one global
-        // atomic per CTA after the final barrier)
-        const unsigned int mask = __activemask();
-        // unscaling by powers of two is monotonic: scale the maximum once
-        if (FMT == 2) tmax = (tmax * ua) * ub;
-        const unsigned int m = __reduce_max_sync(mask, __float_as_uint(tmax));
-        if (lane == __ffs(mask) - 1) atomicMax(s_amax, m);
-      }
+    }
+    if (amax_out && active) {
+      // warp maximum, then the CTA maximum in shared memory (one global
+      // atomic per CTA after the final barrier); unscaling by powers of two is
+      // monotonic, so the maximum is scaled once
+      if (FMT == 2) tmax = (tmax * ua) * ub;
+      const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(tmax));
+      if (lane == 0) atomicMax(s_amax, m);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -436,11 +508,22 @@ static cudaError_t set_attr() {
   return cudaFuncSetAttribute(k_gemm_tc<BN, STAGES, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::TOTAL);
 }
 
+static int sm_count() {
+  static int n[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!n[dev] && cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n[dev] = 152;
+  return n[dev] > 0 ? n[dev] : 152;
+}
+
+// fold = patterns per tile side by side along N (1: none); see the kernel
 template <int BN, int STAGES, int FMT>
-static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s) {
+static cudaError_t run(const GemmParams& p, int fold, unsigned int* status, cudaStream_t s) {
   constexpr int KB = kb_bytes(BN, FMT);
   using Lay = Layout<BN, STAGES, KB>;
   const int64_t K2 = 2 * p.K, N2 = 2 * p.N;
+  const int br = BN / fold;
+  if (fold > 1 && (br != N2 || br < 16 || p.mapA_mode != 1)) return cudaErrorInvalidValue;
   const uint32_t BKE = KB / (FMT ? 2 : 4);
   const int64_t es = FMT ? 2 : 4;
   // A: hi plane then lo plane, each [PA][M][2K]; B: hi plane then lo plane, each [PB][2N][2K]
@@ -451,26 +534,40 @@ static cudaError_t run(const GemmParams& p, unsigned int* status, cudaStream_t s
   CUtensorMap tah, tal, tbh, tbl;
   if (!encode3d(&tah, ahi, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT, KB)) return cudaErrorInvalidValue;
   if (!encode3d(&tal, alo, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT, KB)) return cudaErrorInvalidValue;
-  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, FMT, KB)) return cudaErrorInvalidValue;
-  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, BN, FMT, KB)) return cudaErrorInvalidValue;
-  const int64_t tilesM = (p.M + BM - 1) / BM, tilesN = (N2 + BN - 1) / BN;
-  const int64_t grid = tilesM * tilesN * p.PC;
-  if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_gemm_tc<BN, STAGES, FMT><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(tah, tal, tbh, tbl, (float*)p.C, p.M, N2,
-                                                                            K2, tilesM, tilesN, p.PC, p.mapA, p.mapB,
-                                                                            p.mapA_mode, p.mapB_mode, p.scaleA,
-                                                                            p.scaleB, p.amax, status);
+  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, br, FMT, KB)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, br, FMT, KB)) return cudaErrorInvalidValue;
+  const int64_t tilesM = (p.M + BM - 1) / BM, tilesN = fold > 1 ? 1 : (N2 + BN - 1) / BN;
+  const int64_t PCg = (p.PC + fold - 1) / fold;
+  const int64_t n_tiles = tilesM * tilesN * PCg;
+  if (n_tiles <= 0) return cudaSuccess;
+  // persistent: at most one CTA per SM (the pipeline's shared memory allows one)
+  const int64_t grid = std::min<int64_t>(n_tiles, sm_count());
+  k_gemm_tc<BN, STAGES, FMT><<<(unsigned)grid, kThreads, Lay::TOTAL, s>>>(
+      tah, tal, tbh, tbl, (float*)p.C, p.M, N2, K2, tilesM, tilesN, p.PC, PCg, fold, p.mapA, p.mapB, p.mapA_mode,
+      p.mapB_mode, p.scaleA, p.scaleB, p.amax, status);
   return cudaGetLastError();
 }
 
+// Tile width: the smallest of 16..256 that covers 2N, or, when all patterns
+// share A and 2N >= 16, up to 256 columns of consecutive patterns folded side
+// by side (fold = BN / 2N, as many as the pattern count rounded up to a power
+// of two allows).
 template <int FMT>
 static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStream_t s) {
   const int64_t N2 = 2 * p.N;
-  if (N2 <= 16) return run<16, kb_stages(16, kb_bytes(16, FMT)), FMT>(p, status, s);
-  if (N2 <= 32) return run<32, kb_stages(32, kb_bytes(32, FMT)), FMT>(p, status, s);
-  if (N2 <= 64) return run<64, kb_stages(64, kb_bytes(64, FMT)), FMT>(p, status, s);
-  if (N2 <= 128) return run<128, kb_stages(128, kb_bytes(128, FMT)), FMT>(p, status, s);
-  return run<256, kb_stages(256, kb_bytes(256, FMT)), FMT>(p, status, s);
+  int64_t w = N2;
+  int fold = 1;
+  if (p.mapA_mode == 1 && p.PC > 1 && N2 >= 16 && N2 < 256) {
+    while (w < 256 && fold < p.PC) {
+      w *= 2;
+      fold *= 2;
+    }
+  }
+  if (w <= 16) return run<16, kb_stages(16, kb_bytes(16, FMT)), FMT>(p, fold, status, s);
+  if (w <= 32) return run<32, kb_stages(32, kb_bytes(32, FMT)), FMT>(p, fold, status, s);
+  if (w <= 64) return run<64, kb_stages(64, kb_bytes(64, FMT)), FMT>(p, fold, status, s);
+  if (w <= 128) return run<128, kb_stages(128, kb_bytes(128, FMT)), FMT>(p, fold, status, s);
+  return run<256, kb_stages(256, kb_bytes(256, FMT)), FMT>(p, fold, status, s);
 }
 
 template <int FMT>
@@ -488,8 +585,9 @@ static cudaError_t set_attrs() {
 }  // namespace tc
 
 cudaError_t prepare_gemm_tc() {
-  // the opt-in shared-memory size, set once per device before any launch (and
-  // so before any stream capture)
+  // the opt-in shared-memory size and the SM count, set once per device before
+  // any launch (and so before any stream capture)
+  tc::sm_count();
   cudaError_t e = tc::set_attrs<0>();
   const cudaError_t e1 = tc::set_attrs<1>(), e2 = tc::set_attrs<2>();
   if (e == cudaSuccess) e = e1;

@@ -245,6 +245,60 @@ def test_linear_xeb_formula():
     assert 0.8 < expect < 1.2
 
 
+def test_log_xeb_closed_forms():
+    """Logarithmic XEB through oracle.log_xeb: 1 for exact sampling and 0 for
+    uniform sampling of a Porter-Thomas state (E[log x] = 1 - gamma and
+    -gamma for x = 2^n P), n log 2 + gamma for a basis state sampled exactly;
+    the samples come from NumPy's categorical and uniform generators."""
+    n = 16
+    P = np.zeros(1 << n)
+    P[7] = 1.0
+    assert math.isclose(O.log_xeb(n, P[[7, 7, 7]]), n * math.log(2) + O.EULER_GAMMA, rel_tol=1e-14)
+    c = ci.make_grid_circuit(4, 4, 14, seed=31)
+    P = np.abs(O.statevector(c)) ** 2
+    rng = np.random.default_rng(5)
+    N = 60000
+    s = rng.choice(1 << n, size=N, p=P / P.sum())
+    u = rng.integers(0, 1 << n, N)
+    for samples, want in ((s, 1.0), (u, 0.0)):
+        y = np.log(2.0 ** n * P[samples])
+        assert abs(O.log_xeb(n, P[samples]) - want) < 3 * y.std() / math.sqrt(N) + 0.02
+
+
+def test_entropy_closed_forms_and_sample_estimate():
+    """Entropy of a uniform law over 2^k outcomes is k log 2; a Porter-Thomas
+    law over N outcomes has entropy log N - 1 + gamma (to O(1/sqrt N)); the
+    sample estimate -<log p(s_i)> of samples drawn from p (NumPy's sampler)
+    matches the exact entropy within its standard error."""
+    for k in (1, 5, 12):
+        assert math.isclose(O.entropy(np.ones(1 << k)), k * math.log(2), rel_tol=1e-13)
+    assert O.entropy([0.5, 0.5, 0.0]) == math.log(2)
+    c = ci.make_grid_circuit(4, 4, 14, seed=31)
+    P = np.abs(O.statevector(c)) ** 2
+    Nn = P.size
+    assert abs(O.entropy(P) - (math.log(Nn) - 1 + O.EULER_GAMMA)) < 0.02
+    rng = np.random.default_rng(9)
+    s = rng.choice(Nn, size=50000, p=P / P.sum())
+    y = -np.log(P[s])
+    assert abs(O.entropy_from_samples(P[s]) - O.entropy(P)) < 3 * y.std() / math.sqrt(s.size)
+
+
+def test_group_sampling_law_matches_sampler_frequencies():
+    """The law of one-sample-per-group draws: each group equally often, inside
+    a group |H|^2 normalised; checked against the oracle sampler's counts
+    (chi-squared) and against its closed-form expected XEB."""
+    H = ci.synthetic_head(4, 3, seed=8)
+    q = O.group_sampling_law(H)
+    assert abs(q.sum() - 1) < 1e-14 and np.allclose(q.sum(axis=1), 0.25)
+    n = 40000
+    s = O.sample_groups(H, np.arange(4, dtype=np.uint64) << np.uint64(3), [0, 1, 2], 5, n, 0.0, 1.0, seed=3)
+    cnt = np.bincount(s.astype(np.int64), minlength=32).reshape(4, 8)
+    chi2 = ((cnt - n * q) ** 2 / (n * q)).sum()
+    assert chi2 < 61.1                                   # chi2(31) 99.9%
+    Pid = np.abs(ci.synthetic_head(4, 3, seed=9)) ** 2 / 2 ** 5
+    assert math.isclose((q * Pid).sum() * 2 ** 5 - 1, O.expected_group_sampler_xeb(H, Pid, 5), rel_tol=1e-12)
+
+
 @pytest.mark.parametrize("seed", [21, 22, 23])
 def test_pinned_edges_halve_fidelity(seed):
     """Method, edge breaking: each broken (pinned) edge halves the fidelity, so

@@ -1,0 +1,161 @@
+"""Every launch of a plan stays inside the memory it is given (CPU, no GPU).
+
+For each step of the plan's launch list (from tn_plan_describe), the bytes
+each kernel reads and writes -- as the kernels index them: pattern strides,
+split planes, real embeddings, gather tables -- must lie inside the workspace
+buffer or leaf variant it is handed, every table index inside the meta
+buffer, and buffers that are live at the same time must not overlap.  A
+launch that wrote past its buffer (for example a split permute writing two
+operand planes into space sized for one) fails here before it ever runs on a
+GPU.
+"""
+import numpy as np
+import pytest
+
+import circuit_inputs as ci
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import paper_2111_03011_gb300 as m
+    return m
+
+
+ST_SMALL, ST_PERMUTE, ST_BPREP_TC, ST_GEMM_TC, ST_BPREP_C, ST_GEMM_SIMT, ST_ABSMAX = range(7)
+
+
+def _check_plan(d):
+    meta = np.asarray(d["meta"], dtype=np.int64)
+    bufs = d["bufs"]
+    ws = d["workspace_bytes"]
+    leaf_info = d["leaf_info"]
+    for off, nbytes, first, last in bufs:
+        assert 0 <= off and off + nbytes <= ws
+    for i, (o1, b1, f1, l1) in enumerate(bufs):           # live at the same time -> disjoint
+        for (o2, b2, f2, l2) in bufs[i + 1:]:
+            if f1 <= l2 and f2 <= l1:
+                assert o1 + b1 <= o2 or o2 + b2 <= o1
+    for off, size, nvar in leaf_info:
+        assert off + size * (1 << nvar) <= d["leaf_arena_elems"]
+
+    def cap(ref):
+        """bytes available behind an operand reference"""
+        kind, rid = ref
+        return 8 * leaf_info[rid][1] if kind == 0 else bufs[rid][1]
+
+    def table(mode, off, n, bound):
+        """largest pattern index a map of `n` entries yields (mode 0 identity, 1 zero, 2 table)"""
+        if mode == 0:
+            return n - 1
+        if mode == 1:
+            return 0
+        assert off + n <= meta.size
+        t = meta[off:off + n]
+        assert (t >= 0).all() and (t < bound).all()
+        return int(t.max())
+
+    for i, s in enumerate(d["steps"]):
+        k = s["kind"]
+        if k == ST_SMALL:
+            pa = table(*s["mapA"], s["PC"], s["PA"])
+            pb = table(*s["mapB"], s["PC"], s["PB"])
+            assert 8 * (pa + 1) << s["rA"] <= cap(s["a"])
+            assert 8 * (pb + 1) << s["rB"] <= cap(s["b"])
+            assert 8 * s["PC"] << s["rC"] <= cap(s["c"])
+            assert s["rA"] - s["nk"] + s["nn"] == s["rC"]
+            assert all(0 <= x < s["rA"] for x in s["kposA"][:s["nk"]])
+        elif k == ST_PERMUTE:
+            n = s["PA"] << s["rA"]
+            assert 8 * n <= cap(s["a"])
+            per = {0: 8, 1: 16, 2: 8, 3: 8}[s["split"]]       # bytes written per complex element (both planes)
+            assert per * n <= cap(s["c"]), (i, s["split"])
+            t = s["t_bits"]
+            assert t + s["n_rest"] == s["rA"] and s["n_rest"] <= 32
+            assert s["tab_off"] + 3 * (1 << t) <= meta.size
+            tab = meta[s["tab_off"]:s["tab_off"] + 3 * (1 << t)]
+            assert (tab >= 0).all() and (tab < (1 << s["rA"])).all()
+            assert all(0 <= x < s["rA"] for x in s["rest_in"] + s["rest_out"])
+        elif k in (ST_BPREP_TC, ST_BPREP_C):
+            assert 8 * s["PA"] << s["rA"] <= cap(s["a"])
+            K, N = 1 << s["nk"], 1 << s["nn"]
+            assert s["bk_off"] + K <= meta.size and s["bn_off"] + N <= meta.size
+            assert max(meta[s["bk_off"]:s["bk_off"] + K].max(), meta[s["bn_off"]:s["bn_off"] + N].max()) < (
+                1 << s["rA"])
+            if k == ST_BPREP_TC:
+                es = 4 if s["h16"] == 0 else 2
+                assert 2 * s["PA"] * (2 * N) * (2 * K) * es <= cap(s["c"])
+            else:
+                assert 8 * s["PA"] * K * N <= cap(s["c"])
+        elif k in (ST_GEMM_TC, ST_GEMM_SIMT):
+            M, N, K = 1 << s["nm"], 1 << s["nn"], 1 << s["nk"]
+            pa = table(*s["mapA"], s["PC"], s["PA"])
+            pb = table(*s["mapB"], s["PC"], s["PB"])
+            assert pa < s["PA"] and pb < s["PB"]
+            if k == ST_GEMM_TC:
+                es = 4 if s["h16"] == 0 else 2
+                assert 2 * K * es >= 16                        # TMA row pitch
+                assert 2 * s["PA"] * M * (2 * K) * es <= cap(s["a"])
+                assert 2 * s["PB"] * (2 * N) * (2 * K) * es <= cap(s["b"])
+            else:
+                assert 8 * s["PA"] * M * K <= cap(s["a"])
+                assert 8 * s["PB"] * K * N <= cap(s["b"])
+            assert 8 * s["PC"] * M * N <= cap(s["c"])
+        elif k == ST_ABSMAX:
+            assert 8 * s["PA"] << s["rA"] <= cap(s["a"])
+        else:
+            raise AssertionError(f"unknown step kind {k}")
+    f = d["final"]
+    L = len(d.get("_tails", [])) or None
+    assert 8 * f["PF"] << f["rF"] <= cap(f["ref"])
+    assert all(0 <= x < f["rF"] for x in f["open_pos"])
+    pidx = meta[f["pidx_off"]:f["pidx_off"] + (L or 1)]
+    assert (pidx >= 0).all() and (pidx < f["PF"]).all()
+
+
+CASES = [dict(r=3, c=4, m=6, seed=5, n_open=4, L=6, cut=1),
+         dict(r=4, c=4, m=8, seed=11, n_open=6, L=8, cut=2),
+         dict(r=2, c=4, m=8, seed=6, n_open=0, L=5, cut=1),
+         dict(r=4, c=5, m=10, seed=13, n_open=8, L=24, cut=2),
+         dict(r=3, c=5, m=12, seed=17, n_open=5, L=64, cut=3)]
+ENGINES = [dict(gemm=1), dict(gemm=2), dict(gemm=3), dict(gemm=4), dict(gemm=4, small_max_bits=-1),
+           dict(gemm=1, small_max_bits=-1), dict(gemm=4, small_max_bits=2)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c['r']}x{c['c']}m{c['m']}L{c['L']}" for c in CASES])
+def test_launch_extents_inside_buffers(tn, case):
+    cfg = ci.config_small(case["r"], case["c"], case["m"], seed=case["seed"], n_open=case["n_open"], L=case["L"],
+                          n_cut_gates=case["cut"])
+    for eng in ENGINES:
+        p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True, **eng)
+        d = tn.tn_plan_describe(p, with_data=True)
+        d["_tails"] = list(cfg["tails"])
+        _check_plan(d)
+
+
+def test_launch_extents_auto_sliced_and_random_gates(tn):
+    cfg = ci.config_small(4, 5, 10, seed=13, n_open=8, L=24, n_cut_gates=1)
+    for gemm in (1, 3, 4):
+        p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True, gemm=gemm,
+                       max_log2_elements=15, auto_slice=16)
+        d = tn.tn_plan_describe(p, with_data=True)
+        d["_tails"] = list(cfg["tails"])
+        _check_plan(d)
+    for seed in (1, 2, 3):
+        c = ci.make_random_2q_circuit(10, 4, seed=seed)
+        oq = [1, 4, 7]
+        tails = ci.draw_tails(10, oq, 16, seed=seed)
+        for gemm in (1, 4):
+            p = tn.tn_plan(c, oq, tails, host_only=True, gemm=gemm, small_max_bits=-1)
+            d = tn.tn_plan_describe(p, with_data=True)
+            d["_tails"] = list(tails)
+            _check_plan(d)
+
+
+def test_launch_extents_of_the_30_qubit_workload(tn):
+    cfg = ci.config_sliced30()
+    for gemm in (1, 4):
+        p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True, gemm=gemm,
+                       order_trials=2048)
+        d = tn.tn_plan_describe(p, with_data=True)
+        d["_tails"] = list(cfg["tails"])
+        _check_plan(d)
