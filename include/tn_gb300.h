@@ -103,6 +103,10 @@ typedef struct {
                                  intermediates).  These internal edges take slice bits k, k+1, ...
                                  and are summed inside every user slice, so slice ids, F_est and
                                  the head are those of the k user edges, exactly. */
+  int    host_fold_log2;      /* host folding: a contraction of the order whose operands are both
+                                 host tensors (leaves or earlier folds) and whose result has at most
+                                 2^this elements (and at most 2^6 slice variants) is done on the host
+                                 in FP64 at plan time and becomes a leaf (0: 12; -1: off) */
 } tn_plan_opts;
 
 typedef struct tn_plan tn_plan_t;
@@ -115,7 +119,7 @@ typedef struct {
   int64_t n_patterns;         /* distinct tails (rows of the final pattern axis) */
   int     n_sliced;           /* k */
   int     n_pinned;           /* PIN edges (each halves F_est) */
-  int     n_leaves;           /* tensors left after host simplification */
+  int     n_leaves;           /* device leaves: tensors left after host simplification and folding */
   int     n_contractions;     /* pairwise contractions per slice */
   int     n_launches;         /* kernel launches per slice (steps incl. permutes/prep + accumulate) */
   double  tc_macs;            /* T_c: complex multiply-adds per slice (algorithmic) */

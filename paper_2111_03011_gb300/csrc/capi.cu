@@ -205,6 +205,8 @@ extern "C" int tn_plan(const tn_circuit* circuit, const tn_open_spec* open_spec,
     if (opts->small_max_bits != 0) in.small_max_bits = opts->small_max_bits < 0 ? -1 : std::min(4, opts->small_max_bits);
     if (opts->auto_slice < 0 || opts->auto_slice > 24) return fail(TN_ERR_INVALID, "auto_slice must be in [0, 24]");
     in.auto_slice = opts->auto_slice;
+    if (opts->host_fold_log2 > 16) return fail(TN_ERR_INVALID, "host_fold_log2 must be at most 16");
+    if (opts->host_fold_log2 != 0) in.fold_log2 = opts->host_fold_log2 < 0 ? -1 : opts->host_fold_log2;
   }
   if (in.gemm_engine < 0 || in.gemm_engine > 4) return fail(TN_ERR_INVALID, "unknown gemm engine");
   if (in.cap_log2 > 34) return fail(TN_ERR_INVALID, "size cap above 2^34 elements");

@@ -1022,6 +1022,102 @@ static void build_leaves(Plan& plan, const std::vector<HostTensor>& T) {
   }
 }
 
+// Two half legs of one tensor that carry the same slice bit (the two ends of
+// a cut edge, brought together by a host contraction) always take the same
+// value: keep the entries where they agree and drop the second leg.
+static void merge_half_legs(const Plan& plan, HostTensor& T) {
+  for (bool again = true; again;) {
+    again = false;
+    for (size_t a = 0; a < T.legs.size() && !again; ++a)
+      for (size_t b = a + 1; b < T.legs.size() && !again; ++b) {
+        const Leg& La = plan.legs[T.legs[a]];
+        const Leg& Lb = plan.legs[T.legs[b]];
+        if (La.kind != LEG_HALF || Lb.kind != LEG_HALF || La.slice_bit != Lb.slice_bit) continue;
+        const int r = (int)T.legs.size();
+        const int64_t n_old = 1LL << r, n_new = 1LL << (r - 1);
+        std::vector<cd> d((size_t)(T.P() * n_new));
+        const int64_t lo_mask = (1LL << b) - 1;
+        for (int64_t p = 0; p < T.P(); ++p)
+          for (int64_t i = 0; i < n_new; ++i) {
+            const int64_t v = (i >> a) & 1;    // leg b takes leg a's value
+            const int64_t src = ((i & ~lo_mask) << 1) | (v << b) | (i & lo_mask);
+            d[(size_t)(p * n_new + i)] = T.data[(size_t)(p * n_old + src)];
+          }
+        T.data.swap(d);
+        T.legs.erase(T.legs.begin() + b);
+        again = true;
+      }
+  }
+}
+
+// Host folding.  A contraction of the order whose two operands are host
+// tensors (leaves, or results folded before) and whose result is small
+// (pattern axis times device legs at most 2^fold_log2 elements, at most 2^6
+// slice variants) is carried out here, once, in FP64, and its result becomes a
+// leaf: the device then runs only the contractions that involve an
+// intermediate.  A pair sharing an automatically sliced leg (one leg id on
+// both operands, summed by the passes of a slice) is left to the device.
+// On return `device_order` holds the remaining pairs over the new leaves and
+// plan.leaves / leaf_info / vts describe those leaves.
+static void fold_small(Plan& plan, const std::vector<std::pair<int, int>>& slot_order, int fold_log2,
+                       std::vector<std::pair<int, int>>& device_order) {
+  const int nleaf = (int)plan.leaves.size();
+  std::vector<HostTensor> T = plan.leaves;
+  std::vector<char> host(nleaf, 1), is_leaf(nleaf, 0);
+  std::vector<int> newslot(nleaf, -1);
+  std::vector<std::pair<int, int>> dev;
+  auto use_on_device = [&](int s) {   // the tensor in slot s (leaf or fold) is a device leaf
+    if (host[s]) {
+      host[s] = 0;
+      is_leaf[s] = 1;
+    }
+  };
+  int last = -1;
+  for (auto pr : slot_order) {
+    const int i = pr.first, j = pr.second;
+    last = i;
+    if (fold_log2 >= 0 && host[i] && host[j]) {
+      bool shared_half = false;
+      int dev_legs = 0, half_bits = 0;
+      std::vector<int> bits;
+      for (int l : T[i].legs) {
+        const bool in_b = find_pos(T[j].legs, l) >= 0;
+        if (plan.legs[l].kind == LEG_HALF && in_b) shared_half = true;
+        if (in_b) continue;
+        if (plan.legs[l].kind == LEG_HALF) bits.push_back(plan.legs[l].slice_bit); else ++dev_legs;
+      }
+      for (int l : T[j].legs) {
+        if (find_pos(T[i].legs, l) >= 0) continue;
+        if (plan.legs[l].kind == LEG_HALF) bits.push_back(plan.legs[l].slice_bit); else ++dev_legs;
+      }
+      std::sort(bits.begin(), bits.end());
+      half_bits = (int)(std::unique(bits.begin(), bits.end()) - bits.begin());
+      const double lsz = std::log2((double)plan.book.count(T[i].tq | T[j].tq)) + dev_legs;
+      if (!shared_half && lsz <= fold_log2 + 1e-9 && half_bits <= 6) {
+        T[i] = contract_host(T[i], T[j], plan.book);
+        merge_half_legs(plan, T[i]);
+        host[j] = 0;
+        continue;
+      }
+    }
+    use_on_device(i);
+    use_on_device(j);
+    dev.push_back(pr);
+  }
+  if (dev.empty()) is_leaf[last >= 0 ? last : 0] = 1;   // everything folded: the result is the only leaf
+  // device leaves keep the order of their slots (with nothing folded, the
+  // leaves and their ids are those of the simplified network)
+  std::vector<HostTensor> leaves;
+  for (int s = 0; s < nleaf; ++s)
+    if (is_leaf[s]) {
+      newslot[s] = (int)leaves.size();
+      leaves.push_back(T[s]);
+    }
+  device_order.clear();
+  for (auto& pr : dev) device_order.push_back({newslot[pr.first], newslot[pr.second]});
+  build_leaves(plan, leaves);
+}
+
 // Slice `legs` (bond legs between leaves) as internal edges: each becomes a
 // half leg with slice bit k, k+1, ... on both leaves that hold it.
 static void apply_internal_slices(Plan& plan, const std::vector<HostTensor>& T, const std::vector<int>& legs) {
@@ -1161,17 +1257,21 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
     if (rc) return rc;
     if (!cut.empty()) apply_internal_slices(plan, b.T, cut);
   }
+  // keep the user-visible order in slot form (over the simplified leaves)
+  std::vector<std::pair<int, int>> saved_slots = slot_order;
+  // small contractions of host tensors become leaves; the device runs the rest
+  std::vector<std::pair<int, int>> device_order;
+  fold_small(plan, slot_order, in.fold_log2, device_order);
+  const int ndev = (int)plan.leaves.size();
   // translate slot pairs to virtual-tensor pairs
-  std::vector<int> slot_vt(nleaf);
-  for (int i = 0; i < nleaf; ++i) slot_vt[i] = i;
+  std::vector<int> slot_vt(ndev);
+  for (int i = 0; i < ndev; ++i) slot_vt[i] = i;
   plan.order.clear();
   std::vector<std::pair<int, int>> vt_pairs;
-  for (auto& pr : slot_order) {
+  for (auto& pr : device_order) {
     vt_pairs.push_back({slot_vt[pr.first], slot_vt[pr.second]});
-    slot_vt[pr.first] = nleaf + (int)vt_pairs.size() - 1;
+    slot_vt[pr.first] = ndev + (int)vt_pairs.size() - 1;
   }
-  // keep the user-visible order in slot form
-  std::vector<std::pair<int, int>> saved_slots = slot_order;
   plan.order = vt_pairs;
   plan.max_log2 = 0;
   for (auto& v : plan.vts) plan.max_log2 = std::max(plan.max_log2, std::log2((double)v.P) + (double)v.legs.size());
@@ -1182,7 +1282,7 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
   plan.order = saved_slots;
 
   // final tensor
-  int fvt = nleaf == 1 && slot_order.empty() ? 0 : (int)plan.vts.size() - 1;
+  int fvt = ndev == 1 && device_order.empty() ? 0 : (int)plan.vts.size() - 1;
   if (nleaf == 0) { err = "empty network"; return TN_ERR_INVALID; }
   const VTensor& F = plan.vts[fvt];
   // the final tensor must carry exactly the open legs and every tail projector

@@ -181,6 +181,7 @@ struct PlanInput {
   int absorb_log2 = 12;
   int small_max_bits = 4;
   int auto_slice = 0;       // at most this many extra sliced edges when no order fits the cap
+  int fold_log2 = 12;       // host folding of small contractions of host tensors (-1: off)
 };
 
 int build_plan(const PlanInput& in, Plan& plan, std::string& err);

@@ -43,9 +43,9 @@ def _close(H, ref):
 
 def test_injected_allocation_failure_on_device(tn, monkeypatch):
     cfg = _cfg()
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_fold_log2=-1)
     monkeypatch.setenv("TN_FAULT_INJECT", "alloc")
-    for make in (lambda: tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"]),
+    for make in (lambda: tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_fold_log2=-1),
                  lambda: tn.tn_head_create(plan)):
         with pytest.raises(tn.TNError) as e:
             make()
@@ -60,7 +60,7 @@ def test_failure_at_slice_keeps_completed_slices(tn, monkeypatch):
     """A failure before slice 5 of [0, 16): slices 0-4 stay recorded, a retry
     of [5, 16) is accepted, a retry of [0, 16) is not, and the sum is exact."""
     cfg = _cfg()
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=4)
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=4, host_fold_log2=-1)
     head = tn.tn_head_create(plan)
     monkeypatch.setenv("TN_FAULT_INJECT", "slice:5")
     with pytest.raises(tn.TNError) as e:
@@ -81,7 +81,7 @@ def test_failure_inside_a_slice_invalidates_the_head(tn, monkeypatch):
     after the first pass leaves the slice partly in H, so the head refuses
     every call until it is reset."""
     cfg = ci.config_small(4, 5, 10, seed=13, n_open=8, L=24, n_cut_gates=1)
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], max_log2_elements=15,
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], max_log2_elements=15, host_fold_log2=-1,
                       auto_slice=16)
     assert tn.tn_plan_get_stats(plan)["n_internal_sliced"] >= 1
     head = tn.tn_head_create(plan)
@@ -106,7 +106,7 @@ def test_device_status_word_reports_timeout(tn, monkeypatch):
     synchronising call; the head is then invalid until reset, and the word is
     cleared."""
     cfg = _cfg()
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=4)
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=4, host_fold_log2=-1)
     for read in (lambda h: _head(tn, cfg, h), lambda h: tn.tn_head_norm(h), lambda h: tn.tn_sample(h, 4, 0.0, 1)):
         head = tn.tn_head_create(plan)
         monkeypatch.setenv("TN_FAULT_INJECT", "status")
@@ -127,7 +127,7 @@ def test_empty_batch_item_keeps_the_range_record(tn):
     """An empty range in a batch records nothing: [0, 4) stays accumulated and
     contracting it again is still rejected."""
     cfg = _cfg()
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_fold_log2=-1)
     head = tn.tn_head_create(plan)
     tn.tn_contract_slices(plan, 0, 4, head)
     tn.tn_contract_batch([plan], [(0, 0)], [head])
@@ -143,7 +143,7 @@ def test_graph_cache_is_bounded_and_replays_correctly(tn):
     """More distinct captured ranges than the per-plan cache holds: the oldest
     graphs are dropped and every replay still adds exactly its slices."""
     cfg = _cfg()
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_fold_log2=-1)
     heads = [tn.tn_head_create(plan) for _ in range(2)]
     for rep in range(2):
         for h in heads:

@@ -6,6 +6,7 @@ relative L2 <= 1e-5 over the whole head tensor (and every element to within
 bit-exact except where an FP64 prefix sum sits within rounding of a draw.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -31,6 +32,9 @@ def rel_l2(a, b):
 
 
 def contract_all(tn, cfg, slice_range=None, **plan_kw):
+    # host folding off unless asked for: these small circuits would otherwise
+    # fold mostly on the host and leave little for the kernels under test
+    plan_kw.setdefault("host_fold_log2", -1)
     plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], **plan_kw)
     head = tn.tn_head_create(plan)
     k = tn.tn_plan_get_stats(plan)["n_sliced"]
@@ -65,9 +69,9 @@ def assert_close(H, ref, tol=REL_L2):
 
 ENGINES = [dict(gemm=0), dict(gemm=2), dict(gemm=0, small_max_bits=-1), dict(gemm=2, small_max_bits=-1),
            dict(gemm=0, small_max_bits=2), dict(gemm=3), dict(gemm=3, small_max_bits=-1), dict(gemm=4),
-           dict(gemm=4, small_max_bits=-1)]
+           dict(gemm=4, small_max_bits=-1), dict(gemm=4, host_fold_log2=0), dict(gemm=0, host_fold_log2=8)]
 ENGINE_IDS = ["tc", "simt", "tc-allgemm", "simt-allgemm", "tc-small2", "bf16", "bf16-allgemm", "fp16",
-              "fp16-allgemm"]
+              "fp16-allgemm", "fp16-fold", "tc-fold8"]
 
 
 def tol_of(eng):
@@ -118,7 +122,7 @@ def test_generic_two_qubit_gates_all_gemm(tn, seed):
 
 def test_slice_ranges_additive_and_fidelity(tn):
     cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)   # 16 slices
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_fold_log2=-1)
     head = tn.tn_head_create(plan)
     tn.tn_contract_slices(plan, 0, 4, head)
     f, done = tn.tn_head_fidelity(head)
@@ -161,7 +165,7 @@ def test_slice_shares_sum_to_the_full_head(tn):
     (and the oracle); each head's F_est counts its own share."""
     from paper_2111_03011_gb300.shard import slice_share
     cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=4)
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=4, host_fold_log2=-1)
     total = 0
     parts = []
     for r in range(3):
@@ -217,7 +221,7 @@ def _synthetic_head(tn, L, h, seed, n_qubits=30):
     tails = ci.draw_tails(n_qubits, oq, L, seed=seed)
     c = ci.make_grid_circuit(2, 2, 1, seed=1)       # plan only carries the sparse-state layout here
     c.n_qubits = n_qubits
-    plan = tn.tn_plan(c, oq, tails)
+    plan = tn.tn_plan(c, oq, tails, host_fold_log2=-1)
     H = ci.synthetic_head(L, h, seed)
     buf = torch.from_numpy(H.copy()).cuda()
     head = tn.tn_head_create(plan, buf)              # zeroes the buffer
@@ -307,6 +311,39 @@ def test_sliced30_full_size_properties(tn):
     assert O.porter_thomas_ks(p / p.mean()) < 0.02
 
 
+_SLICED30_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sliced30_o1.npz")
+
+
+@pytest.mark.parametrize("gemm", [1, 3, 4], ids=["tc3xtf32", "bf16x3", "fp16x3"])
+def test_sliced30_all_amplitudes_vs_stored_o1(tn, gemm):
+    """The full 30-qubit, 14-cycle workload in the bench's launch
+    configuration (the autotuned plan, all 64 slices replayed as one captured
+    graph): every one of the 65,536 sparse-state amplitudes against the O1
+    state vector stored by tests/golden/make_sliced30_golden.py (by the
+    slice-sum identity, the uncut circuit).  The kept prefixes [0, 32) and
+    [0, 16) are compared with the O1 runs that pin the top slice bits to 0,
+    and their fidelity estimates with O1's exact fidelity."""
+    g = np.load(_SLICED30_GOLDEN)
+    cfg = ci.config_sliced30()
+    assert np.array_equal(g["tails"], np.asarray(cfg["tails"], dtype=np.uint64))
+    assert list(g["open_qubits"]) == list(cfg["open_qubits"])
+    assert [tuple(e) for e in g["edges"]] == [(a, b) for (a, b, _, _) in cfg["edges"]]
+    tol = tol_of(dict(gemm=gemm))
+    plan = tn.tn_plan_autotune(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], n_candidates=4,
+                               order_trials=2048, gemm=gemm)
+    head = tn.tn_head_create(plan)
+    tn.tn_contract_slices_graph(plan, 0, 64, head)
+    assert_close(read_head(tn, plan, head, cfg), g["H_full"], tol)
+    for kept in g["prefixes"]:
+        kept = int(kept)
+        h = tn.tn_head_create(plan)
+        tn.tn_contract_slices_graph(plan, 0, kept, h)
+        assert_close(read_head(tn, plan, h, cfg), g[f"H_{kept}"], tol)
+        f_est, done = tn.tn_head_fidelity(h)
+        assert done == kept and math.isclose(f_est, kept / 64)
+        assert abs(float(g[f"F_true_{kept}"]) / f_est - 1) < 0.05     # the kept fraction tracks the fidelity
+
+
 _SLICED30_REF = {}
 
 
@@ -336,7 +373,7 @@ def test_sliced30_full_size_sampled_groups_vs_oracle(tn, gemm):
 
 def test_profile_and_reset(tn):
     cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_fold_log2=-1)
     head = tn.tn_head_create(plan)
     ms = tn.tn_profile_slices(plan, 0, 16, head)
     st = tn.tn_plan_get_stats(plan)
@@ -418,7 +455,7 @@ def test_graph_replay_equals_plain_launches(tn):
     """Batched form: the slice range captured as a CUDA graph and replayed
     gives bit-identical heads to the plain launches (same kernels, order)."""
     cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)
-    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_fold_log2=-1)
     h1 = tn.tn_head_create(plan)
     h2 = tn.tn_head_create(plan)
     tn.tn_contract_slices(plan, 0, 16, h1)
@@ -441,7 +478,7 @@ def test_batch_of_mixed_circuits_in_one_graph(tn):
     cfgs, plans, heads, refs, plain = [], [], [], [], []
     for i, (r, c, m, h, L, cut) in enumerate(shapes):
         cfg = ci.config_small(r, c, m, seed=40 + i, n_open=h, L=L, n_cut_gates=cut)
-        p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+        p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_fold_log2=-1)
         cfgs.append(cfg)
         plans.append(p)
         heads.append(tn.tn_head_create(p))
@@ -469,7 +506,7 @@ def test_batch_of_mixed_circuits_in_one_graph(tn):
     gc.collect()
     cfgs2 = [ci.config_small(r, c, m, seed=70 + i, n_open=h, L=L, n_cut_gates=cut)
              for i, (r, c, m, h, L, cut) in enumerate(shapes)]
-    plans2 = [tn.tn_plan(cf["circuit"], cf["open_qubits"], cf["tails"], cf["edges"]) for cf in cfgs2]
+    plans2 = [tn.tn_plan(cf["circuit"], cf["open_qubits"], cf["tails"], cf["edges"], host_fold_log2=-1) for cf in cfgs2]
     heads2 = [tn.tn_head_create(p) for p in plans2]
     tn.tn_contract_batch(plans2, [(0, 1 << tn.tn_plan_get_stats(p)["n_sliced"]) for p in plans2], heads2)
     for cf, p, hd in zip(cfgs2, plans2, heads2):
@@ -481,7 +518,7 @@ def _server_cases(tn):
     out = []
     for i, (r, c, m, h, L, cut) in enumerate(shapes):
         cfg = ci.config_small(r, c, m, seed=60 + i, n_open=h, L=L, n_cut_gates=cut)
-        plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+        plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_fold_log2=-1)
         k = tn.tn_plan_get_stats(plan)["n_sliced"]
         kept = (0, max(1, (1 << k) // 2))                  # kept fraction 1/2 (1 when k = 0)
         out.append((cfg, plan, kept))

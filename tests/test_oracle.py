@@ -342,6 +342,27 @@ def test_c_statevector_matches_numpy_and_brute_force(seed):
     assert abs(nn - 1) < 1e-12 and abs(ov - 1) < 1e-12
 
 
+def test_sliced30_golden_file_identities():
+    """The stored 30-qubit O1 results obey what the mathematics fixes: the
+    uncut state has norm 1 (unitarity); a kept prefix fixes slice bits to 0,
+    a projection inside a unitary circuit, so <psi|psi_hat> = <psi_hat|psi_hat>
+    and F_true equals the prefix's squared norm exactly; the sparse state's
+    mean |psi|^2 is 2^-30 to a few percent (Porter-Thomas sample of 65,536);
+    its inputs are those of the 30-qubit workload."""
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "sliced30_o1.npz"))
+    cfg = ci.config_sliced30()
+    assert np.array_equal(g["tails"], np.asarray(cfg["tails"], dtype=np.uint64))
+    assert list(g["open_qubits"]) == cfg["open_qubits"]
+    assert abs(float(g["norm2_full"]) - 1) < 1e-12
+    for kept in g["prefixes"]:
+        assert abs(float(g[f"F_true_{kept}"]) - float(g[f"norm2_{kept}"])) < 1e-12
+        assert abs(float(g[f"F_true_{kept}"]) / (kept / 64) - 1) < 0.05
+    m = (np.abs(g["H_full"]) ** 2).mean() * 2 ** 30
+    assert abs(m - 1) < 0.05
+    assert O.porter_thomas_ks((np.abs(g["H_full"]) ** 2 * 2 ** 30).ravel()) < 0.02
+
+
 def test_philox_words_uniform():
     words = []
     for i in range(4000):

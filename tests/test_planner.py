@@ -116,11 +116,12 @@ def test_sparse_state_worked_example_patterns(tn):
     ex = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))["sparse_state_example"]
     c = ci.make_random_2q_circuit(3, 2, seed=1)
     tails = np.array([int(t[::-1], 2) for t in ex["targets"]], dtype=np.uint64)
-    plan0 = tn.tn_plan(c, [], tails, host_only=True, max_host_absorb_log2=1)
+    plan0 = tn.tn_plan(c, [], tails, host_only=True, max_host_absorb_log2=1, host_fold_log2=-1)
     d0 = tn.tn_plan_describe(plan0)
     ids = {lf["tq"]: i for i, lf in enumerate(d0["leaves"]) if lf["tq"] in (2, 4)}
     assert set(ids) == {2, 4}
-    plan = tn.tn_plan(c, [], tails, order=[[ids[2], ids[4]]], host_only=True, max_host_absorb_log2=1)
+    plan = tn.tn_plan(c, [], tails, order=[[ids[2], ids[4]]], host_only=True, max_host_absorb_log2=1,
+                      host_fold_log2=-1)
     d = tn.tn_plan_describe(plan, with_data=True)
     merged = [v for v in d["vts"] if v["tq"] == 6]
     assert merged and merged[0]["P"] == 3
@@ -349,8 +350,9 @@ def test_random_plans_replay_to_the_oracle(tn, case):
     two-qubit gates in both orientations, random open sets and tail counts,
     SLICE / PIN / COMPANION edges on random gates, host absorption caps, the
     small-operand threshold, engines (leaf variants and, for FP16x3, scale
-    slots), automatic slicing under a tight cap -- each replayed on the host
-    and compared with the state-vector oracle over a random slice range."""
+    slots), host folding thresholds, automatic slicing under a tight cap --
+    each replayed on the host and compared with the state-vector oracle over a
+    random slice range."""
     rng = np.random.default_rng(1000 + case)
     n = int(rng.integers(4, 9))
     circ = ci.make_random_2q_circuit(n, int(rng.integers(2, 5)), seed=2000 + case)
@@ -371,8 +373,8 @@ def test_random_plans_replay_to_the_oracle(tn, case):
         edges.append((g, leg, kind, int(rng.integers(0, 2)) if kind == tn.TN_EDGE_PIN else 0))
     gemm = int(rng.choice([tn.TN_GEMM_TC_3XTF32, tn.TN_GEMM_TC_FP16X3, tn.TN_GEMM_TC_BF16X3, tn.TN_GEMM_SIMT_FP32]))
     kw = dict(host_only=True, gemm=gemm, max_host_absorb_log2=int(rng.choice([0, 2, 12])),
-              small_max_bits=int(rng.choice([-1, 2, 4])))
-    free = tn.tn_plan(circ, oq, tails, edges, **kw)
+              small_max_bits=int(rng.choice([-1, 2, 4])), host_fold_log2=int(rng.choice([-1, 3, 5, 12])))
+    free = tn.tn_plan(circ, oq, tails, edges, **dict(kw, host_fold_log2=-1))   # caps are on the unfolded network
     big = tn.tn_plan_get_stats(free)["max_log2_elements"]
     leaves = tn.tn_plan_describe(free)["leaves"]
     floor = max([np.log2(len(set(int(t) for t in tails))) + n_open] +
@@ -391,6 +393,42 @@ def test_random_plans_replay_to_the_oracle(tn, case):
     ref = O.sparse_state_from_vector(O.sliced_statevector(circ, se, pins=pins, slice_range=(b, e)), oq, tails)
     scale = max(np.abs(ref).max(), 1e-300)
     assert np.abs(H - ref).max() <= 1e-11 * scale
+
+
+@pytest.mark.parametrize("fold", [0, 4, 8, 16])
+def test_host_folding_equals_the_device_contraction(tn, fold):
+    """Host folding: contractions of host tensors with small results are done
+    at plan time and become leaves (with a variant per value of their slice
+    bits, the two ends of a cut merged into one variant axis).  The folded
+    plan replays to the same amplitudes as the unfolded one and the oracle,
+    over every slice, with slice, pin and companion cuts; it launches fewer
+    kernels; at 2^16 the whole 16-qubit network folds into one leaf."""
+    cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)
+    c = cfg["circuit"]
+    twoq = c.two_qubit_gates()
+    edges = list(cfg["edges"][:3]) + [(twoq[4], 1, tn.TN_EDGE_COMPANION, 0), (twoq[9], 0, tn.TN_EDGE_PIN, 1)]
+    cfg = dict(cfg, edges=edges)
+    base = tn.tn_plan(c, cfg["open_qubits"], cfg["tails"], edges, host_only=True, host_fold_log2=-1)
+    plan = tn.tn_plan(c, cfg["open_qubits"], cfg["tails"], edges, host_only=True, host_fold_log2=fold)
+    sb, sp = tn.tn_plan_get_stats(base), tn.tn_plan_get_stats(plan)
+    assert sp["n_sliced"] == sb["n_sliced"] == 4 and sp["n_pinned"] == 1
+    assert sp["n_launches"] <= sb["n_launches"]
+    if fold == 16:
+        assert sp["n_leaves"] == 1 and sp["n_contractions"] == 0 and sp["n_launches"] == 1
+    if fold >= 8:
+        assert sp["n_launches"] < sb["n_launches"]
+    H = emulate(tn.tn_plan_describe(plan, with_data=True), cfg["tails"], cfg["open_qubits"], range(16))
+    Hb = emulate(tn.tn_plan_describe(base, with_data=True), cfg["tails"], cfg["open_qubits"], range(16))
+    se = [(g, l, True) if kd == tn.TN_EDGE_COMPANION else (g, l) for (g, l, kd, v) in edges if kd != tn.TN_EDGE_PIN]
+    pins = [(g, l, v) for (g, l, kd, v) in edges if kd == tn.TN_EDGE_PIN]
+    ref = O.sparse_state_from_vector(O.sliced_statevector(c, se, pins=pins), cfg["open_qubits"], cfg["tails"])
+    assert np.abs(H - ref).max() < 1e-12 * np.abs(ref).max()
+    assert np.abs(H - Hb).max() < 1e-12 * np.abs(ref).max()
+    # the user-visible order is still over the simplified leaves: planning
+    # again with it gives the same folded plan
+    again = tn.tn_plan(c, cfg["open_qubits"], cfg["tails"], edges, order=tn.tn_plan_order(plan), host_only=True,
+                       host_fold_log2=fold)
+    assert tn.tn_plan_get_stats(again)["n_launches"] == sp["n_launches"]
 
 
 def test_companion_fixing_an_open_qubit_final_wire(tn):
