@@ -41,6 +41,15 @@ sys.path.insert(0, ROOT)
 
 import circuit_inputs as ci  # noqa: E402
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch,
+# from a single-kernel ncu capture of the current kernel; keyed by the GEMM
+# engine and the launch's algorithmic complex MACs and bytes (tn_plan_step_info).
+# A dominant launch with no entry reports traffic null.
+MEASURED_TRAFFIC = {
+    ("fp16", 270582939648, 1329594368): (7.264653e9 + 0.2639552e9,
+                                         "profiles/gemm_tc_fp16x3_grid5x6_m14_open10_L64_k6.md"),
+}
+
 KIND_NAMES = {0: "small_operand", 1: "permute", 2: "bprep_tc", 3: "gemm_tc_3xtf32", 4: "bprep_simt",
               5: "gemm_simt_fp32", 6: "operand_max", -1: "accumulate"}
 ORDER_TRIALS = 2048
@@ -346,6 +355,11 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None, "kernel": KIND_NAMES[kind],
                 "peak_note": f"{peak_src} hbm_gbs"}
+    tr = MEASURED_TRAFFIC.get((args.engine, int(round(macs)), int(round(abytes))))
+    if tr:
+        roof["traffic"] = tr[0]
+        roof["traffic_note"] = (f"ncu dram bytes of one launch of this kernel and shape ({tr[1]}); algorithmic "
+                                f"bytes {abytes:.4g}")
     roof["dominant_launch_ms"] = round(per_launch[i_dom], 4)
     roof["ms_per_step_profiled"] = round(ms_prof, 3)
     roof["kernel_time_share"] = {k2: round(v / tot, 4) for k2, v in sorted(kind_totals.items(), key=lambda x: -x[1])}

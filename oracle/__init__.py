@@ -22,5 +22,6 @@ from .statevector import (statevector, sliced_statevector, sparse_state_from_vec
 from .network import network_amplitudes
 from .metrics import (fidelity, f_estimate, companion_factor, linear_xeb, expected_group_sampler_xeb,
                       porter_thomas_ks, gpu_efficiency, normalised_probabilities, log_xeb, entropy,
-                      entropy_from_samples, group_sampling_law, EULER_GAMMA)
+                      entropy_from_samples, group_sampling_law, EULER_GAMMA, expected_subgroup_xeb,
+                      subset_fidelity)
 from .sampler import philox4x32_10, sample_groups, sample_groups_mcmc

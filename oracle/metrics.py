@@ -88,6 +88,24 @@ def expected_group_sampler_xeb(H: np.ndarray, P_ideal: np.ndarray, n_qubits: int
     return float((2.0 ** n_qubits) * (w * P_ideal).sum(axis=1).mean() - 1.0)
 
 
+def expected_subgroup_xeb(H: np.ndarray, P_ideal: np.ndarray, n_qubits: int, l: int) -> float:
+    """expected_group_sampler_xeb with every group of the head split into
+    consecutive sub-groups of l members (the open index mu's high bits fixed),
+    each sampled once: the linear XEB of the paper's group sampling as a
+    function of the group size l (Supplement, XEB against group size)."""
+    L, lh = H.shape
+    assert lh % l == 0
+    return expected_group_sampler_xeb(H.reshape(L * (lh // l), l), P_ideal.reshape(L * (lh // l), l), n_qubits)
+
+
+def subset_fidelity(psi, psi_hat) -> float:
+    """fidelity() restricted to the amplitudes given (here the sparse state):
+    |<psi|psi_hat>|^2 / (<psi|psi> <psi_hat|psi_hat>) over that subset, an
+    estimate of the full fidelity when the subset is a random sample of
+    bitstrings."""
+    return fidelity(np.asarray(psi).ravel(), np.asarray(psi_hat).ravel())
+
+
 def normalised_probabilities(H: np.ndarray, n_qubits: int) -> np.ndarray:
     """p(s) = |psi_hat(s)|^2 / (N * 2^n / (L l)), N = sum |psi_hat|^2 over the
     sparse state: the normalisation of the Results section read as 2^n/(L l) N

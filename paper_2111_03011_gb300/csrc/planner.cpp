@@ -3,6 +3,7 @@
 #include "planner.h"
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -580,7 +581,123 @@ static SliceResult slice_order(const Plan& plan, PatternBook& book, const std::v
   return r;
 }
 
-// Randomised greedy search (restarts).  Each trial repeatedly contracts the
+// One partition trial.  Recursive bisection of the leaf graph (nodes = leaves,
+// edge weight = the bond legs two leaves share, i.e. log2 of the dimension cut)
+// gives a contraction tree whose largest intermediates sit at the smallest
+// cuts: each part is contracted on its own and the two results are contracted
+// last.  A part is split by a region grown breadth-first from a random node to
+// a random share of 40-60 % of the nodes, then refined by Fiduccia-Mattheyses
+// passes (move the unlocked node of largest cut reduction that keeps the
+// balance, keep the best prefix of moves).  The tree becomes a pairwise order
+// (each result stored at its first operand's slot) and is scored like a greedy
+// trial: modelled time of its steps and largest intermediate.
+static TrialResult partition_trial(const Plan& plan, PatternBook& book, const std::vector<GNode>& init, double cap,
+                                   uint64_t seed, int trial) {
+  std::mt19937_64 rng(seed * 0xA24BAED4963EE407ULL + (uint64_t)trial * 0x9FB21C651E98DF25ULL + 7);
+  std::uniform_real_distribution<double> ud(0.0, 1.0);
+  const int n = (int)init.size();
+  // weighted adjacency over bond legs held by exactly two leaves
+  std::unordered_map<int, std::vector<int>> owners;
+  for (int i = 0; i < n; ++i)
+    for (int l : init[i].legs)
+      if (plan.legs[l].kind == LEG_BOND) owners[l].push_back(i);
+  std::vector<std::unordered_map<int, int>> adj(n);
+  for (auto& kv : owners)
+    if (kv.second.size() == 2) {
+      ++adj[kv.second[0]][kv.second[1]];
+      ++adj[kv.second[1]][kv.second[0]];
+    }
+  const double share = 0.4 + 0.2 * ud(rng);
+  std::vector<std::pair<int, int>> order;
+  std::vector<int> side(n, -1);
+  // returns the slot holding the part's result
+  std::function<int(std::vector<int>&)> build = [&](std::vector<int>& part) -> int {
+    const int m = (int)part.size();
+    if (m == 1) return part[0];
+    if (m == 2) {
+      order.push_back({part[0], part[1]});
+      return part[0];
+    }
+    for (int v : part) side[v] = 0;
+    // initial cut: a region grown breadth-first from a random node
+    const int target = std::max(1, std::min(m - 1, (int)std::lround(share * m)));
+    std::vector<int> q{part[(size_t)(ud(rng) * m) % m]};
+    side[q[0]] = 1;
+    int grown = 1;
+    for (size_t h = 0; h < q.size() && grown < target; ++h)
+      for (auto& nb : adj[q[h]])
+        if (side[nb.first] == 0 && grown < target) {
+          side[nb.first] = 1;
+          q.push_back(nb.first);
+          ++grown;
+        }
+    for (size_t i = 0; grown < target && i < part.size(); ++i)   // disconnected remainder
+      if (side[part[i]] == 0) { side[part[i]] = 1; ++grown; }
+    // Fiduccia-Mattheyses refinement within balance [lo, hi] for side 1
+    const int lo = std::max(1, (int)std::floor(0.35 * m)), hi = std::min(m - 1, (int)std::ceil(0.65 * m));
+    for (int pass = 0; pass < 6; ++pass) {
+      std::vector<char> locked(n, 0);
+      std::vector<int> moves;
+      int cur = 0, best = 0, best_len = 0, size1 = grown;
+      for (int step = 0; step < m; ++step) {
+        int bv = -1, bg = INT32_MIN;
+        for (int v : part) {
+          if (locked[v]) continue;
+          const int to = 1 - side[v];
+          const int ns = size1 + (to == 1 ? 1 : -1);
+          if (ns < lo || ns > hi) continue;
+          int g = 0;
+          for (auto& nb : adj[v])
+            if (side[nb.first] >= 0) g += side[nb.first] == side[v] ? -nb.second : nb.second;
+          if (g > bg || (g == bg && ud(rng) < 0.5)) { bg = g; bv = v; }
+        }
+        if (bv < 0) break;
+        size1 += side[bv] == 0 ? 1 : -1;
+        side[bv] = 1 - side[bv];
+        locked[bv] = 1;
+        moves.push_back(bv);
+        cur += bg;
+        if (cur > best) { best = cur; best_len = (int)moves.size(); }
+      }
+      for (int i = (int)moves.size() - 1; i >= best_len; --i) side[moves[i]] = 1 - side[moves[i]];
+      grown = 0;
+      for (int v : part) grown += side[v] == 1;
+      if (best <= 0) break;
+    }
+    std::vector<int> a, b;
+    for (int v : part) (side[v] == 1 ? a : b).push_back(v);
+    for (int v : part) side[v] = -1;
+    if (a.empty() || b.empty()) {   // degenerate split: halve by position
+      a.assign(part.begin(), part.begin() + m / 2);
+      b.assign(part.begin() + m / 2, part.end());
+    }
+    const int sa = build(a);
+    const int sb = build(b);
+    order.push_back({sa, sb});
+    return sa;
+  };
+  std::vector<int> all(n);
+  for (int i = 0; i < n; ++i) all[i] = i;
+  if (n > 1) build(all);
+  TrialResult res;
+  std::vector<StepLegs> steps = replay_steps(book, init, order);
+  const std::vector<char> none(plan.legs.size(), 0);
+  double mx = 0, cost = 0;
+  for (auto& x : init) mx = std::max(mx, x.lsz);
+  for (auto& st : steps) {
+    double lc = 0;
+    cost += sliced_step_time(st, none, plan.gemm_engine != TN_GEMM_SIMT_FP32, &lc);
+    mx = std::max(mx, lc);
+  }
+  res.order = std::move(order);
+  res.fits = mx <= cap + 1e-9;
+  res.cost = cost;
+  res.mx = mx;
+  return res;
+}
+
+// Order search (restarts).  Even trials are randomised greedy; odd trials are
+// recursive bisections (partition_trial).  A greedy trial repeatedly contracts the
 // connected pair minimising size(C) - alpha * (size(A) + size(B)), with alpha
 // drawn per trial and Gumbel noise of temperature tau on log-scores after the
 // first trial.  A trial never stops at the cap: it records its largest
@@ -611,7 +728,9 @@ static int greedy_order(Plan& plan, const std::vector<GNode>& init, double cap, 
         double tcap = cap;
         if (budget > 0 && trial % 3 == 1) tcap = 1e9;
         if (budget > 0 && trial % 3 == 2) tcap = cap + 2 + (trial / 3) % 6;
-        TrialResult r = greedy_trial(plan, book, init, tcap, seed, trial);
+        // odd trials (from the second on) build the order by recursive bisection
+        TrialResult r = (trial % 2 == 1 && init.size() >= 8) ? partition_trial(plan, book, init, tcap, seed, trial)
+                                                             : greedy_trial(plan, book, init, tcap, seed, trial);
         if (budget > 0) {
           SliceResult sr = slice_order(plan, book, init, r.order, cap, budget);
           r.fits = sr.ok;

@@ -283,6 +283,20 @@ def test_entropy_closed_forms_and_sample_estimate():
     assert abs(O.entropy_from_samples(P[s]) - O.entropy(P)) < 3 * y.std() / math.sqrt(s.size)
 
 
+def test_subgroup_xeb_dirichlet_closed_form():
+    """XEB of one exact draw per sub-group of size l from Porter-Thomas
+    weights is (l - 1)/(l + 1) (the Dirichlet form); the sub-group split of a
+    head equals building the smaller groups directly, and l = 1 gives 0."""
+    L, h = 256, 10
+    H = ci.synthetic_head(L, h, seed=12)
+    P = np.abs(H) ** 2 / 2 ** 30
+    for l in (2, 8, 64, 1024):
+        x = O.expected_subgroup_xeb(H, P, 30, l)
+        assert abs(x - (l - 1) / (l + 1)) < 0.02, (l, x)
+        assert math.isclose(x, O.expected_group_sampler_xeb(H.reshape(-1, l), P.reshape(-1, l), 30), rel_tol=1e-12)
+    assert abs(O.expected_subgroup_xeb(H, P, 30, 1) - (P.mean() * 2 ** 30 - 1)) < 1e-12
+
+
 def test_group_sampling_law_matches_sampler_frequencies():
     """The law of one-sample-per-group draws: each group equally often, inside
     a group |H|^2 normalised; checked against the oracle sampler's counts
