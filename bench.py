@@ -199,7 +199,7 @@ def run_ours(args):
             "fp16": tn.TN_GEMM_TC_FP16X3}[args.engine]
     t0 = time.time()
     popts = cfg.get("plan_opts", {})
-    trials = ORDER_TRIALS if args.workload == "sliced30" else 0
+    trials = ORDER_TRIALS if args.workload in ("sliced30", "syc53") else 0
     if rank == 0 and args.autotune > 0:
         plan = tn.tn_plan_autotune(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"],
                                    n_candidates=args.autotune, gemm=gemm, order_trials=trials, **popts)
@@ -209,11 +209,12 @@ def run_ours(args):
     if ws > 1:
         # every rank contracts with rank 0's plan: its order goes to the others
         import torch.distributed as dist
-        box = [tn.tn_plan_order(plan).tolist() if rank == 0 else None]
+        box = [(tn.tn_plan_order(plan).tolist(), tn.tn_plan_get_stats(plan)["gemm_pair"]) if rank == 0 else None]
         dist.broadcast_object_list(box, src=0)
         if rank != 0:
             plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=gemm,
-                              order=np.array(box[0], dtype=np.int32).reshape(-1, 2), **popts)
+                              order=np.array(box[0][0], dtype=np.int32).reshape(-1, 2), gemm_pair=box[0][1],
+                              **popts)
     plan_s = time.time() - t0
     st = tn.tn_plan_get_stats(plan)
     k = st["n_sliced"]
@@ -402,6 +403,8 @@ def run_ours(args):
                              "launches with CUDA events around each (tn_profile_slices)",
                 "plan_seconds": round(plan_s, 2), "order_trials": ORDER_TRIALS,
                 "autotune_candidates": st["autotune_candidates"], "rank0_slices": [b0, e0_],
+                "gemm_tiles": "CTA pairs (cta_group::2, 256x256) where they apply" if st["gemm_pair"] == 0 and
+                              args.engine in ("fp16", "bf16") else "one-CTA 128-row tiles",
                 "partial_slices_for_profiling": bool(args.slices)},
         "amplitudes_per_s": round(jobs * n_amp / (ms * 1e-3), 1),
         "slices_per_s": round(jobs * n_slices / (ms * 1e-3), 2),
@@ -476,7 +479,8 @@ def run_serve(args):
         else:
             bits_of.append(None)
     results = {}
-    for engine, gemm in (("tc", tn.TN_GEMM_TC_3XTF32), ("simt", tn.TN_GEMM_SIMT_FP32)):
+    for engine, gemm in (("fp16", tn.TN_GEMM_TC_FP16X3), ("bf16", tn.TN_GEMM_TC_BF16X3), ("tc", tn.TN_GEMM_TC_3XTF32),
+                         ("simt", tn.TN_GEMM_SIMT_FP32)):
         plans = [tn.tn_plan(c["circuit"], c["open_qubits"], c["tails"], c["edges"], gemm=gemm, order_trials=16)
                  for c in mix]
         head_bytes = [tn.tn_plan_get_stats(p)["n_tails"] * (16 << tn.tn_plan_get_stats(p)["n_open"]) for p in plans]
@@ -511,14 +515,16 @@ def run_serve(args):
                            "amplitudes_per_s": round(n_amp / wall, 1),
                            "completed": st["completed"] - base, "evictions": st["evictions"]}
         tn.tn_server_free(sv)
-    out = {"metric": "p99 request latency", "value": results["tc"]["p99_ms"], "unit": "ms",
+    out = {"metric": "p99 request latency", "value": results["fp16"]["p99_ms"], "unit": "ms",
            "higher_is_better": False, "n_gpus": 1, "mode": "serving",
            "config": {"workload": "poisson mix of 6 circuits (20-25 qubits, 8-12 cycles, 6-8 open, 32-256 tails)",
                       "cache": "cold start; HBM budget holds about half the heads (evicted heads are recontracted)",
                       "requests": args.requests, "rate_per_s": args.rate, "slots": 8,
                       "sizes": "amplitude batches 1e3-1e5 (log-uniform), samples 1e2-1e4"},
-           "tc_3xtf32": results["tc"], "plain_c64_simt": results["simt"],
-           "p99_vs_plain_c64": round(results["tc"]["p99_ms"] / results["simt"]["p99_ms"], 3)}
+           "fp16x3": results["fp16"], "bf16x3": results["bf16"], "tc_3xtf32": results["tc"],
+           "plain_c64_simt": results["simt"],
+           "p99_vs_plain_c64": {k: round(results[k]["p99_ms"] / results["simt"]["p99_ms"], 3)
+                                for k in ("fp16", "bf16", "tc")}}
     print(json.dumps(out), flush=True)
 
 
@@ -538,7 +544,7 @@ def run_torch(args):
     cfg = _workload(args.workload)
     popts = cfg.get("plan_opts", {})
     plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True,
-                      order_trials=ORDER_TRIALS if args.workload == "sliced30" else 0, order_seed=1, **popts)
+                      order_trials=ORDER_TRIALS if args.workload in ("sliced30", "syc53") else 0, order_seed=1, **popts)
     st = tn.tn_plan_get_stats(plan)
     d = tn.tn_plan_describe(plan, with_data=True)
     tm = [int(t) & d["tail_mask"] for t in cfg["tails"]]

@@ -107,6 +107,9 @@ typedef struct {
                                  host tensors (leaves or earlier folds) and whose result has at most
                                  2^this elements (and at most 2^6 slice variants) is done on the host
                                  in FP64 at plan time and becomes a leaf (0: 12; -1: off) */
+  int    gemm_pair;           /* 0: 16-bit GEMM steps with 256-wide tiles and M >= 256 run on CTA pairs
+                                 (cta_group::2, 256 x 256 tiles); -1: one-CTA 128-row tiles only.
+                                 tn_plan_autotune times both and keeps the faster. */
 } tn_plan_opts;
 
 typedef struct tn_plan tn_plan_t;
@@ -131,6 +134,7 @@ typedef struct {
   int     autotune_candidates;/* tn_plan_autotune: distinct orders timed */
   int     n_internal_sliced;  /* edges added by auto_slice; n_launches, tc_macs and alg_bytes count
                                  all 2^n_internal_sliced passes of one user slice */
+  int     gemm_pair;          /* the plan's tn_plan_opts.gemm_pair (as chosen by tn_plan_autotune) */
 } tn_plan_stats;
 
 /* Plan the contraction (host).  `order`: n_pairs pairs (i, j) of leaf ids, the
@@ -259,7 +263,12 @@ int  tn_sample_ex(tn_head_t* head, int64_t n, double target_fidelity, uint64_t s
  * host memory and must stay valid until tn_server_wait returns.  Results are
  * those of tn_amplitudes / tn_sample_ex on the same head.  Plans registered
  * with a server must not be used by other calls while it runs. */
-typedef struct { int n_slots; int64_t hbm_budget_bytes; } tn_server_opts;   /* 0: 8 slots, 64 GiB */
+/* n_slots: 0 means 8.  hbm_budget_bytes: bytes of cached heads; 0 means the
+ * device's free memory when the server is created, less 1 GiB.  Admission of
+ * a new head also requires that much free device memory now (cudaMemGetInfo)
+ * beyond a 1 GiB reserve; idle heads are evicted least-recently-used until
+ * both hold. */
+typedef struct { int n_slots; int64_t hbm_budget_bytes; } tn_server_opts;
 typedef struct tn_server tn_server_t;
 enum { TN_REQ_AMPLITUDES = 0, TN_REQ_SAMPLE = 1 };
 typedef struct {
@@ -333,6 +342,23 @@ int  tn_plan_step_info(const tn_plan_t* plan, int64_t i, int* kind, double* macs
  * call's contents: calls whose kernels overlap on the GPU (different streams,
  * or different host threads) race on it, so serialise them. */
 int  tn_head_norm_noalloc(const void* head_c128, int64_t n_groups, int n_open, double* norm_out, void* stream);
+
+/* Standalone complex GEMM step (the contraction kernel of every GEMM step, the
+ * K2 step of the contraction; Supplement complexity table, 8 flops per complex
+ * multiply-add): C[p] = A[mapA(p)] B[mapB(p)] for p < PC, complex64, with
+ * A [PA][M][K], B [PB][K][N] and C [PC][M][N] row-major device buffers.
+ * M, N and K are powers of two (K >= 2 on the tensor-core engines; 16-bit
+ * engines take K = 2 in tf32, as the planner does).  mapA / mapB are host
+ * arrays of PC pattern indices, or NULL for the identity (P = PC) or pattern 0
+ * (P = 1).  The operands pass through the same split permute, B preparation
+ * and GEMM kernels as a plan's steps (engine TN_GEMM_*; pair as
+ * tn_plan_opts.gemm_pair).  It allocates its
+ * scratch (split planes, prepared B, tables) with cudaMalloc, frees it before
+ * returning, and synchronises `stream`.  TN_ERR_TIMEOUT if a bounded device
+ * wait gave up. */
+int  tn_gemm_c64(int engine, const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K,
+                 int64_t PA, int64_t PB, int64_t PC, const int32_t* mapA, const int32_t* mapB, int pair,
+                 void* stream);
 
 const char* tn_last_error(void);
 const char* tn_version(void);

@@ -56,7 +56,8 @@ class tn_range(C.Structure):
 class tn_plan_opts(C.Structure):
     _fields_ = [("max_log2_elements", C.c_double), ("gemm", C.c_int), ("host_only", C.c_int),
                 ("order_trials", C.c_int), ("order_seed", C.c_uint64), ("max_host_absorb_log2", C.c_int),
-                ("small_max_bits", C.c_int), ("auto_slice", C.c_int), ("host_fold_log2", C.c_int)]
+                ("small_max_bits", C.c_int), ("auto_slice", C.c_int), ("host_fold_log2", C.c_int),
+                ("gemm_pair", C.c_int)]
 
 
 class tn_server_opts(C.Structure):
@@ -90,7 +91,7 @@ class tn_plan_stats(C.Structure):
                 ("max_log2_elements", C.c_double), ("workspace_bytes", C.c_int64),
                 ("n_gemm_tc", C.c_int), ("n_gemm_simt", C.c_int), ("n_small", C.c_int), ("n_permute", C.c_int),
                 ("measured_slice_ms", C.c_double), ("autotune_candidates", C.c_int),
-                ("n_internal_sliced", C.c_int)]
+                ("n_internal_sliced", C.c_int), ("gemm_pair", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -139,6 +140,7 @@ def _load():
     lib.tn_profile_slices.argtypes = [vp, tn_range, vp, vp, C.POINTER(C.c_double), i64]
     lib.tn_plan_step_info.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.tn_head_norm_noalloc.argtypes = [vp, i64, C.c_int, vp, vp]
+    lib.tn_gemm_c64.argtypes = [C.c_int, vp, vp, vp, i64, i64, i64, i64, i64, i64, i32p, i32p, C.c_int, vp]
     lib.tn_last_error.restype = C.c_char_p
     lib.tn_version.restype = C.c_char_p
     for name in ("tn_plan", "tn_plan_autotune", "tn_plan_get_stats", "tn_plan_order", "tn_head_create", "tn_head_fidelity",
@@ -231,7 +233,7 @@ class Head:
 
 def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements=0.0, gemm=TN_GEMM_AUTO,
             host_only=False, order_trials=0, order_seed=0, max_host_absorb_log2=0, small_max_bits=0,
-            auto_slice=0, host_fold_log2=0) -> Plan:
+            auto_slice=0, host_fold_log2=0, gemm_pair=0) -> Plan:
     gates = gates_to_c(circuit)
     circ = tn_circuit(int(circuit.n_qubits), len(circuit.gates), gates)
     oq = (C.c_int * max(1, len(open_qubits)))(*[int(q) for q in open_qubits])
@@ -243,7 +245,7 @@ def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements
         ed[i] = tn_edge(int(g), int(leg), int(kind), int(val))
     opts = tn_plan_opts(float(max_log2_elements), int(gemm), int(bool(host_only)), int(order_trials),
                         int(order_seed), int(max_host_absorb_log2), int(small_max_bits), int(auto_slice),
-                        int(host_fold_log2))
+                        int(host_fold_log2), int(gemm_pair))
     h = C.c_void_p()
     if order is not None:
         o = np.ascontiguousarray(np.asarray(order, dtype=np.int32).reshape(-1))
@@ -256,7 +258,7 @@ def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements
 
 def tn_plan_autotune(circuit, open_qubits, tails, edges=(), n_candidates=4, max_log2_elements=0.0,
                      gemm=TN_GEMM_AUTO, order_trials=0, order_seed=0, max_host_absorb_log2=0, small_max_bits=0,
-                     stream=None, auto_slice=0, host_fold_log2=0) -> Plan:
+                     stream=None, auto_slice=0, host_fold_log2=0, gemm_pair=0) -> Plan:
     gates = gates_to_c(circuit)
     circ = tn_circuit(int(circuit.n_qubits), len(circuit.gates), gates)
     oq = (C.c_int * max(1, len(open_qubits)))(*[int(q) for q in open_qubits])
@@ -267,7 +269,8 @@ def tn_plan_autotune(circuit, open_qubits, tails, edges=(), n_candidates=4, max_
         g, leg, kind, val = (list(e) + [TN_EDGE_SLICE, 0])[:4] if len(e) < 4 else e
         ed[i] = tn_edge(int(g), int(leg), int(kind), int(val))
     opts = tn_plan_opts(float(max_log2_elements), int(gemm), 0, int(order_trials), int(order_seed),
-                        int(max_host_absorb_log2), int(small_max_bits), int(auto_slice), int(host_fold_log2))
+                        int(max_host_absorb_log2), int(small_max_bits), int(auto_slice), int(host_fold_log2),
+                        int(gemm_pair))
     h = C.c_void_p()
     _check(_lib.tn_plan_autotune(C.byref(circ), C.byref(spec), ed, len(edges), C.byref(opts), int(n_candidates),
                                  _stream(stream), C.byref(h)))
@@ -395,6 +398,23 @@ def tn_plan_step_info(plan: Plan, i: int):
     b = C.c_double()
     _check(_lib.tn_plan_step_info(plan.handle, int(i), C.byref(k), C.byref(m), C.byref(b)))
     return k.value, m.value, b.value
+
+
+def tn_gemm_c64(a, b, c, engine=TN_GEMM_AUTO, map_a=None, map_b=None, pair=0, stream=None):
+    """c[p] = a[map_a(p)] @ b[map_b(p)] on the device (torch complex64 tensors of
+    shapes [PA, M, K], [PB, K, N], [PC, M, N]); maps are sequences of PC ints
+    or None."""
+    PA, M, K = (int(x) for x in a.shape)
+    PB, K2, N = (int(x) for x in b.shape)
+    PC = int(c.shape[0])
+    assert K2 == K and tuple(c.shape[1:]) == (M, N)
+    i32p = C.POINTER(C.c_int32)
+    ma = np.ascontiguousarray(np.asarray(map_a, dtype=np.int32)) if map_a is not None else None
+    mb = np.ascontiguousarray(np.asarray(map_b, dtype=np.int32)) if map_b is not None else None
+    _check(_lib.tn_gemm_c64(int(engine), _ptr(a), _ptr(b), _ptr(c), M, N, K, PA, PB, PC,
+                            ma.ctypes.data_as(i32p) if ma is not None else None,
+                            mb.ctypes.data_as(i32p) if mb is not None else None, int(pair), _stream(stream)))
+    return c
 
 
 def tn_head_norm_noalloc(head_buffer, n_groups: int, n_open: int, norm_out, stream=None):

@@ -207,6 +207,7 @@ extern "C" int tn_plan(const tn_circuit* circuit, const tn_open_spec* open_spec,
     in.auto_slice = opts->auto_slice;
     if (opts->host_fold_log2 > 16) return fail(TN_ERR_INVALID, "host_fold_log2 must be at most 16");
     if (opts->host_fold_log2 != 0) in.fold_log2 = opts->host_fold_log2 < 0 ? -1 : opts->host_fold_log2;
+    in.gemm_pair = opts->gemm_pair < 0 ? -1 : 0;
   }
   if (in.gemm_engine < 0 || in.gemm_engine > 4) return fail(TN_ERR_INVALID, "unknown gemm engine");
   if (in.cap_log2 > 34) return fail(TN_ERR_INVALID, "size cap above 2^34 elements");
@@ -245,6 +246,7 @@ extern "C" int tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* s) {
   s->tc_macs = P.tc_macs * ni;
   s->alg_bytes = P.alg_bytes * ni;
   s->n_internal_sliced = P.n_internal;
+  s->gemm_pair = P.gemm_pair;
   s->max_log2_elements = P.max_log2;
   s->workspace_bytes = P.workspace_bytes;
   s->measured_slice_ms = plan->measured_slice_ms;
@@ -465,6 +467,7 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
         gp.scaleA = scale_ptr(p, x.slot);
         gp.scaleB = scale_ptr(p, x.slotB);
         gp.amax = scale_ptr(p, x.max_slot);
+        gp.pair = P.gemm_pair;
         e = x.kind == tn::ST_GEMM_SIMT ? tn::launch_gemm_simt(gp, st) : tn::launch_gemm_tc(gp, p->d_status, st);
         break;
       }
@@ -902,6 +905,158 @@ int check_slice_range(tn_plan_t* plan, tn_range r, tn_head_t* head) { return che
 void mark_slices_done(tn_head_t* head, tn_range r) { mark_done(head, r); }
 }  // namespace tn
 
+// ------------------------------------------------------- standalone GEMM
+
+extern "C" int tn_gemm_c64(int engine, const void* A, const void* B, void* C, int64_t M, int64_t N, int64_t K,
+                           int64_t PA, int64_t PB, int64_t PC, const int32_t* mapA, const int32_t* mapB, int pair,
+                           void* stream) {
+  if (engine == TN_GEMM_AUTO) engine = TN_GEMM_TC_3XTF32;
+  if (engine < TN_GEMM_TC_3XTF32 || engine > TN_GEMM_TC_FP16X3) return fail(TN_ERR_INVALID, "unknown gemm engine");
+  if (!A || !B || !C) return fail(TN_ERR_INVALID, "NULL operand");
+  auto pow2 = [](int64_t x) { return x >= 1 && (x & (x - 1)) == 0; };
+  if (!pow2(M) || !pow2(N) || !pow2(K)) return fail(TN_ERR_INVALID, "M, N and K must be powers of two");
+  if (PA < 1 || PB < 1 || PC < 1) return fail(TN_ERR_INVALID, "pattern counts must be >= 1");
+  if (M * K > (1LL << 32) || K * N > (1LL << 32) || M * N > (1LL << 32))
+    return fail(TN_ERR_INVALID, "operand above 2^32 elements");
+  const bool simt = engine == TN_GEMM_SIMT_FP32;
+  int nk = 0, nn = 0, nmk = 0;
+  while ((1LL << nk) < K) ++nk;
+  while ((1LL << nn) < N) ++nn;
+  while ((1LL << nmk) < M * K) ++nmk;
+  if (!simt && nk < 1) return fail(TN_ERR_INVALID, "tensor-core engines need K >= 2");
+  // like the planner: 16-bit operands need K >= 4 (16-byte rows); K = 2 uses tf32
+  const int h16 = simt ? 0 : nk >= 2 ? (engine == TN_GEMM_TC_BF16X3 ? 1 : engine == TN_GEMM_TC_FP16X3 ? 2 : 0) : 0;
+  // pattern maps: a table of PC entries, or identity (P == PC) / all zero (P == 1)
+  int mode[2];
+  std::vector<uint32_t> maps[2];
+  const int32_t* user[2] = {mapA, mapB};
+  const int64_t PX[2] = {PA, PB};
+  for (int x = 0; x < 2; ++x) {
+    if (user[x]) {
+      mode[x] = 2;
+      for (int64_t p = 0; p < PC; ++p) {
+        if (user[x][p] < 0 || user[x][p] >= PX[x]) return fail(TN_ERR_INVALID, "pattern map entry out of range");
+        maps[x].push_back((uint32_t)user[x][p]);
+      }
+    } else if (PX[x] == PC) {
+      mode[x] = 0;
+    } else if (PX[x] == 1) {
+      mode[x] = 1;
+    } else {
+      return fail(TN_ERR_INVALID, "a pattern count differs from PC and no map is given");
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(tn::prepare_gemm_tc());   // kernel attributes (shared-memory size), as at plan upload
+  // scratch: split A planes, prepared B, tables, scale slots
+  const int64_t es = h16 ? 2 : 4;
+  const int split = simt ? 0 : (h16 == 2 ? 3 : h16 == 1 ? 2 : 1);
+  const int64_t a_bytes = simt ? 0 : PA * M * K * 8 * (split == 1 ? 2 : 1);
+  const int64_t b_bytes = simt ? PB * K * N * 8 : 2 * PB * (2 * N) * (2 * K) * es;
+  const int t = std::min(nmk, 10);
+  std::vector<uint32_t> meta;
+  const size_t tab_off = meta.size();
+  for (int i = 0; i < (1 << t); ++i) meta.push_back((uint32_t)i);   // identity tile: in offsets
+  for (int i = 0; i < (1 << t); ++i) meta.push_back((uint32_t)i);   // out offsets
+  for (int i = 0; i < (1 << t); ++i) meta.push_back((uint32_t)i);   // slots
+  const size_t bk_off = meta.size();
+  for (int64_t k = 0; k < K; ++k) meta.push_back((uint32_t)(k * N));
+  const size_t bn_off = meta.size();
+  for (int64_t n = 0; n < N; ++n) meta.push_back((uint32_t)n);
+  const size_t map_off[2] = {meta.size(), meta.size() + maps[0].size()};
+  meta.insert(meta.end(), maps[0].begin(), maps[0].end());
+  meta.insert(meta.end(), maps[1].begin(), maps[1].end());
+  char* a_split = nullptr;
+  char* b_prep = nullptr;
+  uint32_t* d_meta = nullptr;
+  unsigned int* d_scale = nullptr;   // [0] max of A, [1] max of B, [2] status
+  int rc = TN_OK;
+  auto cleanup = [&]() {
+    cudaFree(a_split);
+    cudaFree(b_prep);
+    cudaFree(d_meta);
+    cudaFree(d_scale);
+  };
+  if ((a_bytes && cudaMalloc(&a_split, (size_t)a_bytes) != cudaSuccess) ||
+      cudaMalloc(&b_prep, (size_t)b_bytes) != cudaSuccess ||
+      cudaMalloc(&d_meta, meta.size() * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&d_scale, 3 * sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(TN_ERR_OOM, "tn_gemm_c64 scratch allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(d_meta, meta.data(), meta.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_scale, 0, 3 * sizeof(unsigned int), st);
+  if (e == cudaSuccess && h16 == 2) {
+    tn::AbsmaxParams ap{(const float2*)A, PA * M * K, d_scale};
+    e = tn::launch_absmax(ap, st);
+    if (e == cudaSuccess) {
+      tn::AbsmaxParams bp{(const float2*)B, PB * K * N, d_scale + 1};
+      e = tn::launch_absmax(bp, st);
+    }
+  }
+  if (e == cudaSuccess && !simt) {   // A -> split planes (identity bit permutation)
+    tn::PermParams pp;
+    pp.in = (const float2*)A;
+    pp.out = (float2*)a_split;
+    pp.pstride = M * K;
+    pp.P = PA;
+    pp.t = t;
+    pp.n_rest = nmk - t;
+    for (int x = 0; x < pp.n_rest; ++x) pp.rest_in[x] = pp.rest_out[x] = (uint8_t)(t + x);
+    pp.tab = d_meta + tab_off;
+    pp.split = split;
+    pp.scale = d_scale;
+    e = tn::launch_permute(pp, st);
+  }
+  if (e == cudaSuccess) {   // B -> real embedding (tensor cores) or [K][N] copy (CUDA cores)
+    tn::BPrepParams bp;
+    bp.B = (const float2*)B;
+    bp.out = b_prep;
+    bp.b_pstride = K * N;
+    bp.PB = PB;
+    bp.nk = nk;
+    bp.nn = nn;
+    bp.bk = d_meta + bk_off;
+    bp.bn = d_meta + bn_off;
+    bp.h16 = h16;
+    bp.scale = d_scale + 1;
+    e = simt ? tn::launch_bprep_c(bp, st) : tn::launch_bprep_tc(bp, st);
+  }
+  if (e == cudaSuccess) {
+    tn::GemmParams gp;
+    gp.A = simt ? (const float2*)A : (const float2*)a_split;
+    gp.B = b_prep;
+    gp.C = (float2*)C;
+    gp.M = M;
+    gp.N = N;
+    gp.K = K;
+    gp.PA = PA;
+    gp.PB = PB;
+    gp.PC = PC;
+    gp.mapA = d_meta + map_off[0];
+    gp.mapB = d_meta + map_off[1];
+    gp.mapA_mode = mode[0];
+    gp.mapB_mode = mode[1];
+    gp.h16 = h16;
+    gp.scaleA = d_scale;
+    gp.scaleB = d_scale + 1;
+    gp.amax = nullptr;
+    gp.pair = pair < 0 ? -1 : 0;
+    e = simt ? tn::launch_gemm_simt(gp, st) : tn::launch_gemm_tc(gp, d_scale + 2, st);
+  }
+  unsigned int word = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&word, d_scale + 2, sizeof(word), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    rc = fail(TN_ERR_CUDA, std::string("tn_gemm_c64: ") + cudaGetErrorString(e));
+  } else if (word) {
+    rc = fail(TN_ERR_TIMEOUT, "tn_gemm_c64: a bounded device wait gave up");
+  }
+  cleanup();
+  return rc;
+}
+
 extern "C" int tn_plan_autotune(const tn_circuit* circuit, const tn_open_spec* open_spec, const tn_edge* sliced_edges,
                                 int n_edges, const tn_plan_opts* opts, int n_candidates, void* stream,
                                 tn_plan_t** out) {
@@ -941,17 +1096,27 @@ extern "C" int tn_plan_autotune(const tn_circuit* circuit, const tn_open_spec* o
     rc = tn_head_create(p, nullptr, &h);
     double ms = 1e300;
     if (rc == TN_OK) {
-      rc = run_slice(p, 0, h->H, st);   // untimed
-      if (rc == TN_OK) {
+      // with 16-bit operands, time the CTA-pair and the one-CTA GEMM tiles and
+      // keep the faster (unless the caller turned pairs off)
+      const bool both = o.gemm_pair == 0 && (o.gemm == TN_GEMM_TC_BF16X3 || o.gemm == TN_GEMM_TC_FP16X3);
+      int best_pair = p->P.gemm_pair;
+      for (int v = 0; v < (both ? 2 : 1) && rc == TN_OK; ++v) {
+        if (both) p->P.gemm_pair = v == 0 ? 0 : -1;
+        rc = run_slice(p, 0, h->H, st);   // untimed
+        if (rc != TN_OK) break;
         cudaEventRecord(e0, st);
         rc = run_slice(p, 0, h->H, st);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) == cudaSuccess) {
           float f = 0.f;
           cudaEventElapsedTime(&f, e0, e1);
-          ms = f;
+          if (f < ms) {
+            ms = f;
+            best_pair = p->P.gemm_pair;
+          }
         }
       }
+      p->P.gemm_pair = best_pair;
       tn_head_free(h);
     }
     if (rc == TN_OK && ms < best_ms) {

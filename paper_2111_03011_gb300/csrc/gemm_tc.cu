@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 256);
+      mbar_init(&acce[b], 8);               // one arrive per drain warp
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
@@ -407,8 +407,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int e = 0; e < 16; ++e) acc[16 * (p0 + j) + e] += __uint_as_float(v[j][e]);
           }
         }
+        // the warp's TMEM loads are complete (wait::ld above); one lane
+        // releases the buffer for the whole warp
         asm volatile("tcgen05.fence::before_thread_sync;");
-        mbar_arrive(&acce[b]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[b]);
         ++cc;
       }
       if (!ok || !active) continue;
@@ -459,6 +462,344 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 9) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lay::TMEM_COLS));
+  }
+}
+
+// ------------------------------------------------ CTA-pair variant (cta_group::2)
+//
+// Two CTAs of a cluster compute one 256 x 256 tile with 2-SM MMAs: CTA r holds
+// rows [128 r, 128 r + 128) of the A tile and half of the B tile (its 128
+// columns) in its own shared memory, and keeps its 128 rows x 256 columns of
+// the accumulator in its own TMEM.  Each SM so reads half the B tile per MMA,
+// which cuts shared-memory traffic by about a third against the one-CTA
+// 128 x 256 tile and frees shared memory for more pipeline stages.
+//   - The leader (rank 0) issues every MMA and commits them to the barriers of
+//     both CTAs at once (multicast): a stage is free, a chunk is accumulated.
+//   - Both CTAs' TMA loads complete on the leader's stage barrier, which the
+//     leader arms with the bytes of both halves.
+//   - The drain warps of both CTAs release a TMEM chunk buffer by arriving on
+//     the leader's barrier (the peer's arrive is remote).
+//   - TMEM is allocated and freed by one warp of each CTA together.
+// Waits are bounded as in the one-CTA kernel; both CTAs meet at a cluster
+// barrier before freeing TMEM and exiting, so neither leaves while the other
+// may still touch its shared memory.
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// shared::cluster address of the same shared-memory location in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, uint32_t mbar_cluster, int c0,
+                                                 int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar_cluster)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma2(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// arrive on barrier `bar` (a local offset) in both CTAs of the pair once the
+// MMAs issued so far complete
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  const uint16_t mask = 3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+template <int STAGES>
+struct LayoutPair {
+  static constexpr int KB = 64;                   // 64-byte k-blocks (64-byte swizzle)
+  static constexpr int A_BYTES = BM * KB;         // this CTA's 128 rows
+  static constexpr int B_BYTES = 128 * KB;        // this CTA's half of the 256-row B tile
+  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int DATA = STAGES * STAGE;
+  static constexpr int TOTAL = DATA + 1024 + 256;
+  static_assert(TOTAL <= 232448, "shared memory per CTA");
+  static_assert(2 * STAGES + 8 <= 32, "barrier area");
+  static constexpr uint32_t TMEM_COLS = 512;     // two chunk buffers of 256 fp32 columns
+};
+
+// Instruction descriptor of a 256 x 256 pair MMA (kind::f16, fp32 accumulate)
+template <int FMT>
+__device__ __forceinline__ uint32_t idesc_pair() {
+  const uint32_t f = FMT == 1 ? 1u : 0u;
+  return (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+
+template <int STAGES, int FMT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    k_gemm_tc_pair(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+                   const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+                   float* __restrict__ C, int64_t M, int64_t N2, int64_t K2, int64_t tilesM, int64_t tilesN,
+                   int64_t PC, int64_t PCg, int fold, const uint32_t* __restrict__ mapA,
+                   const uint32_t* __restrict__ mapB, int mapA_mode, int mapB_mode, const unsigned int* scaleA,
+                   const unsigned int* scaleB, unsigned int* amax_out, unsigned int* status) {
+  static_assert(FMT == 1 || FMT == 2, "pair MMAs use kind::f16 operands");
+  constexpr int BN = 256;
+  using Lay = LayoutPair<STAGES>;
+  constexpr int KB = Lay::KB;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + Lay::DATA);
+  uint64_t* full = bars;                    // leader: stage loaded in both CTAs  [STAGES]
+  uint64_t* empty = bars + STAGES;          // both: stage consumed               [STAGES]
+  uint64_t* accf = bars + 2 * STAGES;       // both: chunk accumulated            [2]
+  uint64_t* acce = bars + 2 * STAGES + 2;   // leader: chunk drained in both CTAs [2]
+  uint64_t* mma_done = bars + 2 * STAGES + 4;
+  volatile uint32_t* tmem_slot = (volatile uint32_t*)(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = (volatile int*)(bars + 2 * STAGES + 6);
+  unsigned int* s_amax = (unsigned int*)(bars + 2 * STAGES + 7);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int64_t cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
+  const bool a_shared = mapA_mode == 1 && PC > 1;
+  const int64_t n_tiles = tilesM * tilesN * PCg;
+  const int br = BN / fold;                 // B rows per pattern box (2N when folded)
+  const int half_boxes = fold >= 2 ? fold / 2 : 1;   // B boxes this CTA loads per stage
+  const int box_rows = fold >= 2 ? br : 128;
+  constexpr int BKE = KB / 2;               // K elements (16-bit) per k-block
+  constexpr int CH = KBlock<KB>::CH, KK = KBlock<KB>::KK;
+  const int nkb = (int)((K2 + BKE - 1) / BKE);
+  const int nch = (nkb + CH - 1) / CH;
+  auto coords = [&](int64_t t, int64_t& pc0, int64_t& tm, int64_t& tn_) {
+    int64_t pg;
+    tile_coords(t, tilesM, tilesN, PCg, a_shared, pg, tm, tn_);
+    pc0 = pg * fold;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 16);              // one arrive per drain warp of each CTA
+    }
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    *s_amax = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 9) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tmem_slot)),
+                 "r"(Lay::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  cluster_sync_all();                       // both CTAs' barriers exist before any remote use
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t t = cluster; t < n_tiles && ok; t += n_clusters) {
+        int64_t pc0, tm, tn_;
+        coords(t, pc0, tm, tn_);
+        const int64_t pa = mapA_mode == 0 ? pc0 : (mapA_mode == 1 ? 0 : (int64_t)mapA[pc0]);
+        const int row0 = (int)(tm * 2 * BM + rank * BM);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = (int)(it % STAGES);
+          const uint32_t r = it / STAGES;
+          if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
+          const uint32_t fb = mapa_rank(smem_u32(&full[s]), 0);
+          if (leader) mbar_expect_tx(&full[s], (uint32_t)(2 * Lay::STAGE));   // both CTAs' halves
+          uint8_t* st = smem + s * Lay::STAGE;
+          tma_load_3d_pair(st, &tmAhi, fb, kb * BKE, row0, (int)pa);
+          tma_load_3d_pair(st + Lay::A_BYTES, &tmAlo, fb, kb * BKE, row0, (int)pa);
+          for (int h = 0; h < half_boxes; ++h) {
+            int64_t pcf = pc0;
+            int nrow = (int)(tn_ * BN + rank * 128);
+            if (fold >= 2) {
+              const int f = (int)rank * half_boxes + h;
+              pcf = pc0 + f < PC ? pc0 + f : PC - 1;
+              nrow = 0;
+            }
+            const int64_t pb = mapB_mode == 0 ? pcf : (mapB_mode == 1 ? 0 : (int64_t)mapB[pcf]);
+            uint8_t* sb = st + 2 * Lay::A_BYTES + h * box_rows * KB;
+            tma_load_3d_pair(sb, &tmBhi, fb, kb * BKE, nrow, (int)pb);
+            tma_load_3d_pair(sb + Lay::B_BYTES, &tmBlo, fb, kb * BKE, nrow, (int)pb);
+          }
+          ++it;
+        }
+      }
+      if (!ok) {
+        // The copies of both CTAs complete on the leader's stage barriers: the
+        // leader waits out its last STAGES k-blocks there.  The peer cannot
+        // observe its own copies (their barrier is the leader's), and the two
+        // producers may stop one k-block apart, so both also hold for a
+        // bounded time (about a millisecond) before the final cluster barrier.
+        if (leader)
+          for (uint32_t j = it > (uint32_t)STAGES ? it - STAGES : 0; j < it; ++j)
+            mbar_drain(&full[j % STAGES], (j / STAGES) & 1);
+        const long long t0 = clock64();
+        while (clock64() - t0 < (1LL << 21)) {
+        }
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0 && leader) {
+      const uint32_t idesc = idesc_pair<FMT>();
+      uint32_t it = 0, cc = 0;
+      bool ok = true;
+      for (int64_t t = cluster; t < n_tiles && ok; t += n_clusters) {
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = (int)(it % STAGES);
+          const uint32_t r = it / STAGES;
+          const int b = (int)(cc & 1);
+          const uint32_t u = cc >> 1;
+          const bool first = kb % CH == 0, last = kb % CH == CH - 1 || kb == nkb - 1;
+          if (first && !mbar_wait(&acce[b], (u & 1) ^ 1, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&full[s], r & 1, abort_flag)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t d = tmem + (uint32_t)(b * BN);
+          const uint32_t st = smem_u32(smem + s * Lay::STAGE);
+          const uint32_t a_hi = st, a_lo = st + Lay::A_BYTES;
+          const uint32_t b_hi = st + 2 * Lay::A_BYTES, b_lo = b_hi + Lay::B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < KK; ++kk) {
+            const uint32_t o = kk * 32;
+            mma2(d, sdesc<KB>(a_hi + o), sdesc<KB>(b_lo + o), idesc, (first && kk == 0) ? 0u : 1u);
+            mma2(d, sdesc<KB>(a_lo + o), sdesc<KB>(b_hi + o), idesc, 1u);
+          }
+#pragma unroll
+          for (int kk = 0; kk < KK; ++kk) {
+            const uint32_t o = kk * 32;
+            mma2(d, sdesc<KB>(a_hi + o), sdesc<KB>(b_hi + o), idesc, 1u);
+          }
+          mma_commit_pair(&empty[s]);
+          if (last) {
+            mma_commit_pair(&accf[b]);
+            ++cc;
+          }
+          ++it;
+        }
+      }
+      // every issued MMA (they write both CTAs' TMEM) completes before either
+      // CTA frees TMEM; a commit with nothing pending arrives at once
+      mma_commit_pair(mma_done);
+    }
+  } else {
+    // drain warps 0-7 of both CTAs: this CTA's 128 rows, 128 columns per warp
+    constexpr int NCOL = BN / 2;
+    constexpr int NPIECE = NCOL / 16;
+    constexpr int RP = 2;
+    const int q = warp & 3, half = warp >> 2;
+    const int col0 = half * NCOL;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const float ua = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleA)) : 1.0f;
+    const float ub = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleB)) : 1.0f;
+    const uint32_t acce_leader[2] = {mapa_rank(smem_u32(&acce[0]), 0), mapa_rank(smem_u32(&acce[1]), 0)};
+    float tmax = 0.0f;
+    uint32_t cc = 0;
+    bool ok = true;
+    for (int64_t t = cluster; t < n_tiles && ok; t += n_clusters) {
+      int64_t pc0, tm, tn_;
+      coords(t, pc0, tm, tn_);
+      float acc[NCOL];
+#pragma unroll
+      for (int e = 0; e < NCOL; ++e) acc[e] = 0.0f;
+      for (int c = 0; c < nch; ++c) {
+        const int b = (int)(cc & 1);
+        const uint32_t u = cc >> 1;
+        ok = mbar_wait(&accf[b], u & 1, abort_flag);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int p0 = 0; p0 < NPIECE; p0 += RP) {
+          uint32_t v[RP][16];
+#pragma unroll
+          for (int j = 0; j < RP; ++j)
+            tmem_ld16(tmem + lane_base + (uint32_t)(b * BN) + (uint32_t)(col0 + 16 * (p0 + j)), v[j]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < RP; ++j)
+#pragma unroll
+            for (int e = 0; e < 16; ++e) acc[16 * (p0 + j) + e] += __uint_as_float(v[j][e]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(acce_leader[b]);
+        ++cc;
+      }
+      if (!ok) continue;
+      const int64_t row = tm * 2 * BM + (int64_t)rank * BM + q * 32 + lane;
+      if (row >= M) continue;
+#pragma unroll
+      for (int pp = 0; pp < NPIECE; ++pp) {
+        const int cl = col0 + 16 * pp;
+        const int f = cl / br;
+        const int64_t pc = pc0 + f;
+        const int64_t col = tn_ * br + (cl - f * br);
+        if (pc >= PC) continue;
+        float* crow = C + (pc * M + row) * N2;
+        float w[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) w[e] = FMT == 2 ? (acc[16 * pp + e] * ua) * ub : acc[16 * pp + e];
+        if (amax_out) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (col + e < N2) tmax = fmaxf(tmax, fabsf(acc[16 * pp + e]));
+        }
+        if (col + 16 <= N2) {
+          float4* dst = (float4*)(crow + col);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) dst[e] = make_float4(w[4 * e], w[4 * e + 1], w[4 * e + 2], w[4 * e + 3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (col + e < N2) crow[col + e] = w[e];
+        }
+      }
+    }
+    if (amax_out) {
+      if (FMT == 2) tmax = (tmax * ua) * ub;
+      const unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(tmax));
+      if (lane == 0) atomicMax(s_amax, m);
+    }
+  }
+  // both CTAs: wait (bounded) until the leader's MMAs are complete, then meet
+  if (threadIdx.x == 0) mbar_drain(mma_done, 0);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  cluster_sync_all();
+  if (*abort_flag && threadIdx.x == 0) atomicOr(status, 1u);
+  if (amax_out && threadIdx.x == 0 && *s_amax) atomicMax(amax_out, *s_amax);
+  if (warp == 9) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lay::TMEM_COLS));
   }
 }
 
@@ -548,6 +889,47 @@ static cudaError_t run(const GemmParams& p, int fold, unsigned int* status, cuda
   return cudaGetLastError();
 }
 
+constexpr int kPairStages = 6;
+
+template <int FMT>
+static cudaError_t set_attr_pair() {
+  return cudaFuncSetAttribute(k_gemm_tc_pair<kPairStages, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              LayoutPair<kPairStages>::TOTAL);
+}
+
+// The CTA-pair kernel: 256 x 256 tiles on clusters of two CTAs.
+template <int FMT>
+static cudaError_t run_pair(const GemmParams& p, int fold, unsigned int* status, cudaStream_t s) {
+  using Lay = LayoutPair<kPairStages>;
+  constexpr int BN = 256, KB = Lay::KB;
+  const int64_t K2 = 2 * p.K, N2 = 2 * p.N;
+  const int br = BN / fold;
+  if (fold > 1 && (br != N2 || br < 16 || p.mapA_mode != 1 || fold % 2)) return cudaErrorInvalidValue;
+  const uint32_t BKE = KB / 2;
+  const int64_t es = 2;
+  const char* ahi = (const char*)p.A;
+  const char* alo = ahi + p.PA * p.M * K2 * es;
+  const char* bhi = (const char*)p.B;
+  const char* blo = bhi + p.PB * N2 * K2 * es;
+  const uint32_t box_rows = fold >= 2 ? (uint32_t)br : 128u;
+  CUtensorMap tah, tal, tbh, tbl;
+  if (!encode3d(&tah, ahi, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT, KB)) return cudaErrorInvalidValue;
+  if (!encode3d(&tal, alo, (uint64_t)K2, (uint64_t)p.M, (uint64_t)p.PA, BKE, BM, FMT, KB)) return cudaErrorInvalidValue;
+  if (!encode3d(&tbh, bhi, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, box_rows, FMT, KB))
+    return cudaErrorInvalidValue;
+  if (!encode3d(&tbl, blo, (uint64_t)K2, (uint64_t)N2, (uint64_t)p.PB, BKE, box_rows, FMT, KB))
+    return cudaErrorInvalidValue;
+  const int64_t tilesM = (p.M + 2 * BM - 1) / (2 * BM), tilesN = fold > 1 ? 1 : (N2 + BN - 1) / BN;
+  const int64_t PCg = (p.PC + fold - 1) / fold;
+  const int64_t n_tiles = tilesM * tilesN * PCg;
+  if (n_tiles <= 0) return cudaSuccess;
+  const int64_t clusters = std::min<int64_t>(n_tiles, sm_count() / 2);
+  k_gemm_tc_pair<kPairStages, FMT><<<(unsigned)(2 * clusters), kThreads, Lay::TOTAL, s>>>(
+      tah, tal, tbh, tbl, (float*)p.C, p.M, N2, K2, tilesM, tilesN, p.PC, PCg, fold, p.mapA, p.mapB, p.mapA_mode,
+      p.mapB_mode, p.scaleA, p.scaleB, p.amax, status);
+  return cudaGetLastError();
+}
+
 // Tile width: the smallest of 16..256 that covers 2N, or, when all patterns
 // share A and 2N >= 16, up to 256 columns of consecutive patterns folded side
 // by side (fold = BN / 2N, as many as the pattern count rounded up to a power
@@ -567,11 +949,17 @@ static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStrea
   if (w <= 32) return run<32, kb_stages(32, kb_bytes(32, FMT)), FMT>(p, fold, status, s);
   if (w <= 64) return run<64, kb_stages(64, kb_bytes(64, FMT)), FMT>(p, fold, status, s);
   if (w <= 128) return run<128, kb_stages(128, kb_bytes(128, FMT)), FMT>(p, fold, status, s);
+  // 256-wide 16-bit tiles with at least 256 rows run on CTA pairs
+  if (FMT != 0 && p.M >= 2 * BM && p.pair >= 0) return run_pair<FMT == 0 ? 1 : FMT>(p, fold, status, s);
   return run<256, kb_stages(256, kb_bytes(256, FMT)), FMT>(p, fold, status, s);
 }
 
 template <int FMT>
 static cudaError_t set_attrs() {
+  if (FMT != 0) {
+    const cudaError_t e = set_attr_pair<FMT == 0 ? 1 : FMT>();
+    if (e != cudaSuccess) return e;
+  }
   const cudaError_t r[5] = {set_attr<16, kb_stages(16, kb_bytes(16, FMT)), FMT>(),
                             set_attr<32, kb_stages(32, kb_bytes(32, FMT)), FMT>(),
                             set_attr<64, kb_stages(64, kb_bytes(64, FMT)), FMT>(),

@@ -77,6 +77,7 @@ struct GemmParams {
   int h16;               // tensor-core engine: 0 tf32, 1 bf16, 2 scaled fp16 hi/lo operand planes
   const unsigned int* scaleA; const unsigned int* scaleB;   // h16 == 2: the operands' scale slots
   unsigned int* amax;    // non-null: atomicMax of the output's max |re|, |im| (fp32 bits)
+  int pair = 0;          // 0: CTA-pair 256 x 256 tiles where they apply (16-bit, M >= 256); -1: one-CTA tiles
 };
 
 struct AccumParams {

@@ -1279,6 +1279,7 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
   for (uint64_t t : in.tails) plan.book.tails.push_back(t & plan.tail_mask);
   plan.cap_log2 = in.cap_log2;
   plan.gemm_engine = in.gemm_engine;
+  plan.gemm_pair = in.gemm_pair;
   plan.small_max_bits = in.small_max_bits;
 
   // edges

@@ -137,6 +137,7 @@ struct Plan {
   double companion_factor = 1.0;   // product of the companion cuts' kept norm fractions
   double cap_log2 = 28;
   int gemm_engine = 0;
+  int gemm_pair = 0;               // GemmParams::pair of every tensor-core GEMM step
   int small_max_bits = 4;
 
   std::vector<Leg> legs;
@@ -182,6 +183,7 @@ struct PlanInput {
   int small_max_bits = 4;
   int auto_slice = 0;       // at most this many extra sliced edges when no order fits the cap
   int fold_log2 = 12;       // host folding of small contractions of host tensors (-1: off)
+  int gemm_pair = 0;        // 0: CTA-pair GEMM tiles where they apply; -1: one-CTA tiles only
 };
 
 int build_plan(const PlanInput& in, Plan& plan, std::string& err);

@@ -207,9 +207,17 @@ void retire(tn_server* sv, int si) {
   s.circuit = -1;
 }
 
-// Free least-recently-used idle heads until `need` more bytes fit.
+// Device memory kept free beside the heads (request staging, workspaces).
+constexpr int64_t kHbmReserve = (int64_t)1 << 30;
+
+// Admission by memory: a new head must fit both the byte budget and the
+// device's free memory as the driver reports it now (cudaMemGetInfo), less a
+// reserve.  Least-recently-used idle heads are freed until it does.
 bool make_room(tn_server* sv, int64_t need) {
-  while (sv->head_bytes + need > sv->opts.hbm_budget_bytes) {
+  while (true) {
+    size_t fr = 0, tot = 0;
+    const bool dev_ok = cudaMemGetInfo(&fr, &tot) != cudaSuccess || (int64_t)fr >= need + kHbmReserve;
+    if (sv->head_bytes + need <= sv->opts.hbm_budget_bytes && dev_ok) return true;
     int victim = -1;
     for (size_t i = 0; i < sv->circuits.size(); ++i) {
       Circuit& c = sv->circuits[i];
@@ -330,7 +338,16 @@ extern "C" int tn_server_create(const tn_server_opts* opts, tn_server_t** out) {
   *out = nullptr;
   tn_server* sv = new tn_server();
   sv->opts.n_slots = opts && opts->n_slots > 0 ? opts->n_slots : 8;
-  sv->opts.hbm_budget_bytes = opts && opts->hbm_budget_bytes > 0 ? opts->hbm_budget_bytes : ((int64_t)64 << 30);
+  if (opts && opts->hbm_budget_bytes > 0) {
+    sv->opts.hbm_budget_bytes = opts->hbm_budget_bytes;
+  } else {   // the device's free memory now, less the reserve
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = (size_t)64 << 30;
+    }
+    sv->opts.hbm_budget_bytes = std::max<int64_t>((int64_t)fr - kHbmReserve, (int64_t)1 << 26);
+  }
   if (sv->opts.n_slots > 64) {
     delete sv;
     return fail(TN_ERR_INVALID, "at most 64 slots");
