@@ -299,6 +299,16 @@ int  tn_server_wait(tn_server_t* server, uint64_t ticket, tn_request_result* res
 int  tn_server_get_stats(tn_server_t* server, tn_server_stats* out);
 void tn_server_free(tn_server_t* server);   /* drains the queue first */
 
+/* Linear and logarithmic cross-entropy benchmark of n samples against the
+ * probabilities held by `ideal`, a head of exact amplitudes (all slices
+ * kept): P(s) = |H(s)|^2, F_XEB = 2^n_qubits <P(s_i)> - 1 and
+ * log 2^n_qubits + gamma + <log P(s_i)> (Supplement, validation: the XEB
+ * formula and the logarithmic XEB; gamma = Euler's constant), with the sums
+ * reduced in FP64 on the GPU.  samples: host or device uint64 bitstrings,
+ * each in the sparse state (TN_ERR_NOT_IN_STATE otherwise).  Either output
+ * may be NULL.  Synchronises `stream`. */
+int  tn_xeb(tn_head_t* ideal, const uint64_t* samples, int64_t n, double* linear, double* log_xeb, void* stream);
+
 /* Squared norm N = sum |H|^2 (FP64) and, if group_norms != NULL, the L
  * per-group sums (host memory).  Synchronises `stream`. */
 int  tn_head_norm(tn_head_t* head, double* norm, double* group_norms, void* stream);

@@ -140,6 +140,7 @@ def _load():
     lib.tn_profile_slices.argtypes = [vp, tn_range, vp, vp, C.POINTER(C.c_double), i64]
     lib.tn_plan_step_info.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.tn_head_norm_noalloc.argtypes = [vp, i64, C.c_int, vp, vp]
+    lib.tn_xeb.argtypes = [vp, vp, i64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.tn_gemm_c64.argtypes = [C.c_int, vp, vp, vp, i64, i64, i64, i64, i64, i64, i32p, i32p, C.c_int, vp]
     lib.tn_last_error.restype = C.c_char_p
     lib.tn_version.restype = C.c_char_p
@@ -160,7 +161,7 @@ EXPORTED = ["tn_plan", "tn_plan_autotune", "tn_plan_free", "tn_plan_get_stats", 
             "tn_contract_slices", "tn_contract_slices_graph", "tn_contract_batch", "tn_amplitudes", "tn_sample", "tn_sample_ex", "tn_head_norm", "tn_profile_slices",
             "tn_plan_step_info", "tn_head_norm_noalloc", "tn_server_create", "tn_server_add_circuit",
             "tn_server_submit", "tn_server_wait", "tn_server_get_stats", "tn_server_free", "tn_last_error",
-            "tn_version"]
+            "tn_gemm_c64", "tn_xeb", "tn_version"]
 
 
 def _check(rc):
@@ -370,6 +371,16 @@ def tn_sample_ex(head: Head, n: int, target_fidelity=0.0, seed=0, method=TN_SAMP
     _check(_lib.tn_sample_ex(head.handle, int(n), float(target_fidelity), int(seed), int(method), int(param),
                              _ptr(out), _stream(stream)))
     return out
+
+
+def tn_xeb(ideal: Head, samples, stream=None):
+    """(linear XEB, log XEB) of the samples against the exact head `ideal`."""
+    if not hasattr(samples, "data_ptr"):
+        samples = np.ascontiguousarray(np.asarray(samples, dtype=np.uint64))
+    n = int(samples.numel() if hasattr(samples, "numel") else samples.size)
+    lin, lg = C.c_double(), C.c_double()
+    _check(_lib.tn_xeb(ideal.handle, _ptr(samples), n, C.byref(lin), C.byref(lg), _stream(stream)))
+    return lin.value, lg.value
 
 
 def tn_head_norm(head: Head, with_groups=False, stream=None):

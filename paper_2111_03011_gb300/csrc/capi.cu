@@ -811,6 +811,46 @@ extern "C" int tn_amplitudes(tn_head_t* h, const uint64_t* bitstrings, int64_t n
   return TN_OK;
 }
 
+extern "C" int tn_xeb(tn_head_t* h, const uint64_t* samples, int64_t n, double* linear, double* log_xeb,
+                      void* stream) {
+  if (!h || (n > 0 && !samples)) return fail(TN_ERR_INVALID, "NULL argument");
+  if (n < 1) return fail(TN_ERR_INVALID, "n must be >= 1");
+  if (h->invalid) return fail(TN_ERR_INVALID, "head is invalid after a failed or timed-out contraction");
+  tn_plan_t* p = h->plan;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev_in = is_device_ptr(samples);
+  // stage: [samples (host input)] [amplitudes c128] [partials] [2 sums]
+  const size_t in_b = dev_in ? 0 : (size_t)n * 8;
+  const size_t amp_off = (in_b + 255) / 256 * 256;
+  const size_t part_off = amp_off + (size_t)n * 16;
+  const size_t sums_off = part_off + (size_t)tn::xeb_partials(n) * 8;
+  int rc = ensure_stage(h, sums_off + 16);
+  if (rc) return rc;
+  char* stg = (char*)h->d_stage;
+  const uint64_t* d_bits = samples;
+  if (!dev_in) {
+    CUDA_TRY(cudaMemcpyAsync(stg, samples, in_b, cudaMemcpyHostToDevice, st));
+    d_bits = (const uint64_t*)stg;
+  }
+  unsigned long long init = ~0ULL;
+  CUDA_TRY(cudaMemcpyAsync(h->d_status, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(tn::launch_amplitudes(h->H, (int)p->P.open_qubits.size(), p->d_keys, p->d_key_groups, p->n_keys,
+                                 p->P.tail_mask, p->d_open, d_bits, n, stg + amp_off, 1, h->d_status, st));
+  CUDA_TRY(tn::launch_xeb_sums((const double2*)(stg + amp_off), n, (double*)(stg + part_off),
+                               (double*)(stg + sums_off), st));
+  double sums[2] = {0.0, 0.0};
+  unsigned long long status = 0;
+  CUDA_TRY(cudaMemcpyAsync(sums, stg + sums_off, 16, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (status != ~0ULL)
+    return fail(TN_ERR_NOT_IN_STATE, "sample " + std::to_string(status) + " has a tail that is not a group");
+  const int nq = p->P.n_qubits;
+  if (linear) *linear = std::ldexp(sums[0] / (double)n, nq) - 1.0;
+  if (log_xeb) *log_xeb = nq * std::log(2.0) + 0.57721566490153286 + sums[1] / (double)n;
+  return TN_OK;
+}
+
 extern "C" int tn_head_norm(tn_head_t* h, double* norm, double* group_norms, void* stream) {
   if (!h) return fail(TN_ERR_INVALID, "NULL head");
   if (h->invalid) return fail(TN_ERR_INVALID, "head is invalid after a failed or timed-out contraction");

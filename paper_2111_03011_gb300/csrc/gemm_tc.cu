@@ -501,8 +501,14 @@ __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// Arrive on an mbarrier of another CTA of the cluster.  The arrive only has to
+// order this warp's finished TMEM reads (tcgen05.wait::ld, then
+// tcgen05.fence::before_thread_sync) before the leader's next MMA into the same
+// columns, so it keeps the default CTA-scope release: a cluster-scope release
+// would first wait for the previous tile's global stores of C to become
+// visible across the cluster, which stalled the drain warps on every chunk.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, uint32_t mbar_cluster, int c0,

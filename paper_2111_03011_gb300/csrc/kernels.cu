@@ -461,10 +461,13 @@ cudaError_t launch_accum(const AccumParams& p, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------- K7
+// With seg_end (n_seg cumulative ends of merged requests), a missing key i of
+// segment j records its index within the segment in status[j]; otherwise
+// status[0] receives the smallest missing index.
 __global__ void k_amplitudes(const double2* __restrict__ H, int h, const uint64_t* __restrict__ keys,
                              const uint32_t* __restrict__ groups, int64_t n_keys, uint64_t tail_mask,
                              const int* __restrict__ open_q, const uint64_t* __restrict__ bits, int64_t n, void* out,
-                             int dtype, unsigned long long* status) {
+                             int dtype, unsigned long long* status, const int64_t* __restrict__ seg_end, int n_seg) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t b = bits[i];
     const uint64_t key = b & tail_mask;
@@ -479,6 +482,10 @@ __global__ void k_amplitudes(const double2* __restrict__ H, int h, const uint64_
       int64_t mu = 0;
       for (int j = 0; j < h; ++j) mu |= (int64_t)((b >> open_q[j]) & 1ULL) << j;
       v = H[(g << h) + mu];
+    } else if (seg_end) {
+      int j = 0;
+      while (j < n_seg - 1 && i >= seg_end[j]) ++j;
+      atomicMin(status + j, (unsigned long long)(i - (j ? seg_end[j - 1] : 0)));
     } else {
       atomicMin(status, (unsigned long long)i);
     }
@@ -489,11 +496,12 @@ __global__ void k_amplitudes(const double2* __restrict__ H, int h, const uint64_
 
 cudaError_t launch_amplitudes(const double2* H, int h, const uint64_t* keys, const uint32_t* groups, int64_t n_keys,
                               uint64_t tail_mask, const int* open_q, const uint64_t* bits, int64_t n, void* out,
-                              int dtype, unsigned long long* status, cudaStream_t s) {
+                              int dtype, unsigned long long* status, cudaStream_t s, const int64_t* seg_end,
+                              int n_seg) {
   if (n <= 0) return cudaSuccess;
   const int64_t grid = std::min<int64_t>((n + 255) / 256, (int64_t)kSMs * 8);
   k_amplitudes<<<(unsigned)grid, 256, 0, s>>>(H, h, keys, groups, n_keys, tail_mask, open_q, bits, n, out, dtype,
-                                              status);
+                                              status, seg_end, n_seg);
   return cudaGetLastError();
 }
 
@@ -546,6 +554,50 @@ __global__ void k_sum(const double* __restrict__ Z, int64_t L, double* N) {
     if (threadIdx.x == 0) *N = v;
   }
 }
+
+// XEB reductions (FP64): part[b] = sum |a_i|^2 and part[nb + b] = sum log |a_i|^2
+// over block b's share of the n amplitudes (grid-stride, then a block tree).
+__global__ void __launch_bounds__(256) k_xeb_partial(const double2* __restrict__ a, int64_t n, double* part) {
+  __shared__ double s1[8], s2[8];
+  double p = 0.0, lp = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = a[i];
+    const double w = v.x * v.x + v.y * v.y;
+    p += w;
+    lp += log(w);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    p += __shfl_xor_sync(0xffffffffu, p, d);
+    lp += __shfl_xor_sync(0xffffffffu, lp, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = p;
+    s2[threadIdx.x >> 5] = lp;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t1 = 0.0, t2 = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      t1 += s1[w];
+      t2 += s2[w];
+    }
+    part[blockIdx.x] = t1;
+    part[gridDim.x + blockIdx.x] = t2;
+  }
+}
+
+cudaError_t launch_xeb_sums(const double2* amp, int64_t n, double* part, double* sums, cudaStream_t s) {
+  const int64_t nb = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)kSMs * 4));
+  k_xeb_partial<<<(unsigned)nb, 256, 0, s>>>(amp, n, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum<<<1, 1024, 0, s>>>(part, nb, sums);
+  k_sum<<<1, 1024, 0, s>>>(part + nb, nb, sums + 1);
+  return cudaGetLastError();
+}
+
+int64_t xeb_partials(int64_t n) { return 2 * std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)kSMs * 4)); }
 
 cudaError_t launch_group_norms(const double2* H, int64_t L, int h, double* Z, double* N, cudaStream_t s) {
   const int64_t warps = L;

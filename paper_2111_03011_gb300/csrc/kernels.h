@@ -102,13 +102,21 @@ cudaError_t launch_accum(const AccumParams& p, cudaStream_t s);
 cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s);
 cudaError_t prepare_gemm_tc();   // kernel attributes; call before launching or capturing
 
-// amplitude lookup: out[i] = H[g][mu] (c128 or c64); status <- min missing index
+// amplitude lookup: out[i] = H[g][mu] (c128 or c64); status <- min missing
+// index, or with seg_end (cumulative ends of n_seg merged requests, device)
+// status[j] <- min missing index within request j
 cudaError_t launch_amplitudes(const double2* H, int h, const uint64_t* keys, const uint32_t* groups, int64_t n_keys,
                               uint64_t tail_mask, const int* open_q, const uint64_t* bits, int64_t n, void* out,
-                              int dtype, unsigned long long* status, cudaStream_t s);
+                              int dtype, unsigned long long* status, cudaStream_t s, const int64_t* seg_end = nullptr,
+                              int n_seg = 1);
 
 // per-group squared norms Z[g] (chunked warp order) and the total N
 cudaError_t launch_group_norms(const double2* H, int64_t L, int h, double* Z, double* N, cudaStream_t s);
+
+// sums[0] = sum |a_i|^2, sums[1] = sum log |a_i|^2 over n complex128 amplitudes
+// (FP64; `part` holds xeb_partials(n) doubles of scratch)
+cudaError_t launch_xeb_sums(const double2* amp, int64_t n, double* part, double* sums, cudaStream_t s);
+int64_t xeb_partials(int64_t n);
 
 struct SampleParams {
   const double2* H; int64_t L; int h;

@@ -11,6 +11,10 @@
 // Heads are freed least-recently-used first when a new head does not fit the
 // budget.  Completion is detected by polling per-slot events; latency is
 // measured from submit to the moment the result is in the caller's buffer.
+// Amplitude requests on the same ready circuit (and output type) that wait in
+// the queue when a slot frees up are merged into that slot: one staging copy,
+// one lookup launch and one copy back serve up to kMaxMerge of them, each
+// with its own status word.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +48,7 @@ struct Request {
   int status = TN_OK;
   std::string err;
   bool done = false;
+  bool merged = false;   // taken into another request's slot
 };
 
 enum { C_EMPTY = 0, C_BUILDING = 1, C_READY = 2 };
@@ -64,6 +69,7 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   Request* req = nullptr;
+  std::vector<Request*> extra;   // amplitude requests merged into this slot's launch
   int circuit = -1;
   bool building = false;
   void* d_buf = nullptr;     // device: bitstrings then results
@@ -122,58 +128,111 @@ int64_t head_bytes_of(tn_plan_t* p) {
   return (int64_t)p->P.tails_raw.size() * ((int64_t)16 << p->P.open_qubits.size());
 }
 
-// Enqueue one request's device work on its slot (the head is, or will be, ready).
-int enqueue_op(Slot& s, Request* q, Circuit& c) {
-  const tn_request& r = q->r;
+constexpr int kMaxMerge = 16;                       // amplitude requests per slot
+constexpr int64_t kMaxMergeKeys = (int64_t)1 << 22;  // bitstrings per merged launch
+
+// Staging of an amplitude batch: [bitstrings][results][status per request][segment ends]
+struct AmpLayout {
+  size_t out = 0, status = 0, seg = 0, total = 0;
+  int64_t n = 0;
+};
+
+AmpLayout amp_layout(const Slot& s) {
+  AmpLayout L;
+  L.n = s.req->r.n;
+  for (auto* q : s.extra) L.n += q->r.n;
+  const size_t m = 1 + s.extra.size();
+  const size_t esz = s.req->r.dtype == TN_C128 ? 16 : 8;
+  L.out = ((size_t)L.n * 8 + 255) / 256 * 256;
+  L.status = (L.out + (size_t)L.n * esz + 255) / 256 * 256;
+  L.seg = L.status + m * 8;
+  L.total = L.seg + m * 8;
+  return L;
+}
+
+// Enqueue a slot's amplitude batch (s.req and s.extra, one circuit and dtype).
+int enqueue_amplitudes(Slot& s, Circuit& c) {
   tn_plan_t* p = c.plan;
-  const int h = (int)p->P.open_qubits.size();
-  const size_t esz = r.kind == TN_REQ_AMPLITUDES ? (r.dtype == TN_C128 ? 16 : 8) : 8;
-  const size_t n = (size_t)r.n;
-  const size_t in_bytes = r.kind == TN_REQ_AMPLITUDES ? n * 8 : 0;
-  const size_t out_off = (in_bytes + 255) / 256 * 256;
-  int rc = ensure_slot_buffers(s, std::max<size_t>(out_off + n * esz, 256), std::max<size_t>(out_off + n * esz, 256));
-  if (rc) return fail(rc, "server: slot staging allocation failed");
+  const AmpLayout L = amp_layout(s);
+  if (ensure_slot_buffers(s, std::max<size_t>(L.total, 256), std::max<size_t>(L.total, 256)))
+    return fail(TN_ERR_OOM, "server: slot staging allocation failed");
   cudaStream_t st = s.stream;
   if (c.state == C_BUILDING && !s.building) cudaStreamWaitEvent(st, c.ready, 0);
   char* d = (char*)s.d_buf;
   char* hs = (char*)s.h_buf;
-  if (r.kind == TN_REQ_AMPLITUDES) {
-    std::memcpy(hs, r.bitstrings, in_bytes);
-    if (cudaMemcpyAsync(d, hs, in_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return fail(TN_ERR_CUDA, "server: H2D copy");
-    *s.h_status = ~0ULL;
-    cudaMemcpyAsync(s.d_status, s.h_status, sizeof(unsigned long long), cudaMemcpyHostToDevice, st);
-    cudaError_t e = tn::launch_amplitudes(c.head->H, h, p->d_keys, p->d_key_groups, p->n_keys, p->P.tail_mask,
-                                          p->d_open, (const uint64_t*)d, (int64_t)n, d + out_off,
-                                          r.dtype == TN_C128 ? 1 : 0, s.d_status, st);
-    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("server: amplitudes: ") + cudaGetErrorString(e));
-    cudaMemcpyAsync(s.h_status, s.d_status, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-  } else {
-    double f_head = 0.0;
-    tn_head_fidelity(c.head, &f_head, nullptr);
-    double mix = 0.0;
-    if (r.target_fidelity > 0.0 && f_head > 0.0 && r.target_fidelity < f_head) mix = 1.0 - r.target_fidelity / f_head;
-    tn::SampleParams sp;
-    sp.H = c.head->H;
-    sp.L = (int64_t)p->P.tails_raw.size();
-    sp.h = h;
-    sp.tails = p->d_tails;
-    sp.open_mask = p->P.open_mask;
-    sp.open_q = p->d_open;
-    sp.n_qubits = p->P.n_qubits;
-    sp.n = (int64_t)n;
-    sp.mix = mix;
-    sp.seed = r.seed;
-    sp.out = (uint64_t*)(d + out_off);
-    sp.method = r.method;
-    sp.param = r.param != 0 ? r.param
-                            : (r.method == TN_SAMPLE_METROPOLIS ? ((int64_t)1 << h) : (r.method == TN_SAMPLE_FRUGAL ? 10 : 0));
-    cudaError_t e = tn::launch_sample(sp, st);
-    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("server: sample: ") + cudaGetErrorString(e));
+  size_t o = 0;
+  unsigned long long* status = (unsigned long long*)(hs + L.status);
+  int64_t* seg = (int64_t*)(hs + L.seg);
+  int64_t end = 0;
+  for (size_t j = 0; j <= s.extra.size(); ++j) {
+    const tn_request& r = (j == 0 ? s.req : s.extra[j - 1])->r;
+    std::memcpy(hs + o, r.bitstrings, (size_t)r.n * 8);
+    o += (size_t)r.n * 8;
+    end += r.n;
+    status[j] = ~0ULL;
+    seg[j] = end;
   }
-  if (cudaMemcpyAsync(hs + out_off, d + out_off, n * esz, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  const size_t m = 1 + s.extra.size();
+  if (cudaMemcpyAsync(d, hs, (size_t)L.n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d + L.status, hs + L.status, 2 * m * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return fail(TN_ERR_CUDA, "server: H2D copy");
+  cudaError_t e = tn::launch_amplitudes(c.head->H, (int)p->P.open_qubits.size(), p->d_keys, p->d_key_groups,
+                                        p->n_keys, p->P.tail_mask, p->d_open, (const uint64_t*)d, L.n, d + L.out,
+                                        s.req->r.dtype == TN_C128 ? 1 : 0, (unsigned long long*)(d + L.status), st,
+                                        (const int64_t*)(d + L.seg), (int)m);
+  if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("server: amplitudes: ") + cudaGetErrorString(e));
+  if (cudaMemcpyAsync(hs + L.out, d + L.out, L.seg - L.out, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return fail(TN_ERR_CUDA, "server: D2H copy");
   return TN_OK;
+}
+
+// Enqueue one request's device work on its slot (the head is, or will be,
+// ready): an amplitude batch, or one sampling request.
+int enqueue_op(Slot& s, Request* q, Circuit& c) {
+  if (q->r.kind == TN_REQ_AMPLITUDES) return enqueue_amplitudes(s, c);
+  const tn_request& r = q->r;
+  tn_plan_t* p = c.plan;
+  const int h = (int)p->P.open_qubits.size();
+  const size_t n = (size_t)r.n;
+  if (ensure_slot_buffers(s, std::max<size_t>(n * 8, 256), std::max<size_t>(n * 8, 256)))
+    return fail(TN_ERR_OOM, "server: slot staging allocation failed");
+  cudaStream_t st = s.stream;
+  if (c.state == C_BUILDING && !s.building) cudaStreamWaitEvent(st, c.ready, 0);
+  char* d = (char*)s.d_buf;
+  double f_head = 0.0;
+  tn_head_fidelity(c.head, &f_head, nullptr);
+  double mix = 0.0;
+  if (r.target_fidelity > 0.0 && f_head > 0.0 && r.target_fidelity < f_head) mix = 1.0 - r.target_fidelity / f_head;
+  tn::SampleParams sp;
+  sp.H = c.head->H;
+  sp.L = (int64_t)p->P.tails_raw.size();
+  sp.h = h;
+  sp.tails = p->d_tails;
+  sp.open_mask = p->P.open_mask;
+  sp.open_q = p->d_open;
+  sp.n_qubits = p->P.n_qubits;
+  sp.n = (int64_t)n;
+  sp.mix = mix;
+  sp.seed = r.seed;
+  sp.out = (uint64_t*)d;
+  sp.method = r.method;
+  sp.param = r.param != 0 ? r.param
+                          : (r.method == TN_SAMPLE_METROPOLIS ? ((int64_t)1 << h) : (r.method == TN_SAMPLE_FRUGAL ? 10 : 0));
+  cudaError_t e = tn::launch_sample(sp, st);
+  if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("server: sample: ") + cudaGetErrorString(e));
+  if (cudaMemcpyAsync(s.h_buf, d, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return fail(TN_ERR_CUDA, "server: D2H copy");
+  return TN_OK;
+}
+
+void finish(tn_server* sv, Request* q, Circuit& c) {
+  q->t_done = Clock::now();
+  q->done = true;
+  if (q->status == TN_OK)
+    sv->latencies_us.push_back(std::chrono::duration<double, std::micro>(q->t_done - q->t_submit).count());
+  else
+    ++sv->failed;
+  --c.users;
 }
 
 void retire(tn_server* sv, int si) {
@@ -185,25 +244,30 @@ void retire(tn_server* sv, int si) {
     c.builder_slot = -1;
     s.building = false;
   }
-  const tn_request& r = q->r;
-  if (q->status == TN_OK) {
-    const size_t esz = r.kind == TN_REQ_AMPLITUDES ? (r.dtype == TN_C128 ? 16 : 8) : 8;
-    const size_t in_bytes = r.kind == TN_REQ_AMPLITUDES ? (size_t)r.n * 8 : 0;
-    const size_t out_off = (in_bytes + 255) / 256 * 256;
-    std::memcpy(r.out, (char*)s.h_buf + out_off, (size_t)r.n * esz);
-    if (r.kind == TN_REQ_AMPLITUDES && *s.h_status != ~0ULL) {
-      q->status = TN_ERR_NOT_IN_STATE;
-      q->err = "bitstring " + std::to_string(*s.h_status) + " has a tail that is not a group";
+  if (q->r.kind == TN_REQ_AMPLITUDES) {
+    const AmpLayout L = amp_layout(s);
+    const size_t esz = q->r.dtype == TN_C128 ? 16 : 8;
+    const unsigned long long* status = (const unsigned long long*)((char*)s.h_buf + L.status);
+    size_t off = 0;
+    for (size_t j = 0; j <= s.extra.size(); ++j) {
+      Request* x = j == 0 ? q : s.extra[j - 1];
+      if (x->status == TN_OK) {
+        std::memcpy(x->r.out, (char*)s.h_buf + L.out + off * esz, (size_t)x->r.n * esz);
+        if (status[j] != ~0ULL) {
+          x->status = TN_ERR_NOT_IN_STATE;
+          x->err = "bitstring " + std::to_string(status[j]) + " has a tail that is not a group";
+        }
+      }
+      off += (size_t)x->r.n;
+      finish(sv, x, c);
     }
+  } else {
+    const tn_request& r = q->r;
+    if (q->status == TN_OK) std::memcpy(r.out, (char*)s.h_buf, (size_t)r.n * 8);
+    finish(sv, q, c);
   }
-  q->t_done = Clock::now();
-  q->done = true;
-  if (q->status == TN_OK)
-    sv->latencies_us.push_back(std::chrono::duration<double, std::micro>(q->t_done - q->t_submit).count());
-  else
-    ++sv->failed;
-  --c.users;
   s.req = nullptr;
+  s.extra.clear();
   s.circuit = -1;
 }
 
@@ -255,6 +319,10 @@ void dispatcher(tn_server* sv) {
       if (e != cudaSuccess) {
         s.req->status = TN_ERR_CUDA;
         s.req->err = std::string("server: ") + cudaGetErrorString(e);
+        for (auto* x : s.extra) {
+          x->status = TN_ERR_CUDA;
+          x->err = s.req->err;
+        }
       }
       retire(sv, (int)si);
       progressed = true;
@@ -297,10 +365,27 @@ void dispatcher(tn_server* sv) {
       }
       q->t_start = Clock::now();
       s.req = q;
+      s.extra.clear();
       s.circuit = q->r.circuit;
       s.building = build;
       ++c.users;
       c.last_use = ++sv->tick;
+      // continuous batching: waiting amplitude requests on the same ready
+      // circuit and output type join this slot's launch
+      if (q->r.kind == TN_REQ_AMPLITUDES && c.state == C_READY) {
+        int64_t total = q->r.n;
+        for (auto jt = std::next(it); jt != sv->queue.end() && (int)s.extra.size() < kMaxMerge - 1; ++jt) {
+          Request* o = *jt;
+          if (o->merged || o->r.kind != TN_REQ_AMPLITUDES || o->r.circuit != q->r.circuit ||
+              o->r.dtype != q->r.dtype || total + o->r.n > kMaxMergeKeys)
+            continue;
+          total += o->r.n;
+          o->merged = true;
+          o->t_start = q->t_start;
+          s.extra.push_back(o);
+          ++c.users;
+        }
+      }
       int rc = TN_OK;
       if (build) {
         rc = tn::enqueue_slices(c.plan, c.kept, c.head->H, s.stream);
@@ -313,6 +398,10 @@ void dispatcher(tn_server* sv) {
       if (rc != TN_OK) {
         q->status = rc;
         q->err = "server: enqueue failed";
+        for (auto* x : s.extra) {
+          x->status = rc;
+          x->err = q->err;
+        }
         if (build) {   // leave the circuit unbuilt: the next request starts over
           cudaStreamSynchronize(s.stream);
           tn_head_free(c.head);
@@ -325,6 +414,11 @@ void dispatcher(tn_server* sv) {
       }
       cudaEventRecord(s.done, s.stream);
       it = sv->queue.erase(it);
+      if (!s.extra.empty()) {   // drop the merged requests from the queue; rescan from the front
+        sv->queue.erase(std::remove_if(sv->queue.begin(), sv->queue.end(), [](Request* x) { return x->merged; }),
+                        sv->queue.end());
+        it = sv->queue.begin();
+      }
     }
     // wait for new work or poll the device again shortly
     sv->cv_work.wait_for(lock, std::chrono::microseconds(50));

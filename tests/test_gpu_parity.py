@@ -592,6 +592,49 @@ def test_server_results_same_alone_and_in_the_mix(tn):
         tn.tn_server_free(sv)
 
 
+def test_server_merges_waiting_amplitude_requests(tn):
+    """Continuous batching: with one slot busy, amplitude requests that queue
+    on the same ready circuit run merged into one launch per slot; each still
+    gets exactly its own amplitudes (complex64 and complex128 requests are
+    batched separately), and a request with a bitstring outside the sparse
+    state fails alone, reporting its own index."""
+    cfg, plan, kept = _server_cases(tn)[1]
+    hd = tn.tn_head_create(plan)
+    tn.tn_contract_slices(plan, kept[0], kept[1], hd)
+    oq, tails = cfg["open_qubits"], cfg["tails"]
+    rng = np.random.default_rng(19)
+
+    def bits(k):
+        g = rng.integers(0, len(tails), k)
+        mu = rng.integers(0, 1 << len(oq), k)
+        return np.array([O.bitstring_index(int(tails[a]), oq, int(b)) for a, b in zip(g, mu)], dtype=np.uint64)
+
+    sv = tn.tn_server_create(n_slots=1)
+    tn.tn_server_add_circuit(sv, plan, kept[0], kept[1])
+    tn.tn_server_wait(sv, tn.tn_server_submit(sv, 0, tn.TN_REQ_AMPLITUDES, 0, bitstrings=bits(4)))   # build the head
+    reqs = []
+    for j in range(40):
+        b = bits(int(rng.integers(1, 300)))
+        dt = tn.TN_C64 if j % 4 == 3 else tn.TN_C128
+        bad = j == 13
+        if bad:
+            b[3] ^= np.uint64(1 << 0)      # tail bit 0 flipped: not one of the tails
+            assert not any((int(b[3]) & ~sum(1 << q for q in oq)) == (int(t) & ~sum(1 << q for q in oq))
+                           for t in tails)
+        reqs.append((b, dt, bad, tn.tn_server_submit(sv, 0, tn.TN_REQ_AMPLITUDES, 0, bitstrings=b, dtype=dt)))
+    for b, dt, bad, t in reqs:
+        if bad:
+            with pytest.raises(tn.TNError) as e:
+                tn.tn_server_wait(sv, t)
+            assert e.value.code == tn.TN_ERR_NOT_IN_STATE and "bitstring 3 " in str(e.value)
+            continue
+        got = tn.tn_server_wait(sv, t)[0]
+        assert np.array_equal(got, tn.tn_amplitudes(hd, b, dtype=dt))
+    st = tn.tn_server_get_stats(sv)
+    assert st["completed"] == 40 and st["failed"] == 1
+    tn.tn_server_free(sv)
+
+
 def test_autotuned_plan_parity(tn):
     """The autotuner times distinct candidate orders and keeps the fastest;
     whatever it keeps computes the same amplitudes."""

@@ -49,6 +49,8 @@ def test_fidelity_xeb_entropy_against_broken_edges(tn):
     plan = tn.tn_plan(cfg["circuit"], oq, cfg["tails"], cfg["edges"], gemm=tn.TN_GEMM_TC_FP16X3, order_trials=2048,
                       order_seed=1)
     bits = _bits(cfg)
+    exact = tn.tn_head_create(plan)                     # all 64 slices: the exact amplitudes on the GPU
+    tn.tn_contract_slices_graph(plan, 0, 64, exact)
     R = 512                                             # samples per group
     rows = []
     for K in range(0, 7):
@@ -68,6 +70,10 @@ def test_fidelity_xeb_entropy_against_broken_edges(tn):
         x = 2.0 ** n * P[grp, mu]
         xeb = O.linear_xeb(n, P[grp, mu])
         lxeb = O.log_xeb(n, P[grp, mu])
+        # the same benchmarks reduced in FP64 on the GPU against the GPU's exact head
+        g_lin, g_log = tn.tn_xeb(exact, s)
+        assert abs(g_lin - xeb) < 1e-4 * max(1.0, abs(xeb)), (K, g_lin, xeb)
+        assert abs(g_log - lxeb) < 1e-4, (K, g_log, lxeb)
         q = O.group_sampling_law(Hh)
         ent, ent_s = O.entropy(q), O.entropy_from_samples(q[grp, mu])
         y = -np.log(q[grp, mu])
@@ -109,3 +115,21 @@ def test_xeb_against_group_size(tn):
             l = 1 << b
             assert abs(v / (F_S * (l - 1) / (l + 1)) - 1) < 0.2, (kept, l, v, F_S)
         assert curve[5] / curve[-1] > 0.93                 # l = 64 against l = 1024
+
+
+def test_xeb_reduction_rejects_samples_outside_the_sparse_state(tn):
+    cfg = ci.config_small(4, 4, 8, seed=11, n_open=6, L=8, n_cut_gates=2)
+    plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"])
+    head = tn.tn_head_create(plan)
+    tn.tn_contract_slices(plan, 0, 16, head)
+    s = tn.tn_sample(head, 64, 0.0, 3)
+    lin, lg = tn.tn_xeb(head, s)
+    psi = O.sliced_statevector(cfg["circuit"], [(g, l) for (g, l, k, v) in cfg["edges"]])
+    P = np.abs(psi) ** 2
+    assert abs(lin - O.linear_xeb(16, P[s.astype(np.int64)])) < 1e-4
+    assert abs(lg - O.log_xeb(16, P[s.astype(np.int64)])) < 1e-4
+    bad = s.copy()
+    bad[7] ^= np.uint64(1)                               # flip a tail bit: not a group
+    with pytest.raises(tn.TNError) as e:
+        tn.tn_xeb(head, bad)
+    assert e.value.code == tn.TN_ERR_NOT_IN_STATE
