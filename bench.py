@@ -43,11 +43,14 @@ import circuit_inputs as ci  # noqa: E402
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch,
 # from a single-kernel ncu capture of the current kernel; keyed by the GEMM
-# engine and the launch's algorithmic complex MACs and bytes (tn_plan_step_info).
 # A dominant launch with no entry reports traffic null.
+# engine, the GEMM tiling ("cta" or "pair") and the launch's algorithmic
+# complex MACs and bytes (tn_plan_step_info).
 MEASURED_TRAFFIC = {
-    ("fp16", 270582939648, 1329594368): (7.264653e9 + 0.2639552e9,
-                                         "profiles/gemm_tc_fp16x3_grid5x6_m14_open10_L64_k6.md"),
+    ("fp16", "cta", 270582939648, 1329594368): (7.264653e9 + 0.2639552e9,
+                                                "profiles/gemm_tc_fp16x3_grid5x6_m14_open10_L64_k6.md"),
+    ("fp16", "pair", 270582939648, 1329594368): (4.611263e9 + 0.264522496e9,
+                                                 "profiles/gemm_tc_pair_fp16x3_grid5x6_m14_open10_L64_k6.md"),
 }
 
 KIND_NAMES = {0: "small_operand", 1: "permute", 2: "bprep_tc", 3: "gemm_tc_3xtf32", 4: "bprep_simt",
@@ -78,6 +81,13 @@ def _workload(name):
         oq = list(range(n - 6, n))
         return dict(circuit=circ, open_qubits=oq, tails=ci.draw_tails(n, oq, 1024, seed=55), edges=[],
                     name="sycamore53_m8_open6_L1024", plan_opts=dict(max_log2_elements=30, auto_slice=16))
+    if name == "precision40":
+        # 40-qubit 5x8 grid, 16 cycles, 12 open qubits x 1 tail, 2^10 slices of
+        # which the kept 1/8 (128) are summed; a step times the first
+        # --slices of them (default 4) and the line projects the kept sum
+        cfg = ci.config_precision40(16)
+        cfg.update(plan_opts=dict(max_log2_elements=32, auto_slice=24), order_trials=4096, default_slices=4)
+        return cfg
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -199,7 +209,7 @@ def run_ours(args):
             "fp16": tn.TN_GEMM_TC_FP16X3}[args.engine]
     t0 = time.time()
     popts = cfg.get("plan_opts", {})
-    trials = ORDER_TRIALS if args.workload in ("sliced30", "syc53") else 0
+    trials = cfg.get("order_trials", ORDER_TRIALS if args.workload in ("sliced30", "syc53") else 0)
     if rank == 0 and args.autotune > 0:
         plan = tn.tn_plan_autotune(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"],
                                    n_candidates=args.autotune, gemm=gemm, order_trials=trials, **popts)
@@ -218,7 +228,7 @@ def run_ours(args):
     plan_s = time.time() - t0
     st = tn.tn_plan_get_stats(plan)
     k = st["n_sliced"]
-    n_slices = 1 << k
+    n_slices = cfg.get("kept", 1 << k)            # the kept prefix [0, kept) of the 2^k slices
     if args.slices:
         n_slices = min(n_slices, args.slices)     # profiling runs only: fewer launches per step
     L, h = int(st["n_tails"]), int(st["n_open"])
@@ -356,7 +366,8 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None, "kernel": KIND_NAMES[kind],
                 "peak_note": f"{peak_src} hbm_gbs"}
-    tr = MEASURED_TRAFFIC.get((args.engine, int(round(macs)), int(round(abytes))))
+    tiling = "pair" if st["gemm_pair"] == 0 and args.engine in ("fp16", "bf16") else "cta"
+    tr = MEASURED_TRAFFIC.get((args.engine, tiling, int(round(macs)), int(round(abytes))))
     if tr:
         roof["traffic"] = tr[0]
         roof["traffic_note"] = (f"ncu dram bytes of one launch of this kernel and shape ({tr[1]}); algorithmic "
@@ -401,11 +412,11 @@ def run_ours(args):
                               if use_graph else "plain launches (tn_contract_slices)") +
                              "; the roofline's per-launch times come from a separate timed region of plain "
                              "launches with CUDA events around each (tn_profile_slices)",
-                "plan_seconds": round(plan_s, 2), "order_trials": ORDER_TRIALS,
+                "plan_seconds": round(plan_s, 2), "order_trials": trials,
                 "autotune_candidates": st["autotune_candidates"], "rank0_slices": [b0, e0_],
                 "gemm_tiles": "CTA pairs (cta_group::2, 256x256) where they apply" if st["gemm_pair"] == 0 and
                               args.engine in ("fp16", "bf16") else "one-CTA 128-row tiles",
-                "partial_slices_for_profiling": bool(args.slices)},
+                "partial_slices_for_profiling": bool(args.slices) and "kept" not in cfg},
         "amplitudes_per_s": round(jobs * n_amp / (ms * 1e-3), 1),
         "slices_per_s": round(jobs * n_slices / (ms * 1e-3), 2),
         "ms_per_pass": round(ms / (n_slices * n_pass), 3),
@@ -417,7 +428,15 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clocks,
     }
-    if ws == 1 and not args.no_cpu_baseline:
+    if "kept" in cfg:
+        out["kept_slices"] = cfg["kept"]
+        out["timed_slices_per_step"] = n_slices
+        out["projected_s_for_kept_sum"] = round(ms * 1e-3 / n_slices * cfg["kept"], 1)
+    if ws == 1 and not args.no_cpu_baseline and "kept" in cfg:
+        out["cpu_baseline"] = {"unavailable": f"one (group, slice) unit of this network is {st['tc_macs']:.2e} complex "
+                                              f"MACs on the planner's order (more on the oracle's own), far beyond a "
+                                              f"bounded CPU sample"}
+    elif ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(out), flush=True)
 
@@ -720,7 +739,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sliced30",
-                    choices=["sliced30", "tiny", "grid25", "syc53", "serve", "batch"])
+                    choices=["sliced30", "tiny", "grid25", "syc53", "precision40", "serve", "batch"])
     ap.add_argument("--circuits", type=int, default=256, help="batch workload: number of circuits")
     ap.add_argument("--engine", default="fp16", choices=["tc", "simt", "bf16", "fp16", "torch"],
                     help="GEMM-step engine: fp16 = FP16x3 (complex64 accuracy, default), tc = 3xTF32, "
@@ -738,6 +757,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "precision40" and not args.slices:
+        args.slices = _workload("precision40")["default_slices"]
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(_spawn_ranks(args.gpus))

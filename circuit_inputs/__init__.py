@@ -279,6 +279,27 @@ def config_sliced30():
                 sample_seed=4, name="grid5x6_m14_open10_L64_k6")
 
 
+def config_precision40(cycles: int = 16):
+    """40-qubit 5x8 grid (seed 4), `cycles` cycles (16 for the full workload);
+    12 open qubits (q28..q39) and one tail (seed 44): 2^12 head amplitudes;
+    10 sliced edges = inputs of 5 fSim gates of the middle cycle (2^10 slices),
+    of which the kept prefix [0, 128) is summed (kept fraction 1/8).  The
+    2^10-amplitude subset has q28 = 1, q29 = 0 (`subset_bitstrings`)."""
+    circ = make_grid_circuit(5, 8, cycles, seed=4)
+    open_q = list(range(28, 40))
+    tails = draw_tails(40, open_q, 1, seed=44)
+    edges = mid_circuit_cut_edges(circ, 5, EDGE_SLICE)
+    return dict(circuit=circ, open_qubits=open_q, tails=tails, edges=edges, kept=128, n_samples=4096,
+                sample_seed=8, name=f"grid5x8_m{cycles}_open12_L1_k10_kept128")
+
+
+def subset_bitstrings(cfg) -> np.ndarray:
+    """The 2^10 bitstrings of the precision workload's error subset: the tail,
+    q28 = 1, q29 = 0, and q30..q39 = mu (bit j of mu on q30+j), mu = 0..1023."""
+    base = int(cfg["tails"][0]) | (1 << 28)
+    return np.array([base | (mu << 30) for mu in range(1 << 10)], dtype=np.uint64)
+
+
 def config_grid25():
     """25-qubit 5x5 grid, 10 cycles, all qubits open, one group, no slicing: a
     small case with the same step kernels (operands above L2, ~2 GB on device)."""

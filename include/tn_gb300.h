@@ -110,6 +110,11 @@ typedef struct {
   int    gemm_pair;           /* 0: 16-bit GEMM steps with 256-wide tiles and M >= 256 run on CTA pairs
                                  (cta_group::2, 256 x 256 tiles); -1: one-CTA 128-row tiles only.
                                  tn_plan_autotune times both and keeps the faster. */
+  int    side_bprep;          /* 0: a tensor-core B-preparation step whose operand is already written
+                                 runs on a second stream beside the previous tensor-core GEMM (an
+                                 HBM-bound step next to a tensor-bound one); its operand and output
+                                 stay allocated from that GEMM on.  -1: every step in order on the
+                                 caller's stream.  tn_profile_slices always runs in order. */
 } tn_plan_opts;
 
 typedef struct tn_plan tn_plan_t;
@@ -135,6 +140,7 @@ typedef struct {
   int     n_internal_sliced;  /* edges added by auto_slice; n_launches, tc_macs and alg_bytes count
                                  all 2^n_internal_sliced passes of one user slice */
   int     gemm_pair;          /* the plan's tn_plan_opts.gemm_pair (as chosen by tn_plan_autotune) */
+  int     n_side_bprep;       /* B-preparation steps that run beside an earlier GEMM (side_bprep) */
 } tn_plan_stats;
 
 /* Plan the contraction (host).  `order`: n_pairs pairs (i, j) of leaf ids, the

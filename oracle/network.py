@@ -172,11 +172,20 @@ def _absorb_small(T, out_set, stats=None):
             break
 
 
+_ORDER_CACHE = {}
+
+
 def _contract(net, out_labels, stats=None):
     T = net.tensors
     out_set = set(out_labels)
     _absorb_small(T, out_set, stats)
-    order = _find_order({i: l for i, (_, l) in T.items()}, out_set)
+    # The order depends on the label lists alone, which are the same for every
+    # slice of one network (only the cut vectors' entries change), so it is
+    # found once per label structure.
+    key = (tuple(sorted((i, tuple(l)) for i, (_, l) in T.items())), tuple(sorted(out_set)))
+    order = _ORDER_CACHE.get(key)
+    if order is None:
+        order = _ORDER_CACHE[key] = _find_order({i: l for i, (_, l) in T.items()}, out_set)
     for (a, b, c) in order:
         A, la = T.pop(a)
         B, lb = T.pop(b)

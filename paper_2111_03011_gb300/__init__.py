@@ -57,7 +57,7 @@ class tn_plan_opts(C.Structure):
     _fields_ = [("max_log2_elements", C.c_double), ("gemm", C.c_int), ("host_only", C.c_int),
                 ("order_trials", C.c_int), ("order_seed", C.c_uint64), ("max_host_absorb_log2", C.c_int),
                 ("small_max_bits", C.c_int), ("auto_slice", C.c_int), ("host_fold_log2", C.c_int),
-                ("gemm_pair", C.c_int)]
+                ("gemm_pair", C.c_int), ("side_bprep", C.c_int)]
 
 
 class tn_server_opts(C.Structure):
@@ -91,7 +91,7 @@ class tn_plan_stats(C.Structure):
                 ("max_log2_elements", C.c_double), ("workspace_bytes", C.c_int64),
                 ("n_gemm_tc", C.c_int), ("n_gemm_simt", C.c_int), ("n_small", C.c_int), ("n_permute", C.c_int),
                 ("measured_slice_ms", C.c_double), ("autotune_candidates", C.c_int),
-                ("n_internal_sliced", C.c_int), ("gemm_pair", C.c_int)]
+                ("n_internal_sliced", C.c_int), ("gemm_pair", C.c_int), ("n_side_bprep", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -234,7 +234,7 @@ class Head:
 
 def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements=0.0, gemm=TN_GEMM_AUTO,
             host_only=False, order_trials=0, order_seed=0, max_host_absorb_log2=0, small_max_bits=0,
-            auto_slice=0, host_fold_log2=0, gemm_pair=0) -> Plan:
+            auto_slice=0, host_fold_log2=0, gemm_pair=0, side_bprep=0) -> Plan:
     gates = gates_to_c(circuit)
     circ = tn_circuit(int(circuit.n_qubits), len(circuit.gates), gates)
     oq = (C.c_int * max(1, len(open_qubits)))(*[int(q) for q in open_qubits])
@@ -246,7 +246,7 @@ def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements
         ed[i] = tn_edge(int(g), int(leg), int(kind), int(val))
     opts = tn_plan_opts(float(max_log2_elements), int(gemm), int(bool(host_only)), int(order_trials),
                         int(order_seed), int(max_host_absorb_log2), int(small_max_bits), int(auto_slice),
-                        int(host_fold_log2), int(gemm_pair))
+                        int(host_fold_log2), int(gemm_pair), int(side_bprep))
     h = C.c_void_p()
     if order is not None:
         o = np.ascontiguousarray(np.asarray(order, dtype=np.int32).reshape(-1))
@@ -259,7 +259,7 @@ def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements
 
 def tn_plan_autotune(circuit, open_qubits, tails, edges=(), n_candidates=4, max_log2_elements=0.0,
                      gemm=TN_GEMM_AUTO, order_trials=0, order_seed=0, max_host_absorb_log2=0, small_max_bits=0,
-                     stream=None, auto_slice=0, host_fold_log2=0, gemm_pair=0) -> Plan:
+                     stream=None, auto_slice=0, host_fold_log2=0, gemm_pair=0, side_bprep=0) -> Plan:
     gates = gates_to_c(circuit)
     circ = tn_circuit(int(circuit.n_qubits), len(circuit.gates), gates)
     oq = (C.c_int * max(1, len(open_qubits)))(*[int(q) for q in open_qubits])
@@ -271,7 +271,7 @@ def tn_plan_autotune(circuit, open_qubits, tails, edges=(), n_candidates=4, max_
         ed[i] = tn_edge(int(g), int(leg), int(kind), int(val))
     opts = tn_plan_opts(float(max_log2_elements), int(gemm), 0, int(order_trials), int(order_seed),
                         int(max_host_absorb_log2), int(small_max_bits), int(auto_slice), int(host_fold_log2),
-                        int(gemm_pair))
+                        int(gemm_pair), int(side_bprep))
     h = C.c_void_p()
     _check(_lib.tn_plan_autotune(C.byref(circ), C.byref(spec), ed, len(edges), C.byref(opts), int(n_candidates),
                                  _stream(stream), C.byref(h)))

@@ -100,7 +100,9 @@ static void plan_release(tn_plan_t* p) {
     cudaFree(p->d_scale);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     for (auto& e : p->prof_events) cudaEventDestroy(e);
-    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (auto& e : p->side_fork) if (e) cudaEventDestroy(e);
+    for (auto& e : p->side_join) if (e) cudaEventDestroy(e);
+    if (p->side_stream) cudaStreamDestroy(p->side_stream);
     if (cur >= 0) cudaSetDevice(cur);
   }
   delete p;
@@ -157,6 +159,21 @@ static int plan_upload(tn_plan_t* p) {
     if (n_static)
       CUDA_TRY(cudaMemcpy(p->d_scale, P.scale_static.data(), n_static * sizeof(unsigned int), cudaMemcpyHostToDevice));
   }
+  if (P.n_side_bprep > 0) {
+    const size_t ns = P.steps.size();
+    p->side_fork.assign(ns, nullptr);
+    p->side_join.assign(ns, nullptr);
+    p->forks_at.assign(ns, {});
+    CUDA_TRY(cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking));
+    for (size_t i = 0; i < ns; ++i) {
+      const int f = P.steps[i].fork;
+      if (f < 0) continue;
+      if (f >= (int)i) return fail(TN_ERR_INVALID, "internal: side step forks after itself");
+      p->forks_at[f].push_back((int)i);
+      if (!p->side_fork[f]) CUDA_TRY(cudaEventCreateWithFlags(&p->side_fork[f], cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&p->side_join[i], cudaEventDisableTiming));
+    }
+  }
   return TN_OK;
 }
 
@@ -208,6 +225,7 @@ extern "C" int tn_plan(const tn_circuit* circuit, const tn_open_spec* open_spec,
     if (opts->host_fold_log2 > 16) return fail(TN_ERR_INVALID, "host_fold_log2 must be at most 16");
     if (opts->host_fold_log2 != 0) in.fold_log2 = opts->host_fold_log2 < 0 ? -1 : opts->host_fold_log2;
     in.gemm_pair = opts->gemm_pair < 0 ? -1 : 0;
+    in.side_bprep = opts->side_bprep >= 0;
   }
   if (in.gemm_engine < 0 || in.gemm_engine > 4) return fail(TN_ERR_INVALID, "unknown gemm engine");
   if (in.cap_log2 > 34) return fail(TN_ERR_INVALID, "size cap above 2^34 elements");
@@ -247,6 +265,7 @@ extern "C" int tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* s) {
   s->alg_bytes = P.alg_bytes * ni;
   s->n_internal_sliced = P.n_internal;
   s->gemm_pair = P.gemm_pair;
+  s->n_side_bprep = P.n_side_bprep;
   s->max_log2_elements = P.max_log2;
   s->workspace_bytes = P.workspace_bytes;
   s->measured_slice_ms = plan->measured_slice_ms;
@@ -377,8 +396,112 @@ static unsigned int* scale_ptr(const tn_plan_t* p, int slot) {
   return p->d_scale + (slot >= 0 ? n_static + slot : (int64_t)(-(slot + 2)));
 }
 
+// Launch one step of the launch list for the full slice id s on stream st
+// (`side`: a B-prep beside a running GEMM, launched with one block per SM).
+static cudaError_t launch_step(tn_plan_t* p, const tn::Step& x, int64_t s, cudaStream_t st, bool side) {
+  const tn::Plan& P = p->P;
+  cudaError_t e = cudaSuccess;
+  switch (x.kind) {
+    case tn::ST_SMALL: {
+      tn::SmallParams sp;
+      sp.A = ref_ptr(p, x.a, s);
+      sp.B = ref_ptr(p, x.b, s);
+      sp.C = buf_ptr(p, x.c);
+      sp.a_pstride = 1LL << x.rA;
+      sp.b_pstride = 1LL << x.rB;
+      sp.c_pstride = 1LL << x.rC;
+      sp.M = 1LL << (x.rA - x.nk);
+      sp.PC = x.PC;
+      sp.rA = x.rA;
+      sp.nk = x.nk;
+      sp.nn = x.nn;
+      for (int j = 0; j < 4; ++j) sp.kpos[j] = x.kposA[j];
+      std::memcpy(sp.boffK, x.boffK, sizeof(sp.boffK));
+      std::memcpy(sp.boffN, x.boffN, sizeof(sp.boffN));
+      sp.mapA = p->d_meta + x.mapA_off;
+      sp.mapB = p->d_meta + x.mapB_off;
+      sp.mapA_mode = x.mapA_mode;
+      sp.mapB_mode = x.mapB_mode;
+      sp.amax = scale_ptr(p, x.max_slot);
+      e = tn::launch_small(sp, st);
+      break;
+    }
+    case tn::ST_PERMUTE: {
+      tn::PermParams pp;
+      pp.in = ref_ptr(p, x.a, s);
+      pp.out = buf_ptr(p, x.c);
+      pp.pstride = 1LL << x.rA;
+      pp.P = x.PA;
+      pp.t = x.t_bits;
+      pp.n_rest = x.n_rest;
+      std::memcpy(pp.rest_in, x.rest_in, sizeof(pp.rest_in));
+      std::memcpy(pp.rest_out, x.rest_out, sizeof(pp.rest_out));
+      pp.tab = p->d_meta + x.tab_off;
+      pp.split = x.split;
+      pp.scale = scale_ptr(p, x.slot);
+      e = tn::launch_permute(pp, st);
+      break;
+    }
+    case tn::ST_BPREP_C:
+    case tn::ST_BPREP_TC: {
+      tn::BPrepParams bp;
+      bp.B = ref_ptr(p, x.a, s);
+      bp.out = buf_ptr(p, x.c);
+      bp.b_pstride = 1LL << x.rA;
+      bp.PB = x.PA;
+      bp.nk = x.nk;
+      bp.nn = x.nn;
+      bp.bk = p->d_meta + x.bk_off;
+      bp.bn = p->d_meta + x.bn_off;
+      bp.h16 = x.h16;
+      bp.scale = scale_ptr(p, x.slot);
+      e = x.kind == tn::ST_BPREP_C ? tn::launch_bprep_c(bp, st) : tn::launch_bprep_tc(bp, st, side);
+      break;
+    }
+    case tn::ST_GEMM_SIMT:
+    case tn::ST_GEMM_TC: {
+      tn::GemmParams gp;
+      gp.A = ref_ptr(p, x.a, s);
+      gp.B = (const void*)ref_ptr(p, x.b, s);
+      gp.C = buf_ptr(p, x.c);
+      gp.M = 1LL << x.nm;
+      gp.N = 1LL << x.nn;
+      gp.K = 1LL << x.nk;
+      gp.PA = x.PA;
+      gp.PB = x.PB;
+      gp.PC = x.PC;
+      gp.mapA = p->d_meta + x.mapA_off;
+      gp.mapB = p->d_meta + x.mapB_off;
+      gp.mapA_mode = x.mapA_mode;
+      gp.mapB_mode = x.mapB_mode;
+      gp.h16 = x.h16;
+      gp.scaleA = scale_ptr(p, x.slot);
+      gp.scaleB = scale_ptr(p, x.slotB);
+      gp.amax = scale_ptr(p, x.max_slot);
+      gp.pair = P.gemm_pair;
+      e = x.kind == tn::ST_GEMM_SIMT ? tn::launch_gemm_simt(gp, st) : tn::launch_gemm_tc(gp, p->d_status, st);
+      break;
+    }
+    case tn::ST_ABSMAX: {
+      tn::AbsmaxParams ap;
+      ap.in = ref_ptr(p, x.a, s);
+      ap.n = x.PA << x.rA;
+      ap.out = scale_ptr(p, x.slot);
+      e = tn::launch_absmax(ap, st);
+      break;
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return e;
+}
+
 // One pass of the launch list for the full slice id s (user bits, then the
-// bits of automatically sliced edges).
+// bits of automatically sliced edges).  With per-launch timing events (ev)
+// every step runs in order on st; otherwise a B-prep step with fork f is
+// launched on the plan's side stream just before step f (after everything
+// before f is done) and step f + ... waits for it right before the GEMM that
+// consumes its output.
 static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEvent_t* ev) {
   const tn::Plan& P = p->P;
   if (P.n_scale_slots > 0) {
@@ -386,106 +509,48 @@ static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEv
                                     (size_t)P.n_scale_slots * sizeof(unsigned int), st);
     if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("scale reset: ") + cudaGetErrorString(e));
   }
+  const bool use_side = !ev && p->side_stream != nullptr;
+  std::vector<int> pending;      // side steps launched and not yet joined
+  auto join_pending = [&]() {
+    for (int j : pending) cudaStreamWaitEvent(st, p->side_join[j], 0);
+    pending.clear();
+  };
   int si = 0;
   for (const tn::Step& x : P.steps) {
     cudaError_t e = cudaSuccess;
-    if (ev) cudaEventRecord(ev[2 * si], st);
-    switch (x.kind) {
-      case tn::ST_SMALL: {
-        tn::SmallParams sp;
-        sp.A = ref_ptr(p, x.a, s);
-        sp.B = ref_ptr(p, x.b, s);
-        sp.C = buf_ptr(p, x.c);
-        sp.a_pstride = 1LL << x.rA;
-        sp.b_pstride = 1LL << x.rB;
-        sp.c_pstride = 1LL << x.rC;
-        sp.M = 1LL << (x.rA - x.nk);
-        sp.PC = x.PC;
-        sp.rA = x.rA;
-        sp.nk = x.nk;
-        sp.nn = x.nn;
-        for (int j = 0; j < 4; ++j) sp.kpos[j] = x.kposA[j];
-        std::memcpy(sp.boffK, x.boffK, sizeof(sp.boffK));
-        std::memcpy(sp.boffN, x.boffN, sizeof(sp.boffN));
-        sp.mapA = p->d_meta + x.mapA_off;
-        sp.mapB = p->d_meta + x.mapB_off;
-        sp.mapA_mode = x.mapA_mode;
-        sp.mapB_mode = x.mapB_mode;
-        sp.amax = scale_ptr(p, x.max_slot);
-        e = tn::launch_small(sp, st);
-        break;
+    if (use_side && !p->forks_at[si].empty()) {
+      e = cudaEventRecord(p->side_fork[si], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side_stream, p->side_fork[si], 0);
+      for (int j : p->forks_at[si]) {
+        if (e == cudaSuccess) e = launch_step(p, P.steps[j], s, p->side_stream, true);
+        if (e == cudaSuccess) e = cudaEventRecord(p->side_join[j], p->side_stream);
+        if (e == cudaSuccess) pending.push_back(j);
       }
-      case tn::ST_PERMUTE: {
-        tn::PermParams pp;
-        pp.in = ref_ptr(p, x.a, s);
-        pp.out = buf_ptr(p, x.c);
-        pp.pstride = 1LL << x.rA;
-        pp.P = x.PA;
-        pp.t = x.t_bits;
-        pp.n_rest = x.n_rest;
-        std::memcpy(pp.rest_in, x.rest_in, sizeof(pp.rest_in));
-        std::memcpy(pp.rest_out, x.rest_out, sizeof(pp.rest_out));
-        pp.tab = p->d_meta + x.tab_off;
-        pp.split = x.split;
-        pp.scale = scale_ptr(p, x.slot);
-        e = tn::launch_permute(pp, st);
-        break;
+      if (e != cudaSuccess) {
+        join_pending();
+        return fail(TN_ERR_CUDA, std::string("side launch: ") + cudaGetErrorString(e));
       }
-      case tn::ST_BPREP_C:
-      case tn::ST_BPREP_TC: {
-        tn::BPrepParams bp;
-        bp.B = ref_ptr(p, x.a, s);
-        bp.out = buf_ptr(p, x.c);
-        bp.b_pstride = 1LL << x.rA;
-        bp.PB = x.PA;
-        bp.nk = x.nk;
-        bp.nn = x.nn;
-        bp.bk = p->d_meta + x.bk_off;
-        bp.bn = p->d_meta + x.bn_off;
-        bp.h16 = x.h16;
-        bp.scale = scale_ptr(p, x.slot);
-        e = x.kind == tn::ST_BPREP_C ? tn::launch_bprep_c(bp, st) : tn::launch_bprep_tc(bp, st);
-        break;
-      }
-      case tn::ST_GEMM_SIMT:
-      case tn::ST_GEMM_TC: {
-        tn::GemmParams gp;
-        gp.A = ref_ptr(p, x.a, s);
-        gp.B = (const void*)ref_ptr(p, x.b, s);
-        gp.C = buf_ptr(p, x.c);
-        gp.M = 1LL << x.nm;
-        gp.N = 1LL << x.nn;
-        gp.K = 1LL << x.nk;
-        gp.PA = x.PA;
-        gp.PB = x.PB;
-        gp.PC = x.PC;
-        gp.mapA = p->d_meta + x.mapA_off;
-        gp.mapB = p->d_meta + x.mapB_off;
-        gp.mapA_mode = x.mapA_mode;
-        gp.mapB_mode = x.mapB_mode;
-        gp.h16 = x.h16;
-        gp.scaleA = scale_ptr(p, x.slot);
-        gp.scaleB = scale_ptr(p, x.slotB);
-        gp.amax = scale_ptr(p, x.max_slot);
-        gp.pair = P.gemm_pair;
-        e = x.kind == tn::ST_GEMM_SIMT ? tn::launch_gemm_simt(gp, st) : tn::launch_gemm_tc(gp, p->d_status, st);
-        break;
-      }
-      case tn::ST_ABSMAX: {
-        tn::AbsmaxParams ap;
-        ap.in = ref_ptr(p, x.a, s);
-        ap.n = x.PA << x.rA;
-        ap.out = scale_ptr(p, x.slot);
-        e = tn::launch_absmax(ap, st);
-        break;
-      }
-      default:
-        return fail(TN_ERR_INVALID, "internal: unknown step kind");
     }
-    if (e != cudaSuccess) return fail(TN_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    if (ev) cudaEventRecord(ev[2 * si], st);
+    if (use_side && x.fork >= 0) {
+      // launched on the side stream before step x.fork: wait for it here
+      e = cudaStreamWaitEvent(st, p->side_join[si], 0);
+      pending.erase(std::remove(pending.begin(), pending.end(), si), pending.end());
+    } else {
+      e = launch_step(p, x, s, st, false);
+    }
+    if (e == cudaErrorInvalidValue && (x.kind < 0 || x.kind > tn::ST_ABSMAX)) {
+      join_pending();
+      return fail(TN_ERR_INVALID, "internal: unknown step kind");
+    }
+    if (e != cudaSuccess) {
+      join_pending();
+      return fail(TN_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    }
     if (ev) cudaEventRecord(ev[2 * si + 1], st);
     ++si;
   }
+  join_pending();
   if (ev) cudaEventRecord(ev[2 * si], st);
   tn::AccumParams ap;
   ap.F = ref_ptr(p, P.fin.ref, s);

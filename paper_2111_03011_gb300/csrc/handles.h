@@ -37,7 +37,11 @@ struct tn_plan {
   int autotune_candidates = 0;
   std::vector<GraphEntry> graphs;     // captured slice ranges (tn_contract_slices_graph)
   std::vector<cudaEvent_t> prof_events;   // tn_profile_slices: reused timing events
-  cudaStream_t cap_stream = nullptr;
+  // side stream of the B-prep steps that run beside an earlier GEMM
+  // (Step::fork): one fork event per fork step, one join event per side step
+  cudaStream_t side_stream = nullptr;
+  std::vector<cudaEvent_t> side_fork, side_join;   // indexed by step
+  std::vector<std::vector<int>> forks_at;          // step -> side steps launched before it
   bool on_device = false;
   int device = -1;
   float2* d_leaves = nullptr;

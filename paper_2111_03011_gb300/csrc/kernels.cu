@@ -336,18 +336,36 @@ __global__ void k_bprep_tc(BPrepParams p) {
   T* hi = (T*)p.out;                          // pairs: [PB][2N][K] pairs of reals
   T* lo = hi + 2 * total;
   const float sc = FMT == 2 ? pow2f(fp16_scale_exp(*p.scale)) : 1.0f;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pb = e / per, r = e - pb * per;
-    const int64_t n = r >> p.nk, k = r & (K - 1);
-    const float2 b = p.B[pb * p.b_pstride + p.bk[k] + p.bn[n]];
-    const int64_t o0 = (pb * 2 * N + 2 * n) * K + k;   // pair (2k, 2k+1) of row 2n
-    T h, l;
-    Pair<FMT>::split(b.x, -b.y, sc, h, l);
-    hi[o0] = h;
-    lo[o0] = l;
-    Pair<FMT>::split(b.y, b.x, sc, h, l);
-    hi[o0 + K] = h;                                    // row 2n + 1
-    lo[o0 + K] = l;
+  // kU elements per thread and round, their loads issued before any store,
+  // so that a grid of one block per SM (beside a running GEMM) still keeps
+  // enough loads in flight
+  constexpr int kU = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e0 < total; e0 += kU * stride) {
+    float2 b[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e < total) {
+        const int64_t pb = e / per, r = e - pb * per;
+        b[u] = p.B[pb * p.b_pstride + p.bk[r & (K - 1)] + p.bn[r >> p.nk]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e >= total) break;
+      const int64_t pb = e / per, r = e - pb * per;
+      const int64_t n = r >> p.nk, k = r & (K - 1);
+      const int64_t o0 = (pb * 2 * N + 2 * n) * K + k;   // pair (2k, 2k+1) of row 2n
+      T h, l;
+      Pair<FMT>::split(b[u].x, -b[u].y, sc, h, l);
+      hi[o0] = h;
+      lo[o0] = l;
+      Pair<FMT>::split(b[u].y, b[u].x, sc, h, l);
+      hi[o0 + K] = h;                                    // row 2n + 1
+      lo[o0 + K] = l;
+    }
   }
 }
 
@@ -358,9 +376,12 @@ cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s) {
+cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s, bool beside_gemm) {
   const int64_t total = p.PB << (p.nk + p.nn);
-  const unsigned grid = (unsigned)std::max<int64_t>(std::min<int64_t>((total + 255) / 256, (int64_t)kSMs * 16), 1);
+  // beside a running GEMM (one CTA per SM, most of the registers and shared
+  // memory): one 256-thread block per SM, which fits next to it
+  const int64_t cap = beside_gemm ? (int64_t)kSMs : (int64_t)kSMs * 16;
+  const unsigned grid = (unsigned)std::max<int64_t>(std::min<int64_t>((total + 255) / 256, cap), 1);
   if (p.h16 == 2) k_bprep_tc<2><<<grid, 256, 0, s>>>(p);
   else if (p.h16 == 1) k_bprep_tc<1><<<grid, 256, 0, s>>>(p);
   else k_bprep_tc<0><<<grid, 256, 0, s>>>(p);

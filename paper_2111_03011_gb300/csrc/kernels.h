@@ -92,7 +92,7 @@ cudaError_t launch_small(const SmallParams& p, cudaStream_t s);
 cudaError_t launch_absmax(const AbsmaxParams& p, cudaStream_t s);
 cudaError_t launch_permute(const PermParams& p, cudaStream_t s);
 cudaError_t launch_bprep_c(const BPrepParams& p, cudaStream_t s);
-cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s);
+cudaError_t launch_bprep_tc(const BPrepParams& p, cudaStream_t s, bool beside_gemm = false);
 cudaError_t launch_gemm_simt(const GemmParams& p, cudaStream_t s);
 cudaError_t launch_accum(const AccumParams& p, cudaStream_t s);
 

@@ -1070,6 +1070,45 @@ static int layout_steps(Plan& plan, std::string& err) {
   return TN_OK;
 }
 
+// Tensor-core B-preparation steps that may run beside an earlier GEMM.  The
+// B operand of a stem contraction is usually a branch finished long before
+// (only the A side comes from the step just before), so its preparation, an
+// HBM-bound pass, can run on a second stream during the previous tensor-core
+// GEMM, which leaves HBM mostly idle.  A step qualifies when its operand was
+// written before that GEMM and its FP16 scale (if any) is a leaf's static
+// slot or the operand producer's epilogue maximum (not an ABSMAX step of its
+// own).  Its output buffer then starts at the fork, so nothing running
+// between the fork and the consuming GEMM shares its memory; its operand is
+// live from its producer to the B-prep already.
+static void schedule_side_bprep(Plan& plan) {
+  std::map<int, int> producer;   // workspace buffer id -> step that writes it
+  const int n = (int)plan.steps.size();
+  plan.n_side_bprep = 0;
+  for (int i = 0; i < n; ++i) {
+    Step& x = plan.steps[i];
+    if (x.kind == ST_BPREP_TC && i + 1 < n && plan.steps[i + 1].kind == ST_GEMM_TC &&
+        plan.steps[i + 1].b.kind == 1 && plan.steps[i + 1].b.id == x.c.id) {
+      int prod = -1;
+      bool ok = true;
+      if (x.a.kind == 1) {
+        auto it = producer.find(x.a.id);
+        ok = it != producer.end();
+        if (ok) prod = it->second;
+      }
+      if (ok && x.slot >= 0) ok = prod >= 0 && plan.steps[prod].max_slot == x.slot;
+      int q = -1;
+      for (int j = i - 1; ok && j > prod; --j)
+        if (plan.steps[j].kind == ST_GEMM_TC) { q = j; break; }
+      if (ok && q >= 0) {
+        x.fork = q;
+        plan.bufs[x.c.id].first = std::min(plan.bufs[x.c.id].first, q);
+        ++plan.n_side_bprep;
+      }
+    }
+    if (x.c.kind == 1) producer[x.c.id] = i;
+  }
+}
+
 static void plan_arena(Plan& plan) {
   std::vector<int> idx(plan.bufs.size());
   for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
@@ -1421,6 +1460,7 @@ int build_plan(const PlanInput& in, Plan& plan, std::string& err) {
   for (size_t g = 0; g < pidx.size(); ++g) pidx[g] = (uint32_t)pat_index(fp, plan.book.tails[g]);
   plan.fin.pidx_off = meta_push(plan, pidx);
   touch(plan, F.ref, (int)plan.steps.size());
+  if (in.side_bprep) schedule_side_bprep(plan);
   plan_arena(plan);
   return TN_OK;
 }
@@ -1482,7 +1522,7 @@ std::string describe_plan(const Plan& plan, bool with_data) {
       << ",\"PA\":" << st.PA << ",\"PB\":" << st.PB << ",\"PC\":" << st.PC << ",\"macs\":" << st.macs
       << ",\"bytes\":" << st.bytes << ",\"rA\":" << st.rA << ",\"rB\":" << st.rB << ",\"rC\":" << st.rC
       << ",\"a\":[" << st.a.kind << "," << st.a.id << "],\"b\":[" << st.b.kind << "," << st.b.id << "],\"c\":["
-      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"h16\":" << st.h16 << ",\"slot\":" << st.slot << ",\"slotB\":" << st.slotB << ",\"max_slot\":" << st.max_slot
+      << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"h16\":" << st.h16 << ",\"slot\":" << st.slot << ",\"slotB\":" << st.slotB << ",\"max_slot\":" << st.max_slot << ",\"fork\":" << st.fork
       << ",\"tab_off\":" << st.tab_off << ",\"n_rest\":" << st.n_rest << ",\"rest_in\":[";
     for (int v = 0; v < st.n_rest; ++v) o << (v ? "," : "") << (int)st.rest_in[v];
     o << "],\"rest_out\":[";

@@ -101,6 +101,9 @@ struct Step {
   uint8_t rest_in[64] = {0}, rest_out[64] = {0};
   // BPREP: gather tables bk[K], bn[N] in meta (uint32)
   int64_t bk_off = 0, bn_off = 0;
+  // BPREP_TC run on the side stream: it may start once every step before
+  // `fork` (a tensor-core GEMM) is done, and the next step waits for it
+  int fork = -1;
   double macs = 0, bytes = 0;
   int contraction = -1;   // index of the pairwise contraction this step belongs to
 };
@@ -138,6 +141,7 @@ struct Plan {
   double cap_log2 = 28;
   int gemm_engine = 0;
   int gemm_pair = 0;               // GemmParams::pair of every tensor-core GEMM step
+  int n_side_bprep = 0;            // B-prep steps with fork >= 0
   int small_max_bits = 4;
 
   std::vector<Leg> legs;
@@ -184,6 +188,7 @@ struct PlanInput {
   int auto_slice = 0;       // at most this many extra sliced edges when no order fits the cap
   int fold_log2 = 12;       // host folding of small contractions of host tensors (-1: off)
   int gemm_pair = 0;        // 0: CTA-pair GEMM tiles where they apply; -1: one-CTA tiles only
+  bool side_bprep = true;   // B-prep steps whose operand is ready run beside the previous GEMM
 };
 
 int build_plan(const PlanInput& in, Plan& plan, std::string& err);

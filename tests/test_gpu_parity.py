@@ -635,6 +635,31 @@ def test_server_merges_waiting_amplitude_requests(tn):
     tn.tn_server_free(sv)
 
 
+@pytest.mark.parametrize("gemm", [3, 4], ids=["bf16x3", "fp16x3"])
+def test_side_stream_bprep_bitwise_equal(tn, gemm):
+    """B-prep steps launched on the side stream beside an earlier GEMM give the
+    same head, bit for bit, as every step in order on one stream: in plain
+    launches, in a captured graph, and against tn_profile_slices (which runs in
+    order)."""
+    cfg = ci.config_sliced30()
+    heads = {}
+    for side in (0, -1):
+        plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=gemm,
+                          order_trials=2048, order_seed=1, side_bprep=side)
+        assert (tn.tn_plan_get_stats(plan)["n_side_bprep"] >= 3) == (side == 0)
+        h1 = tn.tn_head_create(plan)
+        tn.tn_contract_slices(plan, 0, 3, h1)
+        h2 = tn.tn_head_create(plan)
+        tn.tn_contract_slices_graph(plan, 0, 3, h2)
+        h3 = tn.tn_head_create(plan)
+        tn.tn_profile_slices(plan, 0, 3, h3)
+        heads[side] = [read_head(tn, plan, h, cfg) for h in (h1, h2, h3)]
+    ref = heads[-1][2]
+    for side in (0, -1):
+        for h in heads[side]:
+            assert np.array_equal(h, ref)
+
+
 def test_autotuned_plan_parity(tn):
     """The autotuner times distinct candidate orders and keeps the fastest;
     whatever it keeps computes the same amplitudes."""

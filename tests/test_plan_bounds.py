@@ -104,6 +104,29 @@ def _check_plan(d):
             assert 8 * s["PA"] << s["rA"] <= cap(s["a"])
         else:
             raise AssertionError(f"unknown step kind {k}")
+    # B-prep steps run on the side stream from their fork: the fork is an
+    # earlier tensor-core GEMM, the operand is written before it, and both the
+    # operand and the output are live from the fork to the consuming GEMM (so
+    # the disjointness above keeps every concurrent step off their memory)
+    steps = d["steps"]
+    for i, s in enumerate(steps):
+        f = s.get("fork", -1)
+        if f < 0:
+            continue
+        assert s["kind"] == ST_BPREP_TC and 0 <= f < i and steps[f]["kind"] == ST_GEMM_TC
+        g = steps[i + 1]
+        assert g["kind"] == ST_GEMM_TC and g["b"] == s["c"]
+        out = bufs[s["c"][1]]
+        assert out[2] <= f and out[3] >= i + 1
+        if s["a"][0] == 1:
+            prod = [j for j in range(i) if steps[j]["c"] == s["a"]]
+            assert len(prod) == 1 and prod[0] < f
+            assert bufs[s["a"][1]][2] <= prod[0] and bufs[s["a"][1]][3] >= i
+            if s["slot"] >= 0:
+                assert steps[prod[0]]["max_slot"] == s["slot"]
+        else:
+            assert s["slot"] < 0 or s["slot"] <= -2 or s["h16"] != 2
+        assert all(steps[j]["c"] != s["a"] for j in range(f, i))
     f = d["final"]
     L = len(d.get("_tails", [])) or None
     assert 8 * f["PF"] << f["rF"] <= cap(f["ref"])
@@ -153,9 +176,17 @@ def test_launch_extents_auto_sliced_and_random_gates(tn):
 
 def test_launch_extents_of_the_30_qubit_workload(tn):
     cfg = ci.config_sliced30()
-    for gemm in (1, 4):
+    for gemm in (1, 3, 4):
         p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True, gemm=gemm,
                        order_trials=2048)
         d = tn.tn_plan_describe(p, with_data=True)
         d["_tails"] = list(cfg["tails"])
         _check_plan(d)
+        # the large B-preps of the stem (operands of 2^19 x 63 and 2^23 elements) run beside a GEMM
+        side = [s for s in d["steps"] if s.get("fork", -1) >= 0]
+        assert tn.tn_plan_get_stats(p)["n_side_bprep"] == len(side) >= 3
+        assert max(8 * s["PA"] << s["rA"] for s in side) >= 1 << 27
+    p = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], host_only=True, gemm=4,
+                   order_trials=2048, side_bprep=-1)
+    assert tn.tn_plan_get_stats(p)["n_side_bprep"] == 0
+    assert all(s["fork"] == -1 for s in tn.tn_plan_describe(p)["steps"])
