@@ -110,11 +110,14 @@ typedef struct {
   int    gemm_pair;           /* 0: 16-bit GEMM steps with 256-wide tiles and M >= 256 run on CTA pairs
                                  (cta_group::2, 256 x 256 tiles); -1: one-CTA 128-row tiles only.
                                  tn_plan_autotune times both and keeps the faster. */
-  int    side_bprep;          /* 0: a tensor-core B-preparation step whose operand is already written
-                                 runs on a second stream beside the previous tensor-core GEMM (an
-                                 HBM-bound step next to a tensor-bound one); its operand and output
-                                 stay allocated from that GEMM on.  -1: every step in order on the
-                                 caller's stream.  tn_profile_slices always runs in order. */
+  int    side_bprep;          /* 1: a large tensor-core B-preparation step (>= 64 MiB) whose operand
+                                 is already written runs on a second stream beside the previous
+                                 tensor-core GEMM if that GEMM is long (>= 2^34 complex MACs): an
+                                 HBM-bound step next to a tensor-bound one; its operand and output
+                                 stay allocated from that GEMM on.  0 (default): every step in order
+                                 on the caller's stream; on the 30-qubit workload the side stream
+                                 measured 5 % slower (the GEMM beside it slows by more than the
+                                 preparation takes).  tn_profile_slices always runs in order. */
 } tn_plan_opts;
 
 typedef struct tn_plan tn_plan_t;

@@ -115,6 +115,7 @@ static int plan_upload(tn_plan_t* p) {
   if (tn::fault_alloc()) return fail(TN_ERR_OOM, "device allocation failed (injected: TN_FAULT_INJECT=alloc)");
   CUDA_TRY(cudaGetDevice(&p->device));
   CUDA_TRY(tn::prepare_gemm_tc());
+  CUDA_TRY(tn::prepare_permute());
   std::vector<float2> leaves(P.leaf_arena.size());
   for (size_t i = 0; i < leaves.size(); ++i)
     leaves[i] = make_float2((float)P.leaf_arena[i].real(), (float)P.leaf_arena[i].imag());
@@ -225,7 +226,7 @@ extern "C" int tn_plan(const tn_circuit* circuit, const tn_open_spec* open_spec,
     if (opts->host_fold_log2 > 16) return fail(TN_ERR_INVALID, "host_fold_log2 must be at most 16");
     if (opts->host_fold_log2 != 0) in.fold_log2 = opts->host_fold_log2 < 0 ? -1 : opts->host_fold_log2;
     in.gemm_pair = opts->gemm_pair < 0 ? -1 : 0;
-    in.side_bprep = opts->side_bprep >= 0;
+    in.side_bprep = opts->side_bprep > 0;
   }
   if (in.gemm_engine < 0 || in.gemm_engine > 4) return fail(TN_ERR_INVALID, "unknown gemm engine");
   if (in.cap_log2 > 34) return fail(TN_ERR_INVALID, "size cap above 2^34 elements");
@@ -1053,6 +1054,7 @@ extern "C" int tn_gemm_c64(int engine, const void* A, const void* B, void* C, in
   }
   cudaStream_t st = (cudaStream_t)stream;
   CUDA_TRY(tn::prepare_gemm_tc());   // kernel attributes (shared-memory size), as at plan upload
+  CUDA_TRY(tn::prepare_permute());
   // scratch: split A planes, prepared B, tables, scale slots
   const int64_t es = h16 ? 2 : 4;
   const int split = simt ? 0 : (h16 == 2 ? 3 : h16 == 1 ? 2 : 1);

@@ -116,7 +116,9 @@ cudaError_t launch_small(const SmallParams& p, cudaStream_t s) {
 // output's, through shared memory.  The tile is padded by one element per 32 so
 // that the strided reads of the write phase fall into different banks.  The
 // tile's base addresses (the remaining "rest" bits of the tile index scattered
-// to their positions) come from four 256-entry tables per direction.
+// to their positions) come from one 256-entry table per byte of the rest bits
+// and direction (only as many as n_rest needs, to keep shared memory small and
+// more blocks, hence more loads, in flight per SM).
 // SPLIT 1: the output is written as two fp32 planes, tf32-rounded hi and the
 // remainder lo; SPLIT 2: two bf16 planes, bf16 hi and the bf16-rounded
 // remainder; SPLIT 3: two fp16 planes of the value times the operand's power-
@@ -130,21 +132,43 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(r);
 }
 
+// Asynchronous 8-byte global -> shared copies (cp.async): the loads of the
+// next tiles land in shared memory without holding registers.
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Tile buffers of the permute: while one tile is written out, the next
+// kPermBufs - 1 are in flight.
+constexpr int kPermBufs = 3;
+
+__host__ __device__ inline int perm_levels(int n_rest) { return n_rest > 0 ? (n_rest + 7) >> 3 : 1; }
+__host__ __device__ inline int perm_tile_stride(int nt) { return nt + (nt >> 5) + 2; }   // float2 per buffer
+
 template <int SPLIT>
 __global__ void __launch_bounds__(256) k_permute(PermParams p) {
   extern __shared__ float2 tile[];
   const int nt = 1 << p.t;
-  uint32_t* s_in = (uint32_t*)(tile + pad32(nt) + 1);
+  const int tstride = perm_tile_stride(nt);
+  uint32_t* s_in = (uint32_t*)(tile + kPermBufs * tstride);
   uint32_t* s_out = s_in + nt;
   uint32_t* s_slot = s_out + nt;
-  uint64_t* r_in = (uint64_t*)(((uintptr_t)(s_slot + nt) + 7) & ~(uintptr_t)7);   // [4][256]
-  uint64_t* r_out = r_in + 1024;
+  const int levels = perm_levels(p.n_rest);
+  uint64_t* r_in = (uint64_t*)(((uintptr_t)(s_slot + nt) + 7) & ~(uintptr_t)7);   // [levels][256]
+  uint64_t* r_out = r_in + 256 * levels;
   for (int i = threadIdx.x; i < nt; i += blockDim.x) {
     s_in[i] = __ldg(p.tab + i);
     s_out[i] = __ldg(p.tab + nt + i);
     s_slot[i] = (uint32_t)pad32((int)__ldg(p.tab + 2 * nt + i));
   }
-  for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+  for (int e = threadIdx.x; e < 256 * levels; e += blockDim.x) {
     const int level = e >> 8, v = e & 255;
     uint64_t bi = 0, bo = 0;
     for (int k = 0; k < 8; ++k) {
@@ -157,56 +181,50 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
     r_in[e] = bi;
     r_out[e] = bo;
   }
-  __syncthreads();  // the tables are read below before the tile loop's own barrier
+  __syncthreads();  // the tables are read below
   const uint64_t nrest_mask = (1ULL << p.n_rest) - 1;
   const uint64_t total_tiles = (uint64_t)p.P << p.n_rest;
   float2* __restrict__ out_lo = p.out + p.P * p.pstride;
   const float sc = SPLIT == 3 ? pow2f(fp16_scale_exp(*p.scale)) : 1.0f;
-  // Software pipeline: the global loads of the next tile are issued into
-  // registers before the current tile is written out, so reads and writes of
-  // consecutive tiles overlap.  A tile has at most 1024 elements: <= 4 per thread.
-  auto tile_base = [&](uint64_t blk, const float2*& src, int64_t& dofs) {
+  // input and output base offsets of tile blk: the pattern's stride plus the
+  // rest bits of the tile index scattered through the per-byte tables
+  auto tile_base = [&](uint64_t blk, int64_t& iofs, int64_t& dofs) {
     const uint64_t pp = blk >> p.n_rest, b = blk & nrest_mask;
-    const uint64_t bi = r_in[b & 255] | r_in[256 + ((b >> 8) & 255)] | r_in[512 + ((b >> 16) & 255)] |
-                        r_in[768 + ((b >> 24) & 255)];
-    const uint64_t bo = r_out[b & 255] | r_out[256 + ((b >> 8) & 255)] | r_out[512 + ((b >> 16) & 255)] |
-                        r_out[768 + ((b >> 24) & 255)];
-    src = p.in + pp * p.pstride + bi;
+    uint64_t bi = 0, bo = 0;
+    for (int l = 0; l < levels; ++l) {
+      const int v = (int)((b >> (8 * l)) & 255);
+      bi |= r_in[256 * l + v];
+      bo |= r_out[256 * l + v];
+    }
+    iofs = (int64_t)(pp * p.pstride + bi);
     dofs = (int64_t)(pp * p.pstride + bo);
   };
-  float2 nxt[4];
-  uint64_t blk = blockIdx.x;
-  const float2* src = nullptr;
-  int64_t dofs = 0;
-  if (blk < total_tiles) {
-    tile_base(blk, src, dofs);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int i = threadIdx.x + c * 256;
-      if (i < nt) nxt[c] = __ldg(src + s_in[i]);
+  // issue the copies of tile blk into buffer buf (an empty group past the
+  // end keeps the group count uniform)
+  auto issue = [&](uint64_t blk, int buf) {
+    if (blk < total_tiles) {
+      int64_t iofs, dofs;
+      tile_base(blk, iofs, dofs);
+      const float2* src = p.in + iofs;
+      float2* dst = tile + buf * tstride;
+      for (int i = threadIdx.x; i < nt; i += blockDim.x) cp_async8(dst + pad32(i), src + s_in[i]);
     }
-  }
-  for (; blk < total_tiles; blk += gridDim.x) {
-    const int64_t cur_dofs = dofs;
-    __syncthreads();   // the previous tile's reads of `tile` are done
+    cp_async_commit();
+  };
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int i = threadIdx.x + c * 256;
-      if (i < nt) tile[pad32(i)] = nxt[c];
-    }
-    __syncthreads();
-    const uint64_t nb = blk + gridDim.x;
-    if (nb < total_tiles) {
-      tile_base(nb, src, dofs);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = threadIdx.x + c * 256;
-        if (i < nt) nxt[c] = __ldg(src + s_in[i]);
-      }
-    }
+  for (int k = 0; k < kPermBufs - 1; ++k) issue((uint64_t)blockIdx.x + (uint64_t)k * gridDim.x, k);
+  int buf = 0;
+  for (uint64_t blk = blockIdx.x; blk < total_tiles; blk += gridDim.x) {
+    cp_async_wait<kPermBufs - 2>();   // this thread's copies of tile blk are done
+    __syncthreads();                  // ... and everyone's; the buffer written out last round is free
+    issue(blk + (uint64_t)(kPermBufs - 1) * gridDim.x, (buf + kPermBufs - 1) % kPermBufs);
+    int64_t iofs, cur_dofs;
+    tile_base(blk, iofs, cur_dofs);
+    const float2* t = tile + buf * tstride;
+    buf = (buf + 1) % kPermBufs;
 #pragma unroll 4
     for (int j = threadIdx.x; j < nt; j += blockDim.x) {
-      const float2 v = tile[s_slot[j]];
+      const float2 v = t[s_slot[j]];
       const int64_t o = cur_dofs + s_out[j];
       if (SPLIT == 1) {
         const float2 h = make_float2(tf32_rn(v.x), tf32_rn(v.y));
@@ -232,6 +250,7 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
       }
     }
   }
+  cp_async_wait<0>();
 }
 
 // Scale slot of the FP16x3 engine: max over the operand of |re| and |im|.
@@ -262,13 +281,30 @@ cudaError_t launch_absmax(const AbsmaxParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Largest dynamic shared memory of a permute launch: kPermBufs tiles of 2^10
+// elements, the three 2^10-entry index tables and four levels of rest-bit
+// tables (about 54 KB), above the 48 KB a launch gets without opting in.
+static size_t perm_smem(int t, int n_rest) {
+  const int nt = 1 << t;
+  return sizeof(float2) * (size_t)kPermBufs * perm_tile_stride(nt) + 3 * sizeof(uint32_t) * (size_t)nt + 8 +
+         2 * 256 * (size_t)perm_levels(n_rest) * sizeof(uint64_t);
+}
+
+cudaError_t prepare_permute() {
+  const int mx = (int)perm_smem(10, 32);
+  cudaError_t e = cudaFuncSetAttribute(k_permute<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_permute<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_permute<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_permute<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return e;
+}
+
 cudaError_t launch_permute(const PermParams& p, cudaStream_t s) {
   if (p.n_rest > 32) return cudaErrorInvalidValue;
   const int64_t blocks = (1LL << p.n_rest) * p.P;
   const int64_t grid = std::min<int64_t>(blocks, (int64_t)kSMs * 8);
-  const int nt = 1 << p.t;
-  const size_t smem = sizeof(float2) * (size_t)(nt + (nt >> 5) + 2) + 3 * sizeof(uint32_t) * (size_t)nt + 8 +
-                      2 * 1024 * sizeof(uint64_t);
+  if (p.t < 0 || p.t > 10) return cudaErrorInvalidValue;
+  const size_t smem = perm_smem(p.t, p.n_rest);
   if (p.split == 1) k_permute<1><<<(unsigned)grid, 256, smem, s>>>(p);
   else if (p.split == 2) k_permute<2><<<(unsigned)grid, 256, smem, s>>>(p);
   else if (p.split == 3) k_permute<3><<<(unsigned)grid, 256, smem, s>>>(p);

@@ -101,6 +101,7 @@ cudaError_t launch_accum(const AccumParams& p, cudaStream_t s);
 // `status` receives a nonzero code if a bounded wait gave up.
 cudaError_t launch_gemm_tc(const GemmParams& p, unsigned int* status, cudaStream_t s);
 cudaError_t prepare_gemm_tc();   // kernel attributes; call before launching or capturing
+cudaError_t prepare_permute();   // the permute's opt-in shared-memory size; likewise
 
 // amplitude lookup: out[i] = H[g][mu] (c128 or c64); status <- min missing
 // index, or with seg_end (cumulative ends of n_seg merged requests, device)

@@ -1077,9 +1077,13 @@ static int layout_steps(Plan& plan, std::string& err) {
 // GEMM, which leaves HBM mostly idle.  A step qualifies when its operand was
 // written before that GEMM and its FP16 scale (if any) is a leaf's static
 // slot or the operand producer's epilogue maximum (not an ABSMAX step of its
-// own).  Its output buffer then starts at the fork, so nothing running
+// own), and it is large (at least 64 MiB) beside a long GEMM (at least 2^34
+// complex MACs).  Its output buffer then starts at the fork, so nothing running
 // between the fork and the consuming GEMM shares its memory; its operand is
 // live from its producer to the B-prep already.
+constexpr double kSideMinBytes = 64.0 * (1 << 20);   // B-prep algorithmic bytes
+constexpr double kSideMinMacs = 0x1p34;              // complex MACs of the GEMM it runs beside
+
 static void schedule_side_bprep(Plan& plan) {
   std::map<int, int> producer;   // workspace buffer id -> step that writes it
   const int n = (int)plan.steps.size();
@@ -1099,6 +1103,9 @@ static void schedule_side_bprep(Plan& plan) {
       int q = -1;
       for (int j = i - 1; ok && j > prod; --j)
         if (plan.steps[j].kind == ST_GEMM_TC) { q = j; break; }
+      // only a large preparation beside a long GEMM gains: each fork and join
+      // costs a dependency edge, and a short GEMM leaves nothing to hide under
+      if (q >= 0 && (x.bytes < kSideMinBytes || plan.steps[q].macs < kSideMinMacs)) q = -1;
       if (ok && q >= 0) {
         x.fork = q;
         plan.bufs[x.c.id].first = std::min(plan.bufs[x.c.id].first, q);

@@ -188,7 +188,7 @@ struct PlanInput {
   int auto_slice = 0;       // at most this many extra sliced edges when no order fits the cap
   int fold_log2 = 12;       // host folding of small contractions of host tensors (-1: off)
   int gemm_pair = 0;        // 0: CTA-pair GEMM tiles where they apply; -1: one-CTA tiles only
-  bool side_bprep = true;   // B-prep steps whose operand is ready run beside the previous GEMM
+  bool side_bprep = false;  // B-prep steps whose operand is ready run beside the previous GEMM
 };
 
 int build_plan(const PlanInput& in, Plan& plan, std::string& err);
