@@ -219,12 +219,16 @@ def run_ours(args):
     if ws > 1:
         # every rank contracts with rank 0's plan: its order goes to the others
         import torch.distributed as dist
-        box = [(tn.tn_plan_order(plan).tolist(), tn.tn_plan_get_stats(plan)["gemm_pair"]) if rank == 0 else None]
+        # (with its CTA-pair choice and the tile variant the step tuner chose for each step)
+        box = [(tn.tn_plan_order(plan).tolist(), tn.tn_plan_get_stats(plan)["gemm_pair"],
+                [s["variant"] for s in tn.tn_plan_describe(plan)["steps"]]) if rank == 0 else None]
         dist.broadcast_object_list(box, src=0)
         if rank != 0:
             plan = tn.tn_plan(cfg["circuit"], cfg["open_qubits"], cfg["tails"], cfg["edges"], gemm=gemm,
                               order=np.array(box[0][0], dtype=np.int32).reshape(-1, 2), gemm_pair=box[0][1],
                               **popts)
+            for i, v in enumerate(box[0][2]):
+                tn.tn_plan_set_step_variant(plan, i, v)
     plan_s = time.time() - t0
     st = tn.tn_plan_get_stats(plan)
     k = st["n_sliced"]
@@ -414,6 +418,9 @@ def run_ours(args):
                              "launches with CUDA events around each (tn_profile_slices)",
                 "plan_seconds": round(plan_s, 2), "order_trials": trials,
                 "autotune_candidates": st["autotune_candidates"], "rank0_slices": [b0, e0_],
+                "step_tuning": {"steps_off_default": int(st["n_tuned_steps"]),
+                                "slice_ms_default_variants": round(st["tune_default_ms"], 3),
+                                "slice_ms_tuned_variants": round(st["tune_tuned_ms"], 3)},
                 "gemm_tiles": "CTA pairs (cta_group::2, 256x256) where they apply" if st["gemm_pair"] == 0 and
                               args.engine in ("fp16", "bf16") else "one-CTA 128-row tiles",
                 "partial_slices_for_profiling": bool(args.slices) and "kept" not in cfg},

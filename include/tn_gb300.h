@@ -118,6 +118,10 @@ typedef struct {
                                  on the caller's stream; on the 30-qubit workload the side stream
                                  measured 5 % slower (the GEMM beside it slows by more than the
                                  preparation takes).  tn_profile_slices always runs in order. */
+  int    tune_steps;          /* tn_plan_autotune only.  0: after choosing the order, tune every
+                                 step's tile variant (tn_plan_tune_steps, 3 repetitions) when a
+                                 slice takes at most 1 s; > 0: tune with this many repetitions
+                                 whatever the slice time; -1: do not tune steps. */
 } tn_plan_opts;
 
 typedef struct tn_plan tn_plan_t;
@@ -144,6 +148,9 @@ typedef struct {
                                  all 2^n_internal_sliced passes of one user slice */
   int     gemm_pair;          /* the plan's tn_plan_opts.gemm_pair (as chosen by tn_plan_autotune) */
   int     n_side_bprep;       /* B-preparation steps that run beside an earlier GEMM (side_bprep) */
+  int     n_tuned_steps;      /* steps whose chosen tile variant is not the default (0: untuned) */
+  double  tune_default_ms;    /* tn_plan_tune_steps: one slice with the variants it started from */
+  double  tune_tuned_ms;      /* ... and with the variants it chose (the faster set is kept) */
 } tn_plan_stats;
 
 /* Plan the contraction (host).  `order`: n_pairs pairs (i, j) of leaf ids, the
@@ -167,6 +174,36 @@ int tn_plan_autotune(const tn_circuit* circuit, const tn_open_spec* open_spec,
                      const tn_edge* sliced_edges, int n_edges, const tn_plan_opts* opts,
                      int n_candidates, void* stream, tn_plan_t** out);
 int  tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* out);
+
+/* Per-step tile variants (the batched form's tuner of tile shapes and permute
+ * schedules; the paper tunes nothing of this kind: its steps are PyTorch
+ * calls, Results, implementation paragraph).  Every variant of a step computes
+ * the same result; they differ only in how the kernel is tiled:
+ *   tensor-core GEMM step: variant j picks the widest tile (real columns) and
+ *     whether 256 x 256 CTA-pair tiles may be used, from (256, pairs),
+ *     (256, one CTA), (128), (64), (32), keeping only choices that launch
+ *     differently for this step's shape (fold of patterns side by side
+ *     included); variant 0 is the default rule;
+ *   permute step of >= 2^20 elements: tile schedules (input-run bits,
+ *     output-run bits, tile bits) = (5, 5, 10) [default], (4, 6, 10),
+ *     (6, 4, 10), (5, 5, 9), (4, 4, 8), duplicates removed;
+ *   every other step: one variant.
+ * tn_plan_step_variants gives step i's variant count and current choice
+ * (steps as in tn_plan_step_info).  tn_plan_set_step_variant chooses one; it
+ * drops the plan's captured graphs (they replay the old launches).  Errors:
+ * TN_ERR_INVALID for a bad plan, step or variant. */
+int  tn_plan_step_variants(const tn_plan_t* plan, int64_t i, int* n_variants, int* chosen);
+int  tn_plan_set_step_variant(tn_plan_t* plan, int64_t i, int variant);
+/* Tuner: times every variant of every step on the current device (one pass of
+ * slice 0 per variant set, per-launch CUDA events on `stream`, in order, the
+ * fastest of `reps` >= 1 repetitions after one untimed pass; variant v of
+ * every step is timed in the same pass), chooses each step's fastest, then
+ * times whole slices with the starting and the chosen variants (alternating,
+ * best of `reps`) and keeps the faster set.  *default_ms / *tuned_ms (may be
+ * NULL) receive those two slice times.  Synchronous; allocates a scratch
+ * head; the plan's heads are not touched.  Errors: TN_ERR_INVALID for a
+ * host-only plan, TN_ERR_CUDA, TN_ERR_TIMEOUT if a bounded wait gave up. */
+int  tn_plan_tune_steps(tn_plan_t* plan, int reps, void* stream, double* default_ms, double* tuned_ms);
 /* Copies up to `cap` pairs of the order used into pairs[2*i], pairs[2*i+1];
  * *n_pairs receives the full count. */
 int  tn_plan_order(const tn_plan_t* plan, int32_t* pairs, int64_t cap, int64_t* n_pairs);

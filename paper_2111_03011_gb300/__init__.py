@@ -57,7 +57,7 @@ class tn_plan_opts(C.Structure):
     _fields_ = [("max_log2_elements", C.c_double), ("gemm", C.c_int), ("host_only", C.c_int),
                 ("order_trials", C.c_int), ("order_seed", C.c_uint64), ("max_host_absorb_log2", C.c_int),
                 ("small_max_bits", C.c_int), ("auto_slice", C.c_int), ("host_fold_log2", C.c_int),
-                ("gemm_pair", C.c_int), ("side_bprep", C.c_int)]
+                ("gemm_pair", C.c_int), ("side_bprep", C.c_int), ("tune_steps", C.c_int)]
 
 
 class tn_server_opts(C.Structure):
@@ -91,7 +91,8 @@ class tn_plan_stats(C.Structure):
                 ("max_log2_elements", C.c_double), ("workspace_bytes", C.c_int64),
                 ("n_gemm_tc", C.c_int), ("n_gemm_simt", C.c_int), ("n_small", C.c_int), ("n_permute", C.c_int),
                 ("measured_slice_ms", C.c_double), ("autotune_candidates", C.c_int),
-                ("n_internal_sliced", C.c_int), ("gemm_pair", C.c_int), ("n_side_bprep", C.c_int)]
+                ("n_internal_sliced", C.c_int), ("gemm_pair", C.c_int), ("n_side_bprep", C.c_int),
+                ("n_tuned_steps", C.c_int), ("tune_default_ms", C.c_double), ("tune_tuned_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -139,6 +140,9 @@ def _load():
     lib.tn_sample_ex.argtypes = [vp, i64, C.c_double, C.c_uint64, C.c_int, i64, vp, vp]
     lib.tn_profile_slices.argtypes = [vp, tn_range, vp, vp, C.POINTER(C.c_double), i64]
     lib.tn_plan_step_info.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.tn_plan_step_variants.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.tn_plan_set_step_variant.argtypes = [vp, i64, C.c_int]
+    lib.tn_plan_tune_steps.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.tn_head_norm_noalloc.argtypes = [vp, i64, C.c_int, vp, vp]
     lib.tn_xeb.argtypes = [vp, vp, i64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.tn_gemm_c64.argtypes = [C.c_int, vp, vp, vp, i64, i64, i64, i64, i64, i64, i32p, i32p, C.c_int, vp]
@@ -146,7 +150,8 @@ def _load():
     lib.tn_version.restype = C.c_char_p
     for name in ("tn_plan", "tn_plan_autotune", "tn_plan_get_stats", "tn_plan_order", "tn_head_create", "tn_head_fidelity",
                  "tn_head_set_fidelity", "tn_contract_slices", "tn_amplitudes", "tn_sample", "tn_head_norm",
-                 "tn_profile_slices", "tn_plan_step_info", "tn_head_reset", "tn_head_norm_noalloc", "tn_sample_ex",
+                 "tn_profile_slices", "tn_plan_step_info", "tn_plan_step_variants", "tn_plan_set_step_variant",
+                 "tn_plan_tune_steps", "tn_head_reset", "tn_head_norm_noalloc", "tn_sample_ex",
                  "tn_contract_slices_graph", "tn_contract_batch", "tn_server_create", "tn_server_add_circuit",
                  "tn_server_submit", "tn_server_wait", "tn_server_get_stats"):
         getattr(lib, name).restype = C.c_int
@@ -159,7 +164,8 @@ lib = _lib
 EXPORTED = ["tn_plan", "tn_plan_autotune", "tn_plan_free", "tn_plan_get_stats", "tn_plan_order", "tn_plan_describe",
             "tn_head_create", "tn_head_free", "tn_head_data", "tn_head_reset", "tn_head_fidelity", "tn_head_set_fidelity",
             "tn_contract_slices", "tn_contract_slices_graph", "tn_contract_batch", "tn_amplitudes", "tn_sample", "tn_sample_ex", "tn_head_norm", "tn_profile_slices",
-            "tn_plan_step_info", "tn_head_norm_noalloc", "tn_server_create", "tn_server_add_circuit",
+            "tn_plan_step_info", "tn_plan_step_variants", "tn_plan_set_step_variant", "tn_plan_tune_steps",
+            "tn_head_norm_noalloc", "tn_server_create", "tn_server_add_circuit",
             "tn_server_submit", "tn_server_wait", "tn_server_get_stats", "tn_server_free", "tn_last_error",
             "tn_gemm_c64", "tn_xeb", "tn_version"]
 
@@ -246,7 +252,7 @@ def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements
         ed[i] = tn_edge(int(g), int(leg), int(kind), int(val))
     opts = tn_plan_opts(float(max_log2_elements), int(gemm), int(bool(host_only)), int(order_trials),
                         int(order_seed), int(max_host_absorb_log2), int(small_max_bits), int(auto_slice),
-                        int(host_fold_log2), int(gemm_pair), int(side_bprep))
+                        int(host_fold_log2), int(gemm_pair), int(side_bprep), 0)
     h = C.c_void_p()
     if order is not None:
         o = np.ascontiguousarray(np.asarray(order, dtype=np.int32).reshape(-1))
@@ -259,7 +265,8 @@ def tn_plan(circuit, open_qubits, tails, edges=(), order=None, max_log2_elements
 
 def tn_plan_autotune(circuit, open_qubits, tails, edges=(), n_candidates=4, max_log2_elements=0.0,
                      gemm=TN_GEMM_AUTO, order_trials=0, order_seed=0, max_host_absorb_log2=0, small_max_bits=0,
-                     stream=None, auto_slice=0, host_fold_log2=0, gemm_pair=0, side_bprep=0) -> Plan:
+                     stream=None, auto_slice=0, host_fold_log2=0, gemm_pair=0, side_bprep=0,
+                     tune_steps=0) -> Plan:
     gates = gates_to_c(circuit)
     circ = tn_circuit(int(circuit.n_qubits), len(circuit.gates), gates)
     oq = (C.c_int * max(1, len(open_qubits)))(*[int(q) for q in open_qubits])
@@ -271,7 +278,7 @@ def tn_plan_autotune(circuit, open_qubits, tails, edges=(), n_candidates=4, max_
         ed[i] = tn_edge(int(g), int(leg), int(kind), int(val))
     opts = tn_plan_opts(float(max_log2_elements), int(gemm), 0, int(order_trials), int(order_seed),
                         int(max_host_absorb_log2), int(small_max_bits), int(auto_slice), int(host_fold_log2),
-                        int(gemm_pair), int(side_bprep))
+                        int(gemm_pair), int(side_bprep), int(tune_steps))
     h = C.c_void_p()
     _check(_lib.tn_plan_autotune(C.byref(circ), C.byref(spec), ed, len(edges), C.byref(opts), int(n_candidates),
                                  _stream(stream), C.byref(h)))
@@ -282,6 +289,24 @@ def tn_plan_get_stats(plan: Plan) -> dict:
     s = tn_plan_stats()
     _check(_lib.tn_plan_get_stats(plan.handle, C.byref(s)))
     return s.as_dict()
+
+
+def tn_plan_step_variants(plan: Plan, i: int):
+    """(number of tile variants of step i, the chosen one)."""
+    n, c = C.c_int(), C.c_int()
+    _check(_lib.tn_plan_step_variants(plan.handle, int(i), C.byref(n), C.byref(c)))
+    return n.value, c.value
+
+
+def tn_plan_set_step_variant(plan: Plan, i: int, variant: int) -> None:
+    _check(_lib.tn_plan_set_step_variant(plan.handle, int(i), int(variant)))
+
+
+def tn_plan_tune_steps(plan: Plan, reps=3, stream=None):
+    """Tune every step's tile variant; returns (slice ms before, slice ms with the chosen variants)."""
+    a, b = C.c_double(), C.c_double()
+    _check(_lib.tn_plan_tune_steps(plan.handle, int(reps), _stream(stream), C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def tn_plan_order(plan: Plan) -> np.ndarray:

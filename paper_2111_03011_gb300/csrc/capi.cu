@@ -271,7 +271,10 @@ extern "C" int tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* s) {
   s->workspace_bytes = P.workspace_bytes;
   s->measured_slice_ms = plan->measured_slice_ms;
   s->autotune_candidates = plan->autotune_candidates;
+  s->tune_default_ms = plan->tune_default_ms;
+  s->tune_tuned_ms = plan->tune_tuned_ms;
   for (auto& st : P.steps) {
+    if (st.variant != 0) ++s->n_tuned_steps;
     if (st.kind == tn::ST_GEMM_TC) ++s->n_gemm_tc;
     if (st.kind == tn::ST_GEMM_SIMT) ++s->n_gemm_simt;
     if (st.kind == tn::ST_SMALL) ++s->n_small;
@@ -479,7 +482,8 @@ static cudaError_t launch_step(tn_plan_t* p, const tn::Step& x, int64_t s, cudaS
       gp.scaleA = scale_ptr(p, x.slot);
       gp.scaleB = scale_ptr(p, x.slotB);
       gp.amax = scale_ptr(p, x.max_slot);
-      gp.pair = P.gemm_pair;
+      gp.pair = P.gemm_pair < 0 ? -1 : x.pair;
+      gp.tile_cap = x.tile_cap;
       e = x.kind == tn::ST_GEMM_SIMT ? tn::launch_gemm_simt(gp, st) : tn::launch_gemm_tc(gp, p->d_status, st);
       break;
     }
@@ -672,6 +676,197 @@ extern "C" int tn_plan_step_info(const tn_plan_t* plan, int64_t i, int* kind, do
   if (kind) *kind = x.kind;
   if (macs) *macs = x.macs;
   if (bytes) *bytes = x.bytes;
+  return TN_OK;
+}
+
+// ------------------------------------------------ per-step tile variants
+
+namespace {
+
+struct GemmVariant {
+  int cap, pair;
+};
+// widest tile (real columns) and CTA pairs allowed (0) or not (-1)
+constexpr GemmVariant kGemmVariants[] = {{256, 0}, {256, -1}, {128, 0}, {64, 0}, {32, 0}};
+constexpr int kNumGemmVariants = (int)(sizeof(kGemmVariants) / sizeof(kGemmVariants[0]));
+
+// Indices into kGemmVariants of the choices that launch differently for the
+// shape of tensor-core GEMM step x (independent of the plan-wide pair flag,
+// so that a step's variant numbers never change).
+std::vector<int> gemm_variants(const tn::Step& x) {
+  std::vector<int> out;
+  std::vector<tn::GemmTile> seen;
+  for (int v = 0; v < kNumGemmVariants; ++v) {
+    tn::GemmParams gp;
+    gp.M = 1LL << x.nm;
+    gp.N = 1LL << x.nn;
+    gp.K = 1LL << x.nk;
+    gp.PC = x.PC;
+    gp.mapA_mode = x.mapA_mode;
+    gp.h16 = x.h16;
+    gp.pair = kGemmVariants[v].pair;
+    gp.tile_cap = kGemmVariants[v].cap;
+    const tn::GemmTile t = tn::gemm_tc_tile(gp);
+    bool dup = false;
+    for (const tn::GemmTile& q : seen) dup |= q.bn == t.bn && q.fold == t.fold && q.paired == t.paired;
+    if (!dup) {
+      seen.push_back(t);
+      out.push_back(v);
+    }
+  }
+  return out;
+}
+
+int step_variant_count(const tn::Step& x) {
+  if (x.kind == tn::ST_GEMM_TC) return (int)gemm_variants(x).size();
+  if (x.kind == tn::ST_PERMUTE) return std::max<int>(1, (int)x.alts.size());
+  return 1;
+}
+
+void apply_step_variant(tn::Step& x, int v) {
+  x.variant = v;
+  if (x.kind == tn::ST_GEMM_TC) {
+    const GemmVariant& g = kGemmVariants[gemm_variants(x)[(size_t)v]];
+    x.tile_cap = g.cap;
+    x.pair = g.pair;
+  } else if (x.kind == tn::ST_PERMUTE && !x.alts.empty()) {
+    tn::apply_perm_schedule(x, x.alts[(size_t)v]);
+  }
+}
+
+// Captured graphs replay the launches they recorded: drop them, and give the
+// plan a new serial so that the batch graph cache (keyed on it) misses too.
+void drop_graphs(tn_plan_t* p) {
+  for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+  p->graphs.clear();
+  p->serial = tn::next_serial();
+}
+
+}  // namespace
+
+extern "C" int tn_plan_step_variants(const tn_plan_t* plan, int64_t i, int* n_variants, int* chosen) {
+  if (!plan) return fail(TN_ERR_INVALID, "NULL plan");
+  if (i < 0 || i >= (int64_t)plan->P.steps.size()) return fail(TN_ERR_INVALID, "step index out of range");
+  const tn::Step& x = plan->P.steps[(size_t)i];
+  if (n_variants) *n_variants = step_variant_count(x);
+  if (chosen) *chosen = x.variant;
+  return TN_OK;
+}
+
+extern "C" int tn_plan_set_step_variant(tn_plan_t* plan, int64_t i, int variant) {
+  if (!plan) return fail(TN_ERR_INVALID, "NULL plan");
+  if (i < 0 || i >= (int64_t)plan->P.steps.size()) return fail(TN_ERR_INVALID, "step index out of range");
+  tn::Step& x = plan->P.steps[(size_t)i];
+  if (variant < 0 || variant >= step_variant_count(x)) return fail(TN_ERR_INVALID, "variant out of range");
+  if (x.variant != variant) {
+    apply_step_variant(x, variant);
+    drop_graphs(plan);
+  }
+  return TN_OK;
+}
+
+extern "C" int tn_plan_tune_steps(tn_plan_t* plan, int reps, void* stream, double* default_ms, double* tuned_ms) {
+  if (!plan) return fail(TN_ERR_INVALID, "NULL plan");
+  if (!plan->on_device) return fail(TN_ERR_INVALID, "plan was made host_only");
+  if (reps < 1 || reps > 64) return fail(TN_ERR_INVALID, "reps must be in [1, 64]");
+  tn::Plan& P = plan->P;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ns = (int64_t)P.steps.size();
+  std::vector<int> start(ns), count(ns);
+  int max_v = 1;
+  for (int64_t i = 0; i < ns; ++i) {
+    start[i] = P.steps[i].variant;
+    count[i] = step_variant_count(P.steps[i]);
+    max_v = std::max(max_v, count[i]);
+  }
+  tn_head_t* h = nullptr;
+  int rc = tn_head_create(plan, nullptr, &h);
+  if (rc) return rc;
+  auto& ev = plan->prof_events;
+  while (ev.size() < (size_t)(2 * (ns + 1))) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      tn_head_free(h);
+      return fail(TN_ERR_CUDA, "event creation failed");
+    }
+    ev.push_back(e);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    tn_head_free(h);
+    return fail(TN_ERR_CUDA, "event creation failed");
+  }
+  auto set_all = [&](const std::vector<int>& v) {
+    for (int64_t i = 0; i < ns; ++i)
+      if (P.steps[i].variant != v[i]) apply_step_variant(P.steps[i], v[i]);
+  };
+  // 1. per-step times of variant v of every step (v past a step's count: its default)
+  std::vector<double> best_ms(ns, 1e300);
+  std::vector<int> best_v(start);
+  for (int v = 0; v < max_v && rc == TN_OK; ++v) {
+    std::vector<int> cur(ns);
+    for (int64_t i = 0; i < ns; ++i) cur[i] = v < count[i] ? v : 0;
+    set_all(cur);
+    for (int r = 0; r <= reps && rc == TN_OK; ++r) {
+      rc = run_pass(plan, 0, h->H, st, ev.data());
+      if (rc) break;
+      const cudaError_t e = cudaEventSynchronize(ev[(size_t)(2 * ns + 1)]);
+      if (e != cudaSuccess) {
+        rc = fail(TN_ERR_CUDA, std::string("tuning pass: ") + cudaGetErrorString(e));
+        break;
+      }
+      if (r == 0) continue;   // untimed
+      for (int64_t i = 0; i < ns; ++i) {
+        if (v >= count[i]) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[(size_t)(2 * i)], ev[(size_t)(2 * i + 1)]);
+        if (ms < best_ms[i]) {
+          best_ms[i] = ms;
+          best_v[i] = v;
+        }
+      }
+    }
+  }
+  // 2. whole slices (the plan's own execution path), starting set against the
+  // chosen one, alternating
+  double t_start = 1e300, t_best = 1e300;
+  for (int r = 0; r <= reps && rc == TN_OK; ++r)
+    for (int which = 0; which < 2 && rc == TN_OK; ++which) {
+      set_all(which == 0 ? start : best_v);
+      cudaEventRecord(e0, st);
+      rc = run_slice(plan, 0, h->H, st);
+      cudaEventRecord(e1, st);
+      if (rc) break;
+      const cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        rc = fail(TN_ERR_CUDA, std::string("tuning slice: ") + cudaGetErrorString(e));
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r == 0) continue;   // untimed
+      double& t = which == 0 ? t_start : t_best;
+      t = std::min(t, (double)ms);
+    }
+  unsigned int word = 0;
+  if (rc == TN_OK && cudaMemcpy(&word, plan->d_status, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = fail(TN_ERR_CUDA, "status read-back failed");
+  if (rc == TN_OK && word) {
+    cudaMemset(plan->d_status, 0, sizeof(word));
+    rc = fail(TN_ERR_TIMEOUT, "a bounded device wait gave up while tuning (status " + std::to_string(word) + ")");
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tn_head_free(h);
+  const bool keep = rc == TN_OK && t_best < t_start;
+  set_all(keep ? best_v : start);
+  drop_graphs(plan);
+  if (rc) return rc;
+  plan->tune_default_ms = t_start;
+  plan->tune_tuned_ms = t_best;
+  if (default_ms) *default_ms = t_start;
+  if (tuned_ms) *tuned_ms = t_best;
   return TN_OK;
 }
 
@@ -1240,6 +1435,15 @@ extern "C" int tn_plan_autotune(const tn_circuit* circuit, const tn_open_spec* o
   if (!best) return last_rc ? last_rc : fail(TN_ERR_OOM, "no candidate plan could be built");
   best->measured_slice_ms = best_ms;
   best->autotune_candidates = distinct;
+  if (o.tune_steps > 0 || (o.tune_steps == 0 && best_ms <= 1000.0)) {
+    double t0 = 0, t1 = 0;
+    const int rc = tn_plan_tune_steps(best, o.tune_steps > 0 ? o.tune_steps : 3, stream, &t0, &t1);
+    if (rc) {
+      tn_plan_free(best);
+      return rc;
+    }
+    best->measured_slice_ms = std::min(t0, t1);
+  }
   *out = best;
   return TN_OK;
 }

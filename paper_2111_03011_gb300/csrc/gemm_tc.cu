@@ -45,6 +45,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -936,27 +937,45 @@ static cudaError_t run_pair(const GemmParams& p, int fold, unsigned int* status,
   return cudaGetLastError();
 }
 
-// Tile width: the smallest of 16..256 that covers 2N, or, when all patterns
-// share A and 2N >= 16, up to 256 columns of consecutive patterns folded side
-// by side (fold = BN / 2N, as many as the pattern count rounded up to a power
-// of two allows).
-template <int FMT>
-static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStream_t s) {
+}  // namespace tc
+
+// Tile width: the smallest of 16..cap (cap = p.tile_cap, a power of two in
+// 16..256; 256 by default) that covers 2N, or, when all patterns share A and
+// 2N >= 16, up to cap columns of consecutive patterns folded side by side
+// (fold = BN / 2N, as many as the pattern count rounded up to a power of two
+// allows).  256-wide 16-bit tiles with at least 256 rows run on CTA pairs
+// unless p.pair < 0.
+GemmTile gemm_tc_tile(const GemmParams& p) {
+  int cap = 16;
+  while (cap < 256 && cap < p.tile_cap) cap *= 2;
   const int64_t N2 = 2 * p.N;
   int64_t w = N2;
   int fold = 1;
-  if (p.mapA_mode == 1 && p.PC > 1 && N2 >= 16 && N2 < 256) {
-    while (w < 256 && fold < p.PC) {
+  if (p.mapA_mode == 1 && p.PC > 1 && N2 >= 16 && N2 < cap) {
+    while (w < cap && fold < p.PC) {
       w *= 2;
       fold *= 2;
     }
   }
-  if (w <= 16) return run<16, kb_stages(16, kb_bytes(16, FMT)), FMT>(p, fold, status, s);
-  if (w <= 32) return run<32, kb_stages(32, kb_bytes(32, FMT)), FMT>(p, fold, status, s);
-  if (w <= 64) return run<64, kb_stages(64, kb_bytes(64, FMT)), FMT>(p, fold, status, s);
-  if (w <= 128) return run<128, kb_stages(128, kb_bytes(128, FMT)), FMT>(p, fold, status, s);
-  // 256-wide 16-bit tiles with at least 256 rows run on CTA pairs
-  if (FMT != 0 && p.M >= 2 * BM && p.pair >= 0) return run_pair<FMT == 0 ? 1 : FMT>(p, fold, status, s);
+  GemmTile t;
+  t.bn = 16;
+  while (t.bn < 256 && t.bn < std::min<int64_t>(w, cap)) t.bn *= 2;
+  t.fold = fold;
+  t.paired = p.h16 != 0 && t.bn == 256 && p.M >= 2 * tc::BM && p.pair >= 0;
+  return t;
+}
+
+namespace tc {
+
+template <int FMT>
+static cudaError_t dispatch(const GemmParams& p, unsigned int* status, cudaStream_t s) {
+  const GemmTile t = gemm_tc_tile(p);
+  const int fold = t.fold;
+  if (t.bn == 16) return run<16, kb_stages(16, kb_bytes(16, FMT)), FMT>(p, fold, status, s);
+  if (t.bn == 32) return run<32, kb_stages(32, kb_bytes(32, FMT)), FMT>(p, fold, status, s);
+  if (t.bn == 64) return run<64, kb_stages(64, kb_bytes(64, FMT)), FMT>(p, fold, status, s);
+  if (t.bn == 128) return run<128, kb_stages(128, kb_bytes(128, FMT)), FMT>(p, fold, status, s);
+  if (t.paired) return run_pair<FMT == 0 ? 1 : FMT>(p, fold, status, s);
   return run<256, kb_stages(256, kb_bytes(256, FMT)), FMT>(p, fold, status, s);
 }
 

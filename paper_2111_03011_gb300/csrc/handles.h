@@ -35,6 +35,7 @@ struct tn_plan {
   tn::Plan P;
   double measured_slice_ms = 0.0;
   int autotune_candidates = 0;
+  double tune_default_ms = 0.0, tune_tuned_ms = 0.0;   // tn_plan_tune_steps: slice times before / after
   std::vector<GraphEntry> graphs;     // captured slice ranges (tn_contract_slices_graph)
   std::vector<cudaEvent_t> prof_events;   // tn_profile_slices: reused timing events
   // side stream of the B-prep steps that run beside an earlier GEMM

@@ -78,7 +78,16 @@ struct GemmParams {
   const unsigned int* scaleA; const unsigned int* scaleB;   // h16 == 2: the operands' scale slots
   unsigned int* amax;    // non-null: atomicMax of the output's max |re|, |im| (fp32 bits)
   int pair = 0;          // 0: CTA-pair 256 x 256 tiles where they apply (16-bit, M >= 256); -1: one-CTA tiles
+  int tile_cap = 256;    // widest tile the dispatch may pick, real columns (16..256)
 };
+
+// Tile a tensor-core GEMM launch runs with: BN real columns per tile, fold
+// patterns side by side in one tile, on CTA pairs or not.
+struct GemmTile {
+  int bn = 256, fold = 1;
+  bool paired = false;
+};
+GemmTile gemm_tc_tile(const GemmParams& p);
 
 struct AccumParams {
   const float2* F; double2* H;

@@ -816,27 +816,20 @@ static void add_absmax(Plan& plan, const VTensor& X, int slot, int ci) {
   plan.steps.push_back(s);
 }
 
-static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& target, Ref out, int ci,
-                        int split) {
-  Step s;
-  s.kind = ST_PERMUTE;
-  s.split = split;
-  s.a = X.ref;
-  s.c = out;
-  s.contraction = ci;
-  const int r = (int)X.legs.size();
-  s.rA = s.rC = r;
-  s.PA = s.PC = X.P;
-  std::vector<int> in_pos(r), inv(r);  // in_pos[o] = input position of output position o
-  for (int o = 0; o < r; ++o) in_pos[o] = find_pos(X.legs, target[o]);
-  for (int o = 0; o < r; ++o) inv[in_pos[o]] = o;
-  const int a = std::min(r, 5), bq = std::min(r, 5);
+// One tile schedule of a permute: the tile's input bits are the `a` lowest
+// input positions and the input positions of the `bq` lowest output
+// positions, grown with further low input bits up to `tmax` bits (longer
+// contiguous runs, fewer tiles); the remaining bits index the tiles.
+static PermSched perm_schedule(Plan& plan, const std::vector<int>& in_pos, const std::vector<int>& inv, int a,
+                               int bq, int tmax) {
+  const int r = (int)in_pos.size();
+  a = std::min(r, a);
+  bq = std::min(r, bq);
   std::vector<int> Tin;
   for (int x = 0; x < a; ++x) Tin.push_back(x);
   for (int o = 0; o < bq; ++o)
     if (std::find(Tin.begin(), Tin.end(), in_pos[o]) == Tin.end()) Tin.push_back(in_pos[o]);
-  // grow small tiles with further input bits (longer contiguous runs, fewer tiles)
-  for (int x = 0; x < r && (int)Tin.size() < 10; ++x)
+  for (int x = 0; x < r && (int)Tin.size() < tmax; ++x)
     if (std::find(Tin.begin(), Tin.end(), x) == Tin.end()) Tin.push_back(x);
   std::sort(Tin.begin(), Tin.end());
   const int t = (int)Tin.size();
@@ -859,15 +852,60 @@ static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& ta
     tab[nt + i] = oo;
     tab[2 * nt + i] = sl;
   }
-  s.t_bits = t;
-  s.tab_off = meta_push(plan, tab);
-  s.n_rest = 0;
+  PermSched ps;
+  ps.t_bits = t;
+  ps.tab_off = meta_push(plan, tab);
+  ps.n_rest = 0;
   for (int x = 0; x < r; ++x)
     if (std::find(Tin.begin(), Tin.end(), x) == Tin.end()) {
-      s.rest_in[s.n_rest] = (uint8_t)x;
-      s.rest_out[s.n_rest] = (uint8_t)inv[x];
-      ++s.n_rest;
+      ps.rest_in[ps.n_rest] = (uint8_t)x;
+      ps.rest_out[ps.n_rest] = (uint8_t)inv[x];
+      ++ps.n_rest;
     }
+  return ps;
+}
+
+void apply_perm_schedule(Step& s, const PermSched& ps) {
+  s.t_bits = ps.t_bits;
+  s.tab_off = ps.tab_off;
+  s.n_rest = ps.n_rest;
+  std::memcpy(s.rest_in, ps.rest_in, sizeof(s.rest_in));
+  std::memcpy(s.rest_out, ps.rest_out, sizeof(s.rest_out));
+}
+
+static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& target, Ref out, int ci,
+                        int split) {
+  Step s;
+  s.kind = ST_PERMUTE;
+  s.split = split;
+  s.a = X.ref;
+  s.c = out;
+  s.contraction = ci;
+  const int r = (int)X.legs.size();
+  s.rA = s.rC = r;
+  s.PA = s.PC = X.P;
+  std::vector<int> in_pos(r), inv(r);  // in_pos[o] = input position of output position o
+  for (int o = 0; o < r; ++o) in_pos[o] = find_pos(X.legs, target[o]);
+  for (int o = 0; o < r; ++o) inv[in_pos[o]] = o;
+  // schedule 0 (the default): 32-element runs on both sides, 2^10-element
+  // tiles.  Permutes of at least 2^20 elements also get the alternatives
+  // that a plan tuner may time: wider input or output runs, smaller tiles
+  // (more resident blocks per SM).
+  static const int kSched[][3] = {{5, 5, 10}, {4, 6, 10}, {6, 4, 10}, {5, 5, 9}, {4, 4, 8}};
+  const int n_sched = (int64_t)X.P << r >= (1LL << 20) ? 5 : 1;
+  for (int v = 0; v < n_sched; ++v) {
+    PermSched ps = perm_schedule(plan, in_pos, inv, kSched[v][0], kSched[v][1], kSched[v][2]);
+    bool dup = false;
+    for (const PermSched& q : s.alts)
+      dup |= q.t_bits == ps.t_bits && q.n_rest == ps.n_rest &&
+             std::memcmp(q.rest_in, ps.rest_in, sizeof(ps.rest_in)) == 0;
+    if (dup) {
+      plan.meta.resize((size_t)ps.tab_off);   // the table just pushed is not needed
+      continue;
+    }
+    s.alts.push_back(ps);
+  }
+  apply_perm_schedule(s, s.alts[0]);
   s.bytes = (split == 1 ? 24.0 : 16.0) * (double)vt_elems(X);
   plan.steps.push_back(s);
 }
@@ -1540,7 +1578,18 @@ std::string describe_plan(const Plan& plan, bool with_data) {
     o << "],\"boffN\":[";
     for (int v = 0; v < 16; ++v) o << (v ? "," : "") << st.boffN[v];
     o << "],\"mapA\":[" << st.mapA_mode << "," << st.mapA_off << "],\"mapB\":[" << st.mapB_mode << ","
-      << st.mapB_off << "],\"bk_off\":" << st.bk_off << ",\"bn_off\":" << st.bn_off << "}";
+      << st.mapB_off << "],\"bk_off\":" << st.bk_off << ",\"bn_off\":" << st.bn_off << ",\"variant\":" << st.variant
+      << ",\"tile_cap\":" << st.tile_cap << ",\"pair\":" << st.pair << ",\"alts\":[";
+    for (size_t a = 0; a < st.alts.size(); ++a) {
+      const PermSched& ps = st.alts[a];
+      o << (a ? "," : "") << "{\"t_bits\":" << ps.t_bits << ",\"tab_off\":" << ps.tab_off << ",\"n_rest\":" << ps.n_rest
+        << ",\"rest_in\":[";
+      for (int v = 0; v < ps.n_rest; ++v) o << (v ? "," : "") << (int)ps.rest_in[v];
+      o << "],\"rest_out\":[";
+      for (int v = 0; v < ps.n_rest; ++v) o << (v ? "," : "") << (int)ps.rest_out[v];
+      o << "]}";
+    }
+    o << "]}";
   }
   o << "],\"final\":{\"vt\":" << plan.fin.vt << ",\"open_pos\":[";
   for (size_t j = 0; j < plan.open_qubits.size(); ++j) o << (j ? "," : "") << plan.fin.open_pos[j];

@@ -74,6 +74,23 @@ struct BufInfo {
   int first = 0, last = 0;  // step lifetime (inclusive)
 };
 
+// Tile schedule of a permute step: tile bits, its tables in meta and the
+// input / output positions of the remaining (tile index) bits.
+struct PermSched {
+  int t_bits = 0;
+  int64_t tab_off = 0;
+  int n_rest = 0;
+  uint8_t rest_in[64] = {0}, rest_out[64] = {0};
+  // PERMUTE: the schedules a plan tuner may choose from (alts[0] is the
+  // default); the fields above hold the chosen one
+  std::vector<PermSched> alts;
+  // GEMM_TC: widest tile (real columns, 16..256) and CTA pairs allowed (0) or
+  // not (-1), as chosen by a plan tuner (default: the dispatch rule's widest)
+  int tile_cap = 256;
+  int pair = 0;
+  int variant = 0;         // index of the chosen variant (0: default)
+};
+
 struct Step {
   int kind = ST_SMALL;
   Ref a, b, c;
@@ -99,6 +116,14 @@ struct Step {
   int64_t tab_off = 0;
   int n_rest = 0;
   uint8_t rest_in[64] = {0}, rest_out[64] = {0};
+  // PERMUTE: the schedules a plan tuner may choose from (alts[0] is the
+  // default); the fields above hold the chosen one
+  std::vector<PermSched> alts;
+  // GEMM_TC: widest tile (real columns, 16..256) and CTA pairs allowed (0) or
+  // not (-1), as chosen by a plan tuner (default: the dispatch rule's widest)
+  int tile_cap = 256;
+  int pair = 0;
+  int variant = 0;         // index of the chosen variant (0: default)
   // BPREP: gather tables bk[K], bn[N] in meta (uint32)
   int64_t bk_off = 0, bn_off = 0;
   // BPREP_TC run on the side stream: it may start once every step before
@@ -192,6 +217,7 @@ struct PlanInput {
 };
 
 int build_plan(const PlanInput& in, Plan& plan, std::string& err);
+void apply_perm_schedule(Step& s, const PermSched& ps);
 std::string describe_plan(const Plan& plan, bool with_data);
 
 }  // namespace tn

@@ -24,6 +24,41 @@ def tn():
 ST_SMALL, ST_PERMUTE, ST_BPREP_TC, ST_GEMM_TC, ST_BPREP_C, ST_GEMM_SIMT, ST_ABSMAX = range(7)
 
 
+def _perm_bit_map(meta, sc, r):
+    """Output bit position of every input bit under one permute schedule, as
+    the kernel indexes it: out[bo + out_off[j]] = in[bi + in_off[slot[j]]]
+    inside a tile, the remaining bits moved by rest_in -> rest_out.  Also
+    checks that the three tables are OR-linear in the tile index (so the
+    single-bit images fix the whole map) and stay inside the tensor."""
+    t = sc["t_bits"]
+    nt = 1 << t
+    assert t + sc["n_rest"] == r and sc["n_rest"] <= 32 and t <= 10
+    assert sc["tab_off"] + 3 * nt <= meta.size
+    tab = meta[sc["tab_off"]:sc["tab_off"] + 3 * nt]
+    assert (tab >= 0).all() and (tab < (1 << r)).all()
+    s_in, s_out, slot = tab[:nt], tab[nt:2 * nt], tab[2 * nt:]
+    assert (slot < nt).all()
+    img = {}
+    for u in range(t):
+        j = 1 << u
+        src, dst = int(s_in[slot[j]]), int(s_out[j])
+        assert src & (src - 1) == 0 and dst & (dst - 1) == 0 and src and dst
+        img[src.bit_length() - 1] = dst.bit_length() - 1
+    js = np.arange(nt)
+    for name, tb in (("out", s_out), ("slot", slot), ("in", s_in)):
+        acc = np.zeros(nt, dtype=np.int64)
+        for u in range(t):
+            acc |= np.where((js >> u) & 1, tb[1 << u], 0)
+        assert (acc == tb).all(), name
+    assert (s_in[slot] == np.bitwise_or.reduce([np.where((js >> u) & 1, s_in[slot[1 << u]], 0)
+                                                for u in range(t)] or [np.zeros(nt, np.int64)])).all()
+    for a, b in zip(sc["rest_in"], sc["rest_out"]):
+        assert 0 <= a < r and 0 <= b < r and a not in img
+        img[a] = b
+    assert sorted(img) == list(range(r))
+    return [img[x] for x in range(r)]
+
+
 def _check_plan(d):
     meta = np.asarray(d["meta"], dtype=np.int64)
     bufs = d["bufs"]
@@ -69,12 +104,13 @@ def _check_plan(d):
             assert 8 * n <= cap(s["a"])
             per = {0: 8, 1: 16, 2: 8, 3: 8}[s["split"]]       # bytes written per complex element (both planes)
             assert per * n <= cap(s["c"]), (i, s["split"])
-            t = s["t_bits"]
-            assert t + s["n_rest"] == s["rA"] and s["n_rest"] <= 32 and t <= 10
-            assert s["tab_off"] + 3 * (1 << t) <= meta.size
-            tab = meta[s["tab_off"]:s["tab_off"] + 3 * (1 << t)]
-            assert (tab >= 0).all() and (tab < (1 << s["rA"])).all()
-            assert all(0 <= x < s["rA"] for x in s["rest_in"] + s["rest_out"])
+            # the chosen schedule and every alternative a tuner may pick: tables
+            # inside meta, and each one the same bit permutation as the default
+            scheds = [s] + list(s["alts"])
+            assert s["alts"] and 0 <= s["variant"] < len(s["alts"])
+            maps = [_perm_bit_map(meta, x, s["rA"]) for x in scheds]
+            assert all(m == maps[1] for m in maps), i
+            assert sorted(maps[0]) == list(range(s["rA"]))
         elif k in (ST_BPREP_TC, ST_BPREP_C):
             assert 8 * s["PA"] << s["rA"] <= cap(s["a"])
             K, N = 1 << s["nk"], 1 << s["nn"]
