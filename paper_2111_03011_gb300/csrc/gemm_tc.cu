@@ -19,11 +19,11 @@
 // nearest, so a long K loop accumulated in place drifts (the error grows
 // linearly with K; see Ootomo and Yokota, "Recovering single precision
 // accuracy from Tensor Cores while surpassing the FP32 theoretical peak
-// performance", 2022).  The K loop is therefore cut into chunks of 128 bytes of K,
-// each accumulated from zero in one of two ping-pong TMEM buffers (2 x BN <= 512
-// columns) and folded by eight drain warps into a running sum held in their
-// registers with ordinary round-to-nearest FP32 adds, while the MMAs of the
-// next chunk fill the other buffer.
+// performance", 2022).  The K loop is therefore cut into chunks of K (see
+// chunk_bytes), each accumulated from zero in one of two ping-pong TMEM
+// buffers (2 x BN <= 512 columns) and folded by eight drain warps into a
+// running sum held in their registers with ordinary round-to-nearest FP32
+// adds, while the MMAs of the next chunk fill the other buffer.
 //
 // Roles (320 threads): warps 0-7 drain chunk accumulators into the running sum
 // and write the tile out (two warps per TMEM lane quarter, half the columns
@@ -58,9 +58,7 @@ namespace tc {
 constexpr int BM = 128;
 // K per k-block (one pipeline stage), KB bytes of each operand row: 128 (the
 // 128-byte swizzle) or 64 (the 64-byte swizzle; stages half the size, twice
-// as many in flight, half the MMAs per k-block).  A chunk (one fresh TMEM
-// accumulation) always spans 128 bytes of K: 32 real terms (tf32) or 64
-// (bf16, fp16), i.e. 128 / KB k-blocks.
+// as many in flight, half the MMAs per k-block).
 // Choice per instantiation (measured on the 30-qubit plan): 128-byte
 // k-blocks for the 16-bit formats up to BN = 128, where the MMAs are short
 // and the per-k-block issue cost shows; 64-byte ones for tf32 and for BN = 256,
@@ -74,9 +72,20 @@ __host__ __device__ constexpr int kb_stages(int BN, int KB) {
 
 template <int KB>
 struct KBlock {
-  static constexpr int CH = 128 / KB;     // k-blocks per chunk
   static constexpr int KK = KB / 32;      // MMAs per product per k-block (32 bytes of K each)
 };
+
+// Bytes of K per chunk (one fresh TMEM accumulation, then one drain into the
+// registers' running sum).  Longer chunks drain less often: on the 30-qubit
+// workload the drain of 128-byte chunks held back the MMAs (the dominant
+// pair GEMM ran 8 % faster with 256-byte chunks and 11 % with 512-byte ones),
+// but each chunk adds more MMA results in the tensor cores' own accumulation.
+// Relative error of the 64-slice head against the O1 state vector with 128,
+// 256 and 512-byte chunks: FP16x3 1.9e-6, 3.4e-6, 5.8e-6; 3xTF32 2.4e-6,
+// 4.0e-6, 7.1e-6; BF16x3 2.02e-5, 2.05e-5, 2.10e-5 (its 8-bit split
+// dominates).  So the engines bound at 1e-5 (3xTF32, FP16x3) take 256 bytes
+// (64 tf32 or 128 fp16 terms) and BF16x3, bound at 1e-4, takes 512.
+__host__ __device__ constexpr int chunk_bytes(int FMT) { return FMT == 1 ? 512 : 256; }
 constexpr int kThreads = 320;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -229,6 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               int mapA_mode, int mapB_mode, const unsigned int* scaleA, const unsigned int* scaleB,
               unsigned int* amax_out, unsigned int* status) {
   constexpr int KB = kb_bytes(BN, FMT);
+  constexpr int CH = chunk_bytes(FMT) / KB;   // k-blocks per chunk
   using Lay = Layout<BN, STAGES, KB>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -248,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int br = BN / fold;                 // B rows per pattern box (2N when folded)
   constexpr bool H16 = FMT != 0;
   constexpr int BKE = KB / (H16 ? 2 : 4);   // K elements per k-block
-  constexpr int CH = KBlock<KB>::CH, KK = KBlock<KB>::KK;
+  constexpr int KK = KBlock<KB>::KK;
   const int nkb = (int)((K2 + BKE - 1) / BKE);
   const int nch = (nkb + CH - 1) / CH;
   // tile t -> first pattern pc0 of its group, m-tile, n-tile
@@ -593,7 +603,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   const int half_boxes = fold >= 2 ? fold / 2 : 1;   // B boxes this CTA loads per stage
   const int box_rows = fold >= 2 ? br : 128;
   constexpr int BKE = KB / 2;               // K elements (16-bit) per k-block
-  constexpr int CH = KBlock<KB>::CH, KK = KBlock<KB>::KK;
+  constexpr int CH = chunk_bytes(FMT) / KB, KK = KBlock<KB>::KK;
   const int nkb = (int)((K2 + BKE - 1) / BKE);
   const int nch = (nkb + CH - 1) / CH;
   auto coords = [&](int64_t t, int64_t& pc0, int64_t& tm, int64_t& tn_) {
@@ -728,7 +738,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const float ua = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleA)) : 1.0f;
     const float ub = FMT == 2 ? pow2f(-fp16_scale_exp(*scaleB)) : 1.0f;
-    const uint32_t acce_leader[2] = {mapa_rank(smem_u32(&acce[0]), 0), mapa_rank(smem_u32(&acce[1]), 0)};
+    // the leader's release barriers: acce[b] sits 8 bytes past acce[0] there
+    // too (an offset, not an indexed local array, which would live in local
+    // memory)
+    const uint32_t acce_leader = mapa_rank(smem_u32(&acce[0]), 0);
     float tmax = 0.0f;
     uint32_t cc = 0;
     bool ok = true;
@@ -758,7 +771,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
-        if (lane == 0) mbar_arrive_cluster(acce_leader[b]);
+        if (lane == 0) mbar_arrive_cluster(acce_leader + 8u * (uint32_t)b);
         ++cc;
       }
       if (!ok) continue;
