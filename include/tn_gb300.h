@@ -186,7 +186,9 @@ int  tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* out);
  *     included); variant 0 is the default rule;
  *   permute step of >= 2^20 elements: tile schedules (input-run bits,
  *     output-run bits, tile bits) = (5, 5, 10) [default], (4, 6, 10),
- *     (6, 4, 10), (5, 5, 9), (4, 4, 8), duplicates removed;
+ *     (6, 4, 10), (5, 5, 9), (4, 4, 8), duplicates removed, each followed
+ *     by its four-outputs-per-store form where output bits 0 and 1 are bits
+ *     of the tile;
  *   every other step: one variant.
  * tn_plan_step_variants gives step i's variant count and current choice
  * (steps as in tn_plan_step_info).  tn_plan_set_step_variant chooses one; it

@@ -443,6 +443,7 @@ static cudaError_t launch_step(tn_plan_t* p, const tn::Step& x, int64_t s, cudaS
       pp.tab = p->d_meta + x.tab_off;
       pp.split = x.split;
       pp.scale = scale_ptr(p, x.slot);
+      pp.vec4 = x.vec4;
       e = tn::launch_permute(pp, st);
       break;
     }

@@ -150,7 +150,20 @@ __device__ __forceinline__ void cp_async_wait() {
 constexpr int kPermBufs = 3;
 
 __host__ __device__ inline int perm_levels(int n_rest) { return n_rest > 0 ? (n_rest + 7) >> 3 : 1; }
-__host__ __device__ inline int perm_tile_stride(int nt) { return nt + (nt >> 5) + 2; }   // float2 per buffer
+// float2 per buffer, even so that the index tables after the buffers start on 16 bytes
+__host__ __device__ inline int perm_tile_stride(int nt) { return (nt + (nt >> 5) + 3) & ~1; }
+
+// Four consecutive outputs of one plane as one 16-byte store (16-bit formats)
+// or two (fp32 pairs); the destination index is a multiple of 4.
+__device__ __forceinline__ void store4(float2* dst, float2 a, float2 b, float2 c, float2 d) {
+  float4* q = (float4*)dst;
+  q[0] = make_float4(a.x, a.y, b.x, b.y);
+  q[1] = make_float4(c.x, c.y, d.x, d.y);
+}
+template <typename H2>
+__device__ __forceinline__ void store4(H2* dst, H2 a, H2 b, H2 c, H2 d) {
+  *(uint4*)dst = make_uint4(*(const uint32_t*)&a, *(const uint32_t*)&b, *(const uint32_t*)&c, *(const uint32_t*)&d);
+}
 
 template <int SPLIT>
 __global__ void __launch_bounds__(256) k_permute(PermParams p) {
@@ -222,6 +235,55 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
     tile_base(blk, iofs, cur_dofs);
     const float2* t = tile + buf * tstride;
     buf = (buf + 1) % kPermBufs;
+    if (p.vec4) {
+      // output bits 0 and 1 are tile bits 0 and 1: outputs 4g .. 4g + 3 of
+      // the tile are consecutive in memory, from a 4-aligned index.  Fewer,
+      // wider stores, but each warp's shared-memory reads take other tile
+      // bits than in the loop below, so which is faster depends on the
+      // permutation: a schedule variant of its own, chosen by timing.
+      for (int g = threadIdx.x; g < (nt >> 2); g += blockDim.x) {
+        const uint4 sl = *(const uint4*)(s_slot + 4 * g);
+        const int64_t o = cur_dofs + s_out[4 * g];
+        const float2 v0 = t[sl.x], v1 = t[sl.y], v2 = t[sl.z], v3 = t[sl.w];
+        if (SPLIT == 1) {
+          const float2 h0 = make_float2(tf32_rn(v0.x), tf32_rn(v0.y)), h1 = make_float2(tf32_rn(v1.x), tf32_rn(v1.y));
+          const float2 h2 = make_float2(tf32_rn(v2.x), tf32_rn(v2.y)), h3 = make_float2(tf32_rn(v3.x), tf32_rn(v3.y));
+          store4(p.out + o, h0, h1, h2, h3);
+          store4(out_lo + o, make_float2(v0.x - h0.x, v0.y - h0.y), make_float2(v1.x - h1.x, v1.y - h1.y),
+                 make_float2(v2.x - h2.x, v2.y - h2.y), make_float2(v3.x - h3.x, v3.y - h3.y));
+        } else if (SPLIT == 3) {
+          __half2* fh = (__half2*)p.out;
+          __half2* fl = fh + p.P * p.pstride;
+          __half2 h[4], l[4];
+          const float2 v[4] = {v0, v1, v2, v3};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 w = make_float2(v[e].x * sc, v[e].y * sc);
+            h[e] = __floats2half2_rn(w.x, w.y);
+            const float2 hf = __half22float2(h[e]);
+            l[e] = __floats2half2_rn(w.x - hf.x, w.y - hf.y);
+          }
+          store4(fh + o, h[0], h[1], h[2], h[3]);
+          store4(fl + o, l[0], l[1], l[2], l[3]);
+        } else if (SPLIT == 2) {
+          __nv_bfloat162* bh = (__nv_bfloat162*)p.out;
+          __nv_bfloat162* bl = bh + p.P * p.pstride;
+          __nv_bfloat162 h[4], l[4];
+          const float2 v[4] = {v0, v1, v2, v3};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            h[e] = __floats2bfloat162_rn(v[e].x, v[e].y);
+            const float2 hf = __bfloat1622float2(h[e]);
+            l[e] = __floats2bfloat162_rn(v[e].x - hf.x, v[e].y - hf.y);
+          }
+          store4(bh + o, h[0], h[1], h[2], h[3]);
+          store4(bl + o, l[0], l[1], l[2], l[3]);
+        } else {
+          store4(p.out + o, v0, v1, v2, v3);
+        }
+      }
+      continue;
+    }
 #pragma unroll 4
     for (int j = threadIdx.x; j < nt; j += blockDim.x) {
       const float2 v = t[s_slot[j]];

@@ -56,6 +56,7 @@ struct PermParams {
   int split;             // 1: write tf32 hi plane then lo plane (fp32 pairs); 2: bf16 planes;
                          // 3: fp16 planes of the value times 2^k (k from *scale)
   const unsigned int* scale;   // SPLIT 3: the operand's scale slot
+  int vec4 = 0;          // 1: output bits 0 and 1 are tile bits 0 and 1 (four outputs per store)
 };
 
 struct BPrepParams {

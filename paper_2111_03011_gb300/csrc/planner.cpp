@@ -854,6 +854,7 @@ static PermSched perm_schedule(Plan& plan, const std::vector<int>& in_pos, const
   }
   PermSched ps;
   ps.t_bits = t;
+  ps.vec4 = 0;
   ps.tab_off = meta_push(plan, tab);
   ps.n_rest = 0;
   for (int x = 0; x < r; ++x)
@@ -869,6 +870,7 @@ void apply_perm_schedule(Step& s, const PermSched& ps) {
   s.t_bits = ps.t_bits;
   s.tab_off = ps.tab_off;
   s.n_rest = ps.n_rest;
+  s.vec4 = ps.vec4;
   std::memcpy(s.rest_in, ps.rest_in, sizeof(s.rest_in));
   std::memcpy(s.rest_out, ps.rest_out, sizeof(s.rest_out));
 }
@@ -891,6 +893,8 @@ static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& ta
   // tiles.  Permutes of at least 2^20 elements also get the alternatives
   // that a plan tuner may time: wider input or output runs, smaller tiles
   // (more resident blocks per SM).
+  // Each schedule whose output bits 0 and 1 are tile bits 0 and 1 also
+  // comes in the four-outputs-per-store form (same tables).
   static const int kSched[][3] = {{5, 5, 10}, {4, 6, 10}, {6, 4, 10}, {5, 5, 9}, {4, 4, 8}};
   const int n_sched = (int64_t)X.P << r >= (1LL << 20) ? 5 : 1;
   for (int v = 0; v < n_sched; ++v) {
@@ -904,6 +908,11 @@ static void add_permute(Plan& plan, const VTensor& X, const std::vector<int>& ta
       continue;
     }
     s.alts.push_back(ps);
+    const uint32_t* out_off = plan.meta.data() + ps.tab_off + ((size_t)1 << ps.t_bits);
+    if (n_sched > 1 && ps.t_bits >= 2 && out_off[1] == 1 && out_off[2] == 2) {
+      ps.vec4 = 1;
+      s.alts.push_back(ps);
+    }
   }
   apply_perm_schedule(s, s.alts[0]);
   s.bytes = (split == 1 ? 24.0 : 16.0) * (double)vt_elems(X);
@@ -1568,7 +1577,7 @@ std::string describe_plan(const Plan& plan, bool with_data) {
       << ",\"bytes\":" << st.bytes << ",\"rA\":" << st.rA << ",\"rB\":" << st.rB << ",\"rC\":" << st.rC
       << ",\"a\":[" << st.a.kind << "," << st.a.id << "],\"b\":[" << st.b.kind << "," << st.b.id << "],\"c\":["
       << st.c.kind << "," << st.c.id << "],\"t_bits\":" << st.t_bits << ",\"split\":" << st.split << ",\"h16\":" << st.h16 << ",\"slot\":" << st.slot << ",\"slotB\":" << st.slotB << ",\"max_slot\":" << st.max_slot << ",\"fork\":" << st.fork
-      << ",\"tab_off\":" << st.tab_off << ",\"n_rest\":" << st.n_rest << ",\"rest_in\":[";
+      << ",\"tab_off\":" << st.tab_off << ",\"vec4\":" << st.vec4 << ",\"n_rest\":" << st.n_rest << ",\"rest_in\":[";
     for (int v = 0; v < st.n_rest; ++v) o << (v ? "," : "") << (int)st.rest_in[v];
     o << "],\"rest_out\":[";
     for (int v = 0; v < st.n_rest; ++v) o << (v ? "," : "") << (int)st.rest_out[v];
@@ -1582,7 +1591,7 @@ std::string describe_plan(const Plan& plan, bool with_data) {
       << ",\"tile_cap\":" << st.tile_cap << ",\"pair\":" << st.pair << ",\"alts\":[";
     for (size_t a = 0; a < st.alts.size(); ++a) {
       const PermSched& ps = st.alts[a];
-      o << (a ? "," : "") << "{\"t_bits\":" << ps.t_bits << ",\"tab_off\":" << ps.tab_off << ",\"n_rest\":" << ps.n_rest
+      o << (a ? "," : "") << "{\"t_bits\":" << ps.t_bits << ",\"vec4\":" << ps.vec4 << ",\"tab_off\":" << ps.tab_off << ",\"n_rest\":" << ps.n_rest
         << ",\"rest_in\":[";
       for (int v = 0; v < ps.n_rest; ++v) o << (v ? "," : "") << (int)ps.rest_in[v];
       o << "],\"rest_out\":[";

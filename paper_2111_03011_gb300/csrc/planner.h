@@ -81,14 +81,7 @@ struct PermSched {
   int64_t tab_off = 0;
   int n_rest = 0;
   uint8_t rest_in[64] = {0}, rest_out[64] = {0};
-  // PERMUTE: the schedules a plan tuner may choose from (alts[0] is the
-  // default); the fields above hold the chosen one
-  std::vector<PermSched> alts;
-  // GEMM_TC: widest tile (real columns, 16..256) and CTA pairs allowed (0) or
-  // not (-1), as chosen by a plan tuner (default: the dispatch rule's widest)
-  int tile_cap = 256;
-  int pair = 0;
-  int variant = 0;         // index of the chosen variant (0: default)
+  int vec4 = 0;            // output bits 0 and 1 are tile bits 0 and 1 (four outputs per store)
 };
 
 struct Step {
@@ -119,6 +112,7 @@ struct Step {
   // PERMUTE: the schedules a plan tuner may choose from (alts[0] is the
   // default); the fields above hold the chosen one
   std::vector<PermSched> alts;
+  int vec4 = 0;            // PERMUTE: of the chosen schedule
   // GEMM_TC: widest tile (real columns, 16..256) and CTA pairs allowed (0) or
   // not (-1), as chosen by a plan tuner (default: the dispatch rule's widest)
   int tile_cap = 256;

@@ -38,6 +38,9 @@ def _perm_bit_map(meta, sc, r):
     assert (tab >= 0).all() and (tab < (1 << r)).all()
     s_in, s_out, slot = tab[:nt], tab[nt:2 * nt], tab[2 * nt:]
     assert (slot < nt).all()
+    if sc["vec4"]:      # outputs 4g .. 4g + 3 of a tile are consecutive, from a 4-aligned offset
+        assert t >= 2 and s_out[1] == 1 and s_out[2] == 2
+        assert all(x >= 2 for x in sc["rest_out"])
     img = {}
     for u in range(t):
         j = 1 << u

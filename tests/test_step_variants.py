@@ -53,6 +53,8 @@ def test_variant_counts_and_defaults(tn, plan30):
             assert (s["t_bits"], s["n_rest"], s["tab_off"]) == (
                 s["alts"][0]["t_bits"], s["alts"][0]["n_rest"], s["alts"][0]["tab_off"])
             n_perm_multi += n > 1
+            assert s["alts"][0]["vec4"] == 0 and all(
+                b["vec4"] == 1 and b["tab_off"] == a["tab_off"] for a, b in zip(s["alts"], s["alts"][1:]) if b["vec4"])
         else:
             assert n == 1
     # the 30-qubit plan has tunable GEMM tiles and permute schedules
@@ -74,8 +76,8 @@ def test_choosing_a_variant_changes_only_its_launch(tn):
             assert x["variant"] == v and tn.tn_plan_step_variants(p, i) == (n, v)
             if s["kind"] == ST_PERMUTE:
                 a = s["alts"][v]
-                assert (x["t_bits"], x["tab_off"], x["n_rest"], x["rest_in"], x["rest_out"]) == (
-                    a["t_bits"], a["tab_off"], a["n_rest"], a["rest_in"], a["rest_out"])
+                assert (x["t_bits"], x["tab_off"], x["n_rest"], x["rest_in"], x["rest_out"], x["vec4"]) == (
+                    a["t_bits"], a["tab_off"], a["n_rest"], a["rest_in"], a["rest_out"], a["vec4"])
             elif s["kind"] == ST_GEMM_TC:
                 # the v-th distinct tile of the list, in list order
                 seen, picks = [], []
@@ -95,7 +97,8 @@ def test_choosing_a_variant_changes_only_its_launch(tn):
     # everything but the variant fields is unchanged
     for s0, s1 in zip(d0["steps"], d1["steps"]):
         for k in s0:
-            if k not in ("variant", "tile_cap", "pair", "t_bits", "tab_off", "n_rest", "rest_in", "rest_out"):
+            if k not in ("variant", "tile_cap", "pair", "t_bits", "tab_off", "n_rest", "rest_in", "rest_out",
+                         "vec4"):
                 assert s0[k] == s1[k], k
     with pytest.raises(tn.TNError):
         tn.tn_plan_step_variants(p, len(d0["steps"]))
