@@ -43,13 +43,11 @@ import circuit_inputs as ci  # noqa: E402
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch,
 # from a single-kernel ncu capture of the current kernel; keyed by the GEMM
-# A dominant launch with no entry reports traffic null.
 # engine, the GEMM tiling ("cta" or "pair") and the launch's algorithmic
-# complex MACs and bytes (tn_plan_step_info).
+# complex MACs and bytes (tn_plan_step_info).  A dominant launch with no
+# entry reports traffic null.
 MEASURED_TRAFFIC = {
-    ("fp16", "cta", 270582939648, 1329594368): (7.264653e9 + 0.2639552e9,
-                                                "profiles/gemm_tc_fp16x3_grid5x6_m14_open10_L64_k6.md"),
-    ("fp16", "pair", 270582939648, 1329594368): (4.611263e9 + 0.264522496e9,
+    ("fp16", "pair", 270582939648, 1329594368): (5.423687e9 + 0.266117888e9,
                                                  "profiles/gemm_tc_pair_fp16x3_grid5x6_m14_open10_L64_k6.md"),
 }
 
