@@ -8,7 +8,9 @@ The shapes cover every GEMM path:
 - 2, 4, 8 and 16 patterns folded side by side, with a ragged last group;
 - ragged K (one k-block and chunks of several);
 - gather tables for both operands;
-- K = 2, which the 16-bit engines run in tf32.
+- K = 2, which the 16-bit engines run in tf32;
+- a partial last wave of pair tiles (80 tiles on 76 clusters) and fewer
+  tiles than clusters.
 
 Tolerance: relative L2 <= 1e-5 (3xTF32, FP16x3, CUDA-core FP32) or 1e-4
 (BF16x3), and every element within twice that of the largest.
@@ -34,6 +36,8 @@ SHAPES = [
     (256, 64, 2, 1, 1, 1, None, None),          # K = 2 (tf32 kernel for the 16-bit engines)
     (128, 32, 64, 3, 4, 7, [0, 2, 1, 2, 0, 1, 2], [3, 0, 1, 2, 3, 3, 0]),   # gather tables
     (512, 128, 128, 2, 6, 6, [0, 1, 0, 1, 0, 1], None),   # A gathered: no fold
+    (4096, 64, 1024, 1, 10, 10, None, None),    # 80 pair tiles on 76 clusters: a 4-tile last wave
+    (2048, 128, 1024, 1, 1, 1, None, None),     # 8 pair tiles, fewer than the clusters
 ]
 
 
