@@ -189,6 +189,9 @@ int  tn_plan_get_stats(const tn_plan_t* plan, tn_plan_stats* out);
  *     (6, 4, 10), (5, 5, 9), (4, 4, 8), duplicates removed, each followed
  *     by its four-outputs-per-store form where output bits 0 and 1 are bits
  *     of the tile;
+ *   tensor-core B preparation of >= 2^20 elements (not beside a GEMM): the
+ *     gather kernel and the permute kernel writing the real embedding, the
+ *     permute first (variant 0) when the gather's loads would not coalesce;
  *   every other step: one variant.
  * tn_plan_step_variants gives step i's variant count and current choice
  * (steps as in tn_plan_step_info).  tn_plan_set_step_variant chooses one; it

@@ -449,6 +449,24 @@ static cudaError_t launch_step(tn_plan_t* p, const tn::Step& x, int64_t s, cudaS
     }
     case tn::ST_BPREP_C:
     case tn::ST_BPREP_TC: {
+      if (x.kind == tn::ST_BPREP_TC && !x.alts.empty() && (x.variant == 0) == (x.bprep_embed0 != 0)) {
+        // the permute kernel onto [N][K] order, writing the real embedding
+        tn::PermParams pp;
+        pp.in = ref_ptr(p, x.a, s);
+        pp.out = buf_ptr(p, x.c);
+        pp.pstride = 1LL << x.rA;
+        pp.P = x.PA;
+        pp.t = x.t_bits;
+        pp.n_rest = x.n_rest;
+        std::memcpy(pp.rest_in, x.rest_in, sizeof(pp.rest_in));
+        std::memcpy(pp.rest_out, x.rest_out, sizeof(pp.rest_out));
+        pp.tab = p->d_meta + x.tab_off;
+        pp.split = 4 + x.h16;
+        pp.scale = scale_ptr(p, x.slot);
+        pp.embed_nk = x.nk;
+        e = tn::launch_permute(pp, st);
+        break;
+      }
       tn::BPrepParams bp;
       bp.B = ref_ptr(p, x.a, s);
       bp.out = buf_ptr(p, x.c);
@@ -721,6 +739,7 @@ std::vector<int> gemm_variants(const tn::Step& x) {
 int step_variant_count(const tn::Step& x) {
   if (x.kind == tn::ST_GEMM_TC) return (int)gemm_variants(x).size();
   if (x.kind == tn::ST_PERMUTE) return std::max<int>(1, (int)x.alts.size());
+  if (x.kind == tn::ST_BPREP_TC) return x.alts.empty() ? 1 : 2;
   return 1;
 }
 

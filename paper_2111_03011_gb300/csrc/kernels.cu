@@ -165,6 +165,40 @@ __device__ __forceinline__ void store4(H2* dst, H2 a, H2 b, H2 c, H2 d) {
   *(uint4*)dst = make_uint4(*(const uint32_t*)&a, *(const uint32_t*)&b, *(const uint32_t*)&c, *(const uint32_t*)&d);
 }
 
+// Split of two reals into the hi and lo parts of a tensor-core operand format
+// (FMT 0: tf32-rounded fp32 hi + fp32 remainder; 1: bf16 hi + bf16 remainder;
+// 2: fp16 of the value times the scale sc).
+template <int FMT>
+struct Pair;
+template <>
+struct Pair<0> {
+  using T = float2;
+  static __device__ __forceinline__ void split(float a, float b, float, T& h, T& l) {
+    h = make_float2(tf32_rn(a), tf32_rn(b));
+    l = make_float2(a - h.x, b - h.y);
+  }
+};
+template <>
+struct Pair<1> {
+  using T = __nv_bfloat162;
+  static __device__ __forceinline__ void split(float a, float b, float, T& h, T& l) {
+    h = __floats2bfloat162_rn(a, b);
+    const float2 f = __bfloat1622float2(h);
+    l = __floats2bfloat162_rn(a - f.x, b - f.y);
+  }
+};
+template <>
+struct Pair<2> {
+  using T = __half2;
+  static __device__ __forceinline__ void split(float a, float b, float sc, T& h, T& l) {
+    a *= sc;
+    b *= sc;
+    h = __floats2half2_rn(a, b);
+    const float2 f = __half22float2(h);
+    l = __floats2half2_rn(a - f.x, b - f.y);
+  }
+};
+
 template <int SPLIT>
 __global__ void __launch_bounds__(256) k_permute(PermParams p) {
   extern __shared__ float2 tile[];
@@ -198,7 +232,7 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
   const uint64_t nrest_mask = (1ULL << p.n_rest) - 1;
   const uint64_t total_tiles = (uint64_t)p.P << p.n_rest;
   float2* __restrict__ out_lo = p.out + p.P * p.pstride;
-  const float sc = SPLIT == 3 ? pow2f(fp16_scale_exp(*p.scale)) : 1.0f;
+  const float sc = (SPLIT == 3 || SPLIT == 6) ? pow2f(fp16_scale_exp(*p.scale)) : 1.0f;
   // input and output base offsets of tile blk: the pattern's stride plus the
   // rest bits of the tile index scattered through the per-byte tables
   auto tile_base = [&](uint64_t blk, int64_t& iofs, int64_t& dofs) {
@@ -235,7 +269,7 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
     tile_base(blk, iofs, cur_dofs);
     const float2* t = tile + buf * tstride;
     buf = (buf + 1) % kPermBufs;
-    if (p.vec4) {
+    if (SPLIT < 4 && p.vec4) {
       // output bits 0 and 1 are tile bits 0 and 1: outputs 4g .. 4g + 3 of
       // the tile are consecutive in memory, from a 4-aligned index.  Fewer,
       // wider stores, but each warp's shared-memory reads take other tile
@@ -288,7 +322,24 @@ __global__ void __launch_bounds__(256) k_permute(PermParams p) {
     for (int j = threadIdx.x; j < nt; j += blockDim.x) {
       const float2 v = t[s_slot[j]];
       const int64_t o = cur_dofs + s_out[j];
-      if (SPLIT == 1) {
+      if constexpr (SPLIT >= 4) {
+        // the tensor-core B operand: output index o = k + K n of a pattern
+        // becomes the 2 x 2 block [[re, -im], [im, re]] at pairs (2k, 2k+1)
+        // of rows 2n and 2n + 1 of the [2N][2K] real embedding
+        using PT = Pair<SPLIT - 4>;
+        using T = typename PT::T;
+        T* hi = (T*)p.out;
+        T* lo = hi + 2 * p.P * p.pstride;
+        const int64_t K = 1LL << p.embed_nk;
+        const int64_t e0 = 2 * o - (o & (K - 1));
+        T h, l;
+        PT::split(v.x, -v.y, sc, h, l);
+        hi[e0] = h;
+        lo[e0] = l;
+        PT::split(v.y, v.x, sc, h, l);
+        hi[e0 + K] = h;
+        lo[e0 + K] = l;
+      } else if (SPLIT == 1) {
         const float2 h = make_float2(tf32_rn(v.x), tf32_rn(v.y));
         p.out[o] = h;
         out_lo[o] = make_float2(v.x - h.x, v.y - h.y);
@@ -358,6 +409,9 @@ cudaError_t prepare_permute() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_permute<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_permute<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_permute<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_permute<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_permute<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_permute<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   return e;
 }
 
@@ -370,6 +424,9 @@ cudaError_t launch_permute(const PermParams& p, cudaStream_t s) {
   if (p.split == 1) k_permute<1><<<(unsigned)grid, 256, smem, s>>>(p);
   else if (p.split == 2) k_permute<2><<<(unsigned)grid, 256, smem, s>>>(p);
   else if (p.split == 3) k_permute<3><<<(unsigned)grid, 256, smem, s>>>(p);
+  else if (p.split == 4) k_permute<4><<<(unsigned)grid, 256, smem, s>>>(p);
+  else if (p.split == 5) k_permute<5><<<(unsigned)grid, 256, smem, s>>>(p);
+  else if (p.split == 6) k_permute<6><<<(unsigned)grid, 256, smem, s>>>(p);
   else k_permute<0><<<(unsigned)grid, 256, smem, s>>>(p);
   return cudaGetLastError();
 }
@@ -394,37 +451,9 @@ __global__ void k_bprep_c(BPrepParams p) {
 // thread per complex element of B: it writes the element's 2 x 2 block as two
 // pairs of adjacent reals (rows 2n and 2n + 1) in each plane; consecutive
 // threads take consecutive k, so every row segment is written contiguously.
-template <int FMT>
-struct Pair;
-template <>
-struct Pair<0> {
-  using T = float2;
-  static __device__ __forceinline__ void split(float a, float b, float, T& h, T& l) {
-    h = make_float2(tf32_rn(a), tf32_rn(b));
-    l = make_float2(a - h.x, b - h.y);
-  }
-};
-template <>
-struct Pair<1> {
-  using T = __nv_bfloat162;
-  static __device__ __forceinline__ void split(float a, float b, float, T& h, T& l) {
-    h = __floats2bfloat162_rn(a, b);
-    const float2 f = __bfloat1622float2(h);
-    l = __floats2bfloat162_rn(a - f.x, b - f.y);
-  }
-};
-template <>
-struct Pair<2> {
-  using T = __half2;
-  static __device__ __forceinline__ void split(float a, float b, float sc, T& h, T& l) {
-    a *= sc;
-    b *= sc;
-    h = __floats2half2_rn(a, b);
-    const float2 f = __half22float2(h);
-    l = __floats2half2_rn(a - f.x, b - f.y);
-  }
-};
-
+// Its loads coalesce only when B's K legs are its low bits; otherwise the
+// plan prepares B with the permute kernel in an embedding mode (split 4-6),
+// which reads through a shared-memory tile.
 template <int FMT>
 __global__ void k_bprep_tc(BPrepParams p) {
   using T = typename Pair<FMT>::T;

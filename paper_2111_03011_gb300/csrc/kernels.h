@@ -54,9 +54,12 @@ struct PermParams {
   uint8_t rest_in[64], rest_out[64];
   const uint32_t* tab;   // in_off[2^t], out_off[2^t], slot[2^t]
   int split;             // 1: write tf32 hi plane then lo plane (fp32 pairs); 2: bf16 planes;
-                         // 3: fp16 planes of the value times 2^k (k from *scale)
+                         // 3: fp16 planes of the value times 2^k (k from *scale);
+                         // 4, 5, 6: the tensor-core B operand (real embedding of the permuted
+                         // [N][K] tensor) in tf32, bf16 or scaled fp16 hi/lo planes
   const unsigned int* scale;   // SPLIT 3: the operand's scale slot
   int vec4 = 0;          // 1: output bits 0 and 1 are tile bits 0 and 1 (four outputs per store)
+  int embed_nk = 0;      // split 4-6: log2 K (the output's low bits are the K legs)
 };
 
 struct BPrepParams {

@@ -1070,6 +1070,22 @@ static int layout_steps(Plan& plan, std::string& err) {
       p.nk = nk; p.nn = nn;
       p.bk_off = meta_push(plan, bk);
       p.bn_off = meta_push(plan, bn);
+      if (tc && (int)sml.legs.size() == nk + nn && vt_elems(sml) >= (1LL << 20)) {
+        // the permute alternative: B's legs to [N][K] order (K legs low),
+        // written as the real embedding; the plan's rule takes it when the
+        // gather's consecutive k are not consecutive in memory
+        std::vector<int> target;
+        for (int l : K) target.push_back(l);
+        for (int l : N) target.push_back(l);
+        const int r = (int)target.size();
+        std::vector<int> in_pos(r), inv(r);
+        for (int o = 0; o < r; ++o) in_pos[o] = find_pos(sml.legs, target[o]);
+        for (int o = 0; o < r; ++o) inv[in_pos[o]] = o;
+        PermSched ps = perm_schedule(plan, in_pos, inv, 5, 5, 10);
+        p.alts.push_back(ps);
+        apply_perm_schedule(p, ps);
+        p.bprep_embed0 = nk >= 1 && bk[1] != 1u;
+      }
       const int64_t bprep_bytes =
           tc ? 2LL * sml.P * (2LL << nn) * (2LL << nk) * (bf16 ? 2 : 4) : sml.P * (1LL << (nk + nn)) * 8;
       {
@@ -1157,6 +1173,9 @@ static void schedule_side_bprep(Plan& plan) {
         x.fork = q;
         plan.bufs[x.c.id].first = std::min(plan.bufs[x.c.id].first, q);
         ++plan.n_side_bprep;
+        // beside a GEMM only the gather kernel fits (one small block per SM)
+        x.alts.clear();
+        x.bprep_embed0 = 0;
       }
     }
     if (x.c.kind == 1) producer[x.c.id] = i;
@@ -1587,7 +1606,7 @@ std::string describe_plan(const Plan& plan, bool with_data) {
     o << "],\"boffN\":[";
     for (int v = 0; v < 16; ++v) o << (v ? "," : "") << st.boffN[v];
     o << "],\"mapA\":[" << st.mapA_mode << "," << st.mapA_off << "],\"mapB\":[" << st.mapB_mode << ","
-      << st.mapB_off << "],\"bk_off\":" << st.bk_off << ",\"bn_off\":" << st.bn_off << ",\"variant\":" << st.variant
+      << st.mapB_off << "],\"bk_off\":" << st.bk_off << ",\"bn_off\":" << st.bn_off << ",\"bprep_embed0\":" << st.bprep_embed0 << ",\"variant\":" << st.variant
       << ",\"tile_cap\":" << st.tile_cap << ",\"pair\":" << st.pair << ",\"alts\":[";
     for (size_t a = 0; a < st.alts.size(); ++a) {
       const PermSched& ps = st.alts[a];

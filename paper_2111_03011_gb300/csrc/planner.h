@@ -113,6 +113,11 @@ struct Step {
   // default); the fields above hold the chosen one
   std::vector<PermSched> alts;
   int vec4 = 0;            // PERMUTE: of the chosen schedule
+  // BPREP_TC with alts (its B operand has >= 2^20 elements): variant 0 or 1 is
+  // the gather kernel, the other the permute kernel in an embedding mode with
+  // the tile schedule alts[0] (fields above) onto [N][K] order; 1 here: the
+  // plan's rule picked the permute (the gather's loads would not coalesce)
+  int bprep_embed0 = 0;
   // GEMM_TC: widest tile (real columns, 16..256) and CTA pairs allowed (0) or
   // not (-1), as chosen by a plan tuner (default: the dispatch rule's widest)
   int tile_cap = 256;

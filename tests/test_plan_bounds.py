@@ -123,6 +123,21 @@ def _check_plan(d):
             if k == ST_BPREP_TC:
                 es = 4 if s["h16"] == 0 else 2
                 assert 2 * s["PA"] * (2 * N) * (2 * K) * es <= cap(s["c"])
+                if s["alts"]:
+                    # the permute alternative: K legs to output bits 0 .. nk-1, N legs
+                    # above them (the order the gather tables encode); it writes
+                    # the same embedded planes into the same buffer
+                    bkt = meta[s["bk_off"]:s["bk_off"] + K]
+                    bnt = meta[s["bn_off"]:s["bn_off"] + N]
+                    want = {}
+                    for q in range(s["nk"]):
+                        want[int(bkt[1 << q]).bit_length() - 1] = q
+                    for q in range(s["nn"]):
+                        want[int(bnt[1 << q]).bit_length() - 1] = s["nk"] + q
+                    assert s["rA"] == s["nk"] + s["nn"] and sorted(want) == list(range(s["rA"]))
+                    assert _perm_bit_map(meta, s["alts"][0], s["rA"]) == [want[x] for x in range(s["rA"])]
+                    assert not s["alts"][0]["vec4"] and s["fork"] < 0
+                    assert s["bprep_embed0"] == int(s["nk"] >= 1 and bkt[1] != 1)
             else:
                 assert 8 * s["PA"] * K * N <= cap(s["c"])
         elif k in (ST_GEMM_TC, ST_GEMM_SIMT):

@@ -4,7 +4,7 @@ import pytest
 
 import circuit_inputs as ci
 
-ST_PERMUTE, ST_GEMM_TC = 1, 3
+ST_PERMUTE, ST_BPREP_TC, ST_GEMM_TC = 1, 2, 3
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +37,7 @@ def _tile(s, cap, pair):
 
 def test_variant_counts_and_defaults(tn, plan30):
     d = tn.tn_plan_describe(plan30)
-    n_gemm_multi = n_perm_multi = 0
+    n_gemm_multi = n_perm_multi = n_bprep_multi = 0
     for i, s in enumerate(d["steps"]):
         n, chosen = tn.tn_plan_step_variants(plan30, i)
         assert chosen == 0 and s["variant"] == 0
@@ -55,10 +55,13 @@ def test_variant_counts_and_defaults(tn, plan30):
             n_perm_multi += n > 1
             assert s["alts"][0]["vec4"] == 0 and all(
                 b["vec4"] == 1 and b["tab_off"] == a["tab_off"] for a, b in zip(s["alts"], s["alts"][1:]) if b["vec4"])
+        elif s["kind"] == ST_BPREP_TC:
+            assert n == (2 if s["alts"] else 1)
+            n_bprep_multi += n > 1
         else:
             assert n == 1
-    # the 30-qubit plan has tunable GEMM tiles and permute schedules
-    assert n_gemm_multi >= 5 and n_perm_multi >= 3
+    # the 30-qubit plan has tunable GEMM tiles, permute schedules and B preparations
+    assert n_gemm_multi >= 5 and n_perm_multi >= 3 and n_bprep_multi >= 1
     assert tn.tn_plan_get_stats(plan30)["n_tuned_steps"] == 0
 
 
