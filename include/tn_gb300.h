@@ -120,8 +120,9 @@ typedef struct {
                                  preparation takes).  tn_profile_slices always runs in order. */
   int    tune_steps;          /* tn_plan_autotune only.  0: after choosing the order, tune every
                                  step's tile variant (tn_plan_tune_steps, 3 repetitions) when a
-                                 slice takes at most 1 s; > 0: tune with this many repetitions
-                                 whatever the slice time; -1: do not tune steps. */
+                                 pass (a slice, or 1/2^n_internal_sliced of it) takes at most 1 s;
+                                 > 0: tune with this many repetitions whatever the time; -1: do not
+                                 tune steps. */
 } tn_plan_opts;
 
 typedef struct tn_plan tn_plan_t;
@@ -149,7 +150,7 @@ typedef struct {
   int     gemm_pair;          /* the plan's tn_plan_opts.gemm_pair (as chosen by tn_plan_autotune) */
   int     n_side_bprep;       /* B-preparation steps that run beside an earlier GEMM (side_bprep) */
   int     n_tuned_steps;      /* steps whose chosen tile variant is not the default (0: untuned) */
-  double  tune_default_ms;    /* tn_plan_tune_steps: one slice with the variants it started from */
+  double  tune_default_ms;    /* tn_plan_tune_steps: one pass of slice 0 with the variants it started from */
   double  tune_tuned_ms;      /* ... and with the variants it chose (the faster set is kept) */
 } tn_plan_stats;
 
@@ -203,9 +204,11 @@ int  tn_plan_set_step_variant(tn_plan_t* plan, int64_t i, int variant);
  * slice 0 per variant set, per-launch CUDA events on `stream`, in order, the
  * fastest of `reps` >= 1 repetitions after one untimed pass; variant v of
  * every step is timed in the same pass), chooses each step's fastest, then
- * times whole slices with the starting and the chosen variants (alternating,
- * best of `reps`) and keeps the faster set.  *default_ms / *tuned_ms (may be
- * NULL) receive those two slice times.  Synchronous; allocates a scratch
+ * times one pass of slice 0 (the whole slice unless the plan has
+ * automatically sliced edges) with the starting and the chosen variants, in
+ * the plan's own launch order (alternating, best of `reps`), and keeps the
+ * faster set.  *default_ms / *tuned_ms (may be NULL) receive those two pass
+ * times.  Synchronous; allocates a scratch
  * head; the plan's heads are not touched.  Errors: TN_ERR_INVALID for a
  * host-only plan, TN_ERR_CUDA, TN_ERR_TIMEOUT if a bounded wait gave up. */
 int  tn_plan_tune_steps(tn_plan_t* plan, int reps, void* stream, double* default_ms, double* tuned_ms);

@@ -848,14 +848,15 @@ extern "C" int tn_plan_tune_steps(tn_plan_t* plan, int reps, void* stream, doubl
       }
     }
   }
-  // 2. whole slices (the plan's own execution path), starting set against the
+  // 2. one pass of slice 0 each (a whole slice unless the plan has automatically
+  // sliced edges) on the plan's own execution path, starting set against the
   // chosen one, alternating
   double t_start = 1e300, t_best = 1e300;
   for (int r = 0; r <= reps && rc == TN_OK; ++r)
     for (int which = 0; which < 2 && rc == TN_OK; ++which) {
       set_all(which == 0 ? start : best_v);
       cudaEventRecord(e0, st);
-      rc = run_slice(plan, 0, h->H, st);
+      rc = run_pass(plan, 0, h->H, st, nullptr);
       cudaEventRecord(e1, st);
       if (rc) break;
       const cudaError_t e = cudaEventSynchronize(e1);
@@ -1455,14 +1456,16 @@ extern "C" int tn_plan_autotune(const tn_circuit* circuit, const tn_open_spec* o
   if (!best) return last_rc ? last_rc : fail(TN_ERR_OOM, "no candidate plan could be built");
   best->measured_slice_ms = best_ms;
   best->autotune_candidates = distinct;
-  if (o.tune_steps > 0 || (o.tune_steps == 0 && best_ms <= 1000.0)) {
+  const double passes = std::ldexp(1.0, best->P.n_internal);
+  if (o.tune_steps > 0 || (o.tune_steps == 0 && best_ms / passes <= 1000.0)) {
     double t0 = 0, t1 = 0;
     const int rc = tn_plan_tune_steps(best, o.tune_steps > 0 ? o.tune_steps : 3, stream, &t0, &t1);
     if (rc) {
       tn_plan_free(best);
       return rc;
     }
-    best->measured_slice_ms = std::min(t0, t1);
+    // the tuner times one pass: a slice is 2^n_internal of them
+    best->measured_slice_ms = best->P.n_internal == 0 ? std::min(t0, t1) : best_ms * std::min(t0, t1) / t0;
   }
   *out = best;
   return TN_OK;
