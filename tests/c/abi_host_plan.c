@@ -52,6 +52,18 @@ int main(void) {
   if (!d || !strstr(d, "\"n_sliced\":1")) return 4;
   int64_t np = 0;
   if (tn_plan_order(plan, NULL, 0, &np) != TN_OK || np < 1) return 5;
+  /* per-step tile variants: every step has at least one; choosing the last
+     and then the first again is accepted, one past the last is not */
+  for (int64_t i = 0; i + 1 < st.n_launches; ++i) {
+    int nv = 0, chosen = -1;
+    if (tn_plan_step_variants(plan, i, &nv, &chosen) != TN_OK || nv < 1 || chosen != 0) return 9;
+    if (tn_plan_set_step_variant(plan, i, nv - 1) != TN_OK) return 10;
+    if (tn_plan_step_variants(plan, i, &nv, &chosen) != TN_OK || chosen != nv - 1) return 11;
+    if (tn_plan_set_step_variant(plan, i, 0) != TN_OK) return 12;
+    if (tn_plan_set_step_variant(plan, i, nv) != TN_ERR_INVALID) return 13;
+  }
+  /* the tuner needs the device: a host-only plan is refused */
+  if (tn_plan_tune_steps(plan, 1, NULL, NULL, NULL) != TN_ERR_INVALID) return 14;
   tn_plan_free(plan);
   /* errors come back as codes with a message, never as an abort */
   spec.n_tails = 0;
