@@ -1,5 +1,6 @@
 // C ABI: plans, heads, slice contraction, amplitudes, sampling.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -37,6 +38,29 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// NVTX range around a scope: a profiler (nsys, or ncu with --nvtx) sees each
+// pass and each step's launch by name; without a tool attached the calls do
+// nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+const char* step_range_name(int kind) {
+  switch (kind) {
+    case tn::ST_SMALL: return "tn small_operand";
+    case tn::ST_PERMUTE: return "tn permute";
+    case tn::ST_BPREP_TC: return "tn bprep_tc";
+    case tn::ST_GEMM_TC: return "tn gemm_tc";
+    case tn::ST_BPREP_C: return "tn bprep_simt";
+    case tn::ST_GEMM_SIMT: return "tn gemm_simt";
+    case tn::ST_ABSMAX: return "tn operand_max";
+    default: return "tn step";
+  }
 }
 
 }  // namespace
@@ -404,6 +428,7 @@ static unsigned int* scale_ptr(const tn_plan_t* p, int slot) {
 // (`side`: a B-prep beside a running GEMM, launched with one block per SM).
 static cudaError_t launch_step(tn_plan_t* p, const tn::Step& x, int64_t s, cudaStream_t st, bool side) {
   const tn::Plan& P = p->P;
+  NvtxRange range(step_range_name(x.kind));
   cudaError_t e = cudaSuccess;
   switch (x.kind) {
     case tn::ST_SMALL: {
@@ -528,6 +553,7 @@ static cudaError_t launch_step(tn_plan_t* p, const tn::Step& x, int64_t s, cudaS
 // consumes its output.
 static int run_pass(tn_plan_t* p, int64_t s, double2* H, cudaStream_t st, cudaEvent_t* ev) {
   const tn::Plan& P = p->P;
+  NvtxRange range("tn pass");
   if (P.n_scale_slots > 0) {
     cudaError_t e = cudaMemsetAsync(p->d_scale + P.scale_static.size(), 0,
                                     (size_t)P.n_scale_slots * sizeof(unsigned int), st);
